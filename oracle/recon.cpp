@@ -1,0 +1,425 @@
+/*
+ * Oracle: spatial reconstruction (Sec. 3.2 CGKS-5th, Sec. 3.3 GKS-2nd).
+ * Test infrastructure only (see oracle.h).
+ *
+ * All polynomials live in normalised cell coordinates
+ * delta = (x - x0)/h per axis (Eq. base), the target cell being
+ * [-1/2, 1/2]^3. Neighbour offsets, in this order:
+ *   face neighbours Omega_{1,m}, m = 0..5:  -x, +x, -y, +y, -z, +z;
+ *   edge neighbours Omega_{2,n}, n = 0..11: (-1,-1,0) (+1,-1,0) (-1,+1,0)
+ *     (+1,+1,0) (-1,0,-1) (+1,0,-1) (-1,0,+1) (+1,0,+1) (0,-1,-1)
+ *     (0,+1,-1) (0,-1,+1) (0,+1,+1).
+ * Per-variable data vector d (63 entries) of the CGKS-5th stencil
+ * (S^data-5th with readings R1, R2 of oracle.h):
+ *   d[m]          Q_{1,m} - Q_0                      (m = 0..5)
+ *   d[6+n]        Q_{2,n} - Q_0                      (n = 0..11)
+ *   d[18+3m+j]    h_j dQ/dx_j averaged over Omega_{1,m}
+ *   d[36+2n+t]    h dQ/dtau_t averaged over Omega_{2,n}: tau_0 is the unit
+ *                 in-plane direction (o_a e_a - o_b e_b)/sqrt(2) orthogonal
+ *                 to the centre-to-centre offset o (a < b its non-zero
+ *                 axes), tau_1 the edge direction (the axis where o = 0)
+ *   d[60+j]       h_j dQ/dx_j averaged over Omega_0.
+ */
+#include "oracle_internal.h"
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+namespace orc {
+
+int frame_axis(int d, int j) { return (d + j) % 3; }
+
+void face_gauss_point(int f, int k, double x[3]) {
+    const int d = f / 2;
+    const double g = 0.5 / std::sqrt(3.0);  /* 2-point Gauss on [-1/2, 1/2] */
+    x[d] = (f % 2) ? 0.5 : -0.5;
+    x[frame_axis(d, 1)] = (k & 1) ? g : -g;
+    x[frame_axis(d, 2)] = (k & 2) ? g : -g;
+}
+
+namespace {
+
+typedef long double ld;
+
+const int kFace[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0},
+                         {0, 1, 0},  {0, 0, -1}, {0, 0, 1}};
+const int kEdge[12][3] = {{-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0},
+                          {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1}, {1, 0, 1},
+                          {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1}};
+
+struct Basis { int d[34][3]; };
+
+Basis make_basis() {
+    Basis b;
+    int n = 0;
+    for (int deg = 1; deg <= 4; ++deg)
+        for (int i = deg; i >= 0; --i)
+            for (int j = deg - i; j >= 0; --j) {
+                b.d[n][0] = i; b.d[n][1] = j; b.d[n][2] = deg - i - j;
+                ++n;
+            }
+    return b;
+}
+
+ld fact(int n) { ld f = 1; for (int i = 2; i <= n; ++i) f *= i; return f; }
+ld ipow(ld x, int n) { ld r = 1; for (int i = 0; i < n; ++i) r *= x; return r; }
+
+/* average of x^n over [o - 1/2, o + 1/2] */
+ld avg1(int o, int n) {
+    return (ipow(o + 0.5L, n + 1) - ipow(o - 0.5L, n + 1)) / (n + 1);
+}
+/* average over the unit cell at offset o of delta^e / e! (e may have a
+ * negative entry: then the derivative vanished and the value is 0)     */
+ld avg_mono(const int o[3], const int e[3]) {
+    for (int j = 0; j < 3; ++j) if (e[j] < 0) return 0;
+    return avg1(o[0], e[0]) * avg1(o[1], e[1]) * avg1(o[2], e[2]) /
+           (fact(e[0]) * fact(e[1]) * fact(e[2]));
+}
+/* average over offset o of p_d (zero mean over the target cell) */
+ld avg_p(const int o[3], const int d[3]) {
+    static const int z[3] = {0, 0, 0};
+    return avg_mono(o, d) - avg_mono(z, d);
+}
+/* average over offset o of d p_d / d delta_j */
+ld avg_dp(const int o[3], const int d[3], int j) {
+    int e[3] = {d[0], d[1], d[2]};
+    e[j] -= 1;
+    return avg_mono(o, e);
+}
+
+/* Gauss-Jordan elimination with partial pivoting on an n x (n + m)
+ * augmented long-double matrix (row major). Returns -1 if singular.    */
+int gauss_jordan(int n, int m, std::vector<ld> &A) {
+    const int w = n + m;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs((double)A[r * w + c]) > std::fabs((double)A[piv * w + c])) piv = r;
+        if (A[piv * w + c] == 0) return -1;
+        if (piv != c)
+            for (int j = 0; j < w; ++j) std::swap(A[c * w + j], A[piv * w + j]);
+        const ld inv = 1 / A[c * w + c];
+        for (int j = 0; j < w; ++j) A[c * w + j] *= inv;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const ld f = A[r * w + c];
+            if (f == 0) continue;
+            for (int j = 0; j < w; ++j) A[r * w + j] -= f * A[c * w + j];
+        }
+    }
+    return 0;
+}
+
+struct Recon5Tables {
+    double R[34][63];          /* coefficients a = R d                      */
+    double H[34][34];          /* IS_H = a^T H a                            */
+    double mean0[34];          /* mean of delta^d/d! over the target cell   */
+    int ok;
+};
+
+Recon5Tables build_tables() {
+    Recon5Tables T;
+    std::memset(&T, 0, sizeof(T));
+    const Basis b = make_basis();
+    static const int z[3] = {0, 0, 0};
+    /* constrained least squares of Eq. compact-big-5:
+     *   C a = d_C  (cell averages of the 18 neighbours, exact),
+     *   B a ~ d_B  (45 derivative equations, least squares, unit weight R3).
+     * KKT system [B^T B  C^T; C  0] [a; lambda] = [B^T d_B; d_C].        */
+    ld C[18][34], B[45][34];
+    for (int k = 0; k < 18; ++k) {
+        const int *o = (k < 6) ? kFace[k] : kEdge[k - 6];
+        for (int i = 0; i < 34; ++i) C[k][i] = avg_p(o, b.d[i]);
+    }
+    int r = 0;
+    for (int m = 0; m < 6; ++m)
+        for (int j = 0; j < 3; ++j, ++r)
+            for (int i = 0; i < 34; ++i) B[r][i] = avg_dp(kFace[m], b.d[i], j);
+    for (int n = 0; n < 12; ++n) {
+        const int *o = kEdge[n];
+        int axes[2], na = 0, ez = 0;
+        for (int j = 0; j < 3; ++j) {
+            if (o[j] != 0) axes[na++] = j; else ez = j;
+        }
+        const ld rs2 = 1 / std::sqrt(2.0L);
+        for (int i = 0; i < 34; ++i)
+            B[r][i] = rs2 * (o[axes[0]] * avg_dp(o, b.d[i], axes[0]) -
+                             o[axes[1]] * avg_dp(o, b.d[i], axes[1]));
+        ++r;
+        for (int i = 0; i < 34; ++i) B[r][i] = avg_dp(o, b.d[i], ez);
+        ++r;
+    }
+    for (int j = 0; j < 3; ++j, ++r)
+        for (int i = 0; i < 34; ++i) B[r][i] = avg_dp(z, b.d[i], j);
+
+    const int n = 34 + 18, m = 63, w = n + m;
+    std::vector<ld> A((size_t)n * w, 0);
+    for (int i = 0; i < 34; ++i) {
+        for (int j = 0; j < 34; ++j) {
+            ld s = 0;
+            for (int q = 0; q < 45; ++q) s += B[q][i] * B[q][j];
+            A[i * w + j] = s;
+        }
+        for (int k = 0; k < 18; ++k) A[i * w + 34 + k] = C[k][i];
+        /* right-hand side for the derivative data: B^T e_q */
+        for (int q = 0; q < 45; ++q) A[i * w + n + 18 + q] = B[q][i];
+    }
+    for (int k = 0; k < 18; ++k) {
+        for (int j = 0; j < 34; ++j) A[(34 + k) * w + j] = C[k][j];
+        A[(34 + k) * w + n + k] = 1;  /* right-hand side for d_C */
+    }
+    if (gauss_jordan(n, m, A)) { T.ok = 0; return T; }
+    for (int i = 0; i < 34; ++i)
+        for (int c = 0; c < 63; ++c) T.R[i][c] = (double)A[i * w + n + c];
+
+    /* smoothness quadratic form: sum over 1 <= |alpha| <= 4 of
+     * int_{[-1/2,1/2]^3} D^alpha p_d D^alpha p_e                         */
+    auto cell_int = [](int e0, int e1, int e2) -> ld {
+        const int e[3] = {e0, e1, e2};
+        ld v = 1;
+        for (int j = 0; j < 3; ++j) {
+            if (e[j] % 2) return 0;
+            v *= ipow(0.5L, e[j]) / (e[j] + 1);
+        }
+        return v;
+    };
+    for (int i = 0; i < 34; ++i)
+        for (int j = 0; j < 34; ++j) {
+            ld s = 0;
+            for (int a0 = 0; a0 <= 4; ++a0)
+                for (int a1 = 0; a0 + a1 <= 4; ++a1)
+                    for (int a2 = 0; a0 + a1 + a2 <= 4; ++a2) {
+                        if (a0 + a1 + a2 == 0) continue;
+                        const int al[3] = {a0, a1, a2};
+                        int ei[3], ej[3];
+                        bool ok = true;
+                        for (int q = 0; q < 3; ++q) {
+                            ei[q] = b.d[i][q] - al[q];
+                            ej[q] = b.d[j][q] - al[q];
+                            if (ei[q] < 0 || ej[q] < 0) ok = false;
+                        }
+                        if (!ok) continue;
+                        s += cell_int(ei[0] + ej[0], ei[1] + ej[1], ei[2] + ej[2]) /
+                             (fact(ei[0]) * fact(ei[1]) * fact(ei[2]) *
+                              fact(ej[0]) * fact(ej[1]) * fact(ej[2]));
+                    }
+            T.H[i][j] = (double)s;
+        }
+    for (int i = 0; i < 34; ++i) T.mean0[i] = (double)avg_mono(z, b.d[i]);
+    T.ok = 1;
+    return T;
+}
+
+const Recon5Tables &tables() {
+    static Recon5Tables T;
+    static std::once_flag once;
+    std::call_once(once, [] { T = build_tables(); });
+    return T;
+}
+
+const Basis &basis() {
+    static const Basis b = make_basis();
+    return b;
+}
+
+/* value and normalised gradient of p_d at x */
+void eval_basis(const double x[3], double p[34], double dp[3][34]) {
+    const Basis &b = basis();
+    const Recon5Tables &T = tables();
+    for (int i = 0; i < 34; ++i) {
+        const int *d = b.d[i];
+        double v = 1.0;
+        for (int j = 0; j < 3; ++j) v *= std::pow(x[j], d[j]) / (double)fact(d[j]);
+        p[i] = v - T.mean0[i];
+        for (int q = 0; q < 3; ++q) {
+            if (d[q] == 0) { dp[q][i] = 0.0; continue; }
+            double g = 1.0;
+            for (int j = 0; j < 3; ++j) {
+                const int e = d[j] - (j == q ? 1 : 0);
+                g *= std::pow(x[j], e) / (double)fact(e);
+            }
+            dp[q][i] = g;
+        }
+    }
+}
+
+}  // namespace
+
+void recon5_cell(const double *q0, const double *dvec, double hx, double hy,
+                 double hz, int nonlinear, double *out, double *chi5) {
+    const Recon5Tables &T = tables();
+    const double h[3] = {hx, hy, hz};
+    /* GENO constants of Eq. weno-new */
+    const double eps = 1e-15, dm = 1.0 / 6.0;
+    double val[5][24], grad[5][24][3];
+    for (int v = 0; v < 5; ++v) {
+        const double *d = dvec + 63 * v;
+        double a[34];
+        for (int i = 0; i < 34; ++i) {
+            double s = 0.0;
+            for (int c = 0; c < 63; ++c) s += T.R[i][c] * d[c];
+            a[i] = s;
+        }
+        double chi = 1.0, w[6] = {0, 0, 0, 0, 0, 0}, bm[6][3];
+        if (nonlinear) {
+            /* linear sub-stencil polynomials P1_m (reading R4) */
+            double IS[6], wsum = 0.0;
+            for (int m = 0; m < 6; ++m) {
+                const int ax = m / 2;
+                const double sg = (m % 2) ? 1.0 : -1.0;
+                for (int j = 0; j < 3; ++j) bm[m][j] = d[60 + j];
+                bm[m][ax] = sg * d[m];
+                IS[m] = bm[m][0] * bm[m][0] + bm[m][1] * bm[m][1] + bm[m][2] * bm[m][2];
+                w[m] = dm / std::pow(IS[m] + eps, 5);
+                wsum += w[m];
+            }
+            double ISL = 0.0;
+            for (int m = 0; m < 6; ++m) { w[m] /= wsum; ISL += w[m] * IS[m]; }
+            double ISH = 0.0;
+            for (int i = 0; i < 34; ++i)
+                for (int j = 0; j < 34; ++j) ISH += a[i] * T.H[i][j] * a[j];
+            /* project-defined chi (reading R5) */
+            const double rr = std::fabs(ISH - ISL) / (ISH + ISL + eps);
+            const double q = rr / 0.1;
+            chi = 1.0 / (1.0 + q * q * q);
+        }
+        if (chi5) chi5[v] = chi;
+        for (int f = 0; f < 6; ++f)
+            for (int k = 0; k < 4; ++k) {
+                double x[3], p[34], dp[3][34];
+                face_gauss_point(f, k, x);
+                eval_basis(x, p, dp);
+                double P4 = q0[v], dP4[3] = {0, 0, 0};
+                for (int i = 0; i < 34; ++i) {
+                    P4 += a[i] * p[i];
+                    for (int j = 0; j < 3; ++j) dP4[j] += a[i] * dp[j][i];
+                }
+                double Q = P4, dQ[3] = {dP4[0], dP4[1], dP4[2]};
+                if (nonlinear) {
+                    double P1 = 0.0, dP1[3] = {0, 0, 0};
+                    for (int m = 0; m < 6; ++m) {
+                        P1 += w[m] * (q0[v] + bm[m][0] * x[0] + bm[m][1] * x[1] +
+                                      bm[m][2] * x[2]);
+                        for (int j = 0; j < 3; ++j) dP1[j] += w[m] * bm[m][j];
+                    }
+                    Q = chi * P4 + (1.0 - chi) * P1;
+                    for (int j = 0; j < 3; ++j) dQ[j] = chi * dP4[j] + (1.0 - chi) * dP1[j];
+                }
+                val[v][f * 4 + k] = Q;
+                for (int j = 0; j < 3; ++j) grad[v][f * 4 + k][j] = dQ[j] / h[j];
+            }
+    }
+    /* face-frame output */
+    for (int f = 0; f < 6; ++f) {
+        const int d = f / 2;
+        for (int k = 0; k < 4; ++k) {
+            double *o = out + (f * 4 + k) * 20;
+            const int g = f * 4 + k;
+            for (int c = 0; c < 5; ++c) {
+                /* component c of the face-frame conserved vector */
+                const int v = (c >= 1 && c <= 3) ? 1 + frame_axis(d, c - 1) : c;
+                o[c] = val[v][g];
+                for (int j = 0; j < 3; ++j) o[5 + 5 * j + c] = grad[v][g][frame_axis(d, j)];
+            }
+        }
+    }
+}
+
+void recon2_cell(const double *q7, double hx, double hy, double hz,
+                 int nonlinear, double *out, double *phi5) {
+    const double h[3] = {hx, hy, hz};
+    /* Venkatakrishnan parameter (reading R9) */
+    const double hv = std::cbrt(hx * hy * hz);
+    const double eps2 = hv * hv * hv;
+    double b[5][3], phi[5];
+    for (int v = 0; v < 5; ++v) {
+        const double Q0 = q7[v];
+        /* least squares of Sec. 3.3: averages of P1 over the six face
+         * neighbours, Q0 + b . offset = Q_m, solved by normal equations  */
+        double A[6][3], r[6];
+        for (int m = 0; m < 6; ++m) {
+            for (int j = 0; j < 3; ++j) A[m][j] = kFace[m][j];
+            r[m] = q7[5 * (m + 1) + v] - Q0;
+        }
+        double N[9], rhs[3];
+        for (int i = 0; i < 3; ++i) {
+            rhs[i] = 0.0;
+            for (int m = 0; m < 6; ++m) rhs[i] += A[m][i] * r[m];
+            for (int j = 0; j < 3; ++j) {
+                double s = 0.0;
+                for (int m = 0; m < 6; ++m) s += A[m][i] * A[m][j];
+                N[3 * i + j] = s;
+            }
+        }
+        solve_dense(3, N, rhs, b[v]);
+        phi[v] = 1.0;
+        if (nonlinear) {
+            double qmax = Q0, qmin = Q0;
+            for (int m = 0; m < 6; ++m) {
+                const double q = q7[5 * (m + 1) + v];
+                if (q > qmax) qmax = q;
+                if (q < qmin) qmin = q;
+            }
+            for (int f = 0; f < 6; ++f) {
+                double xf[3] = {0, 0, 0};
+                xf[f / 2] = (f % 2) ? 0.5 : -0.5;
+                const double d2 = b[v][0] * xf[0] + b[v][1] * xf[1] + b[v][2] * xf[2];
+                double pf = 1.0;
+                if (d2 != 0.0) {
+                    const double dp = (d2 > 0.0) ? qmax - Q0 : qmin - Q0;
+                    pf = (dp * dp + eps2 + 2.0 * d2 * dp) /
+                         (dp * dp + 2.0 * d2 * d2 + d2 * dp + eps2);
+                }
+                if (pf < phi[v]) phi[v] = pf;
+            }
+        }
+        if (phi5) phi5[v] = phi[v];
+    }
+    for (int f = 0; f < 6; ++f) {
+        const int d = f / 2;
+        double xf[3] = {0, 0, 0};
+        xf[d] = (f % 2) ? 0.5 : -0.5;
+        double *o = out + f * 20;
+        for (int c = 0; c < 5; ++c) {
+            const int v = (c >= 1 && c <= 3) ? 1 + frame_axis(d, c - 1) : c;
+            o[c] = q7[v] + phi[v] * (b[v][0] * xf[0] + b[v][1] * xf[1] + b[v][2] * xf[2]);
+            for (int j = 0; j < 3; ++j) {
+                const int ax = frame_axis(d, j);
+                o[5 + 5 * j + c] = phi[v] * b[v][ax] / h[ax];
+            }
+        }
+    }
+}
+
+}  // namespace orc
+
+extern "C" int orc_recon5_matrix(double *R) {
+    const orc::Recon5Tables &T = orc::tables();
+    if (!T.ok) return -1;
+    std::memcpy(R, T.R, sizeof(T.R));
+    return 0;
+}
+
+extern "C" int orc_is_matrix(double *H) {
+    const orc::Recon5Tables &T = orc::tables();
+    if (!T.ok) return -1;
+    std::memcpy(H, T.H, sizeof(T.H));
+    return 0;
+}
+
+extern "C" int orc_recon5_cell(const double *q0, const double *dvec, double hx,
+                               double hy, double hz, int nonlinear,
+                               double *out480, double *chi5) {
+    if (!orc::tables().ok) return -1;
+    orc::recon5_cell(q0, dvec, hx, hy, hz, nonlinear, out480, chi5);
+    return 0;
+}
+
+extern "C" int orc_recon2_cell(const double *q7, double hx, double hy,
+                               double hz, int nonlinear, double *out120,
+                               double *phi5) {
+    orc::recon2_cell(q7, hx, hy, hz, nonlinear, out120, phi5);
+    return 0;
+}

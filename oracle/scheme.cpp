@@ -1,0 +1,366 @@
+/*
+ * Oracle: finite-volume scheme on a periodic uniform Cartesian grid
+ * (Sec. 2 Eq. semi, Sec. 3.1, Sec. 3.4, Sec. 4).
+ * Test infrastructure only (see oracle.h).
+ *
+ * State layout: Q[v][k][j][i] (v = rho, rho U, rho V, rho W, rho E; x
+ * fastest), G[v][axis][k][j][i] the cell-averaged gradients (CGKS-5th).
+ * Face records (per axis d, per cell c, for the face on c's low-d side):
+ * [F(5), F_t(5), Q^l(5), dQ^l/dt(5), Q^r(5), dQ^r/dt(5)], global frame,
+ * each averaged over the face's Gauss points.
+ */
+#include "oracle_internal.h"
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace orc {
+namespace {
+
+struct Grid {
+    int nx, ny, nz;
+    long n;
+    double h[3];
+    long idx(int i, int j, int k) const {
+        i = (i % nx + nx) % nx;
+        j = (j % ny + ny) % ny;
+        k = (k % nz + nz) % nz;
+        return ((long)k * ny + j) * nx + i;
+    }
+    void ijk(long c, int &i, int &j, int &k) const {
+        i = (int)(c % nx);
+        j = (int)((c / nx) % ny);
+        k = (int)(c / ((long)nx * ny));
+    }
+};
+
+Grid make_grid(const orc_params &P) {
+    Grid g;
+    g.nx = P.nx; g.ny = P.ny; g.nz = P.nz;
+    g.n = (long)P.nx * P.ny * P.nz;
+    g.h[0] = P.Lx / P.nx; g.h[1] = P.Ly / P.ny; g.h[2] = P.Lz / P.nz;
+    return g;
+}
+
+const int kFaceOff[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0},
+                            {0, 1, 0},  {0, 0, -1}, {0, 0, 1}};
+const int kEdgeOff[12][3] = {{-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0},
+                             {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1}, {1, 0, 1},
+                             {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1}};
+
+int nthreads(const orc_params &P) { return P.threads > 0 ? P.threads : 1; }
+
+/* Reconstructed face states of every cell: fs[c][f][k][20]. */
+void face_states(const orc_params &P, const Grid &g, const double *Q,
+                 const double *G, std::vector<double> &fs) {
+    const int ngp = P.scheme ? 4 : 1;
+    fs.assign((size_t)g.n * 6 * ngp * 20, 0.0);
+    const long n = g.n;
+#pragma omp parallel for num_threads(nthreads(P)) schedule(static)
+    for (long c = 0; c < n; ++c) {
+        int i, j, k;
+        g.ijk(c, i, j, k);
+        double *o = &fs[(size_t)c * 6 * ngp * 20];
+        if (P.scheme) {
+            double q0[5], d[5 * 63];
+            for (int v = 0; v < 5; ++v) {
+                q0[v] = Q[v * n + c];
+                double *dv = d + 63 * v;
+                for (int m = 0; m < 6; ++m) {
+                    const long nb = g.idx(i + kFaceOff[m][0], j + kFaceOff[m][1], k + kFaceOff[m][2]);
+                    dv[m] = Q[v * n + nb] - q0[v];
+                    for (int a = 0; a < 3; ++a)
+                        dv[18 + 3 * m + a] = g.h[a] * G[(v * 3 + a) * n + nb];
+                }
+                for (int e = 0; e < 12; ++e) {
+                    const long nb = g.idx(i + kEdgeOff[e][0], j + kEdgeOff[e][1], k + kEdgeOff[e][2]);
+                    dv[6 + e] = Q[v * n + nb] - q0[v];
+                    /* tangential derivatives of the edge neighbour (R2) */
+                    const int *o = kEdgeOff[e];
+                    int ax[2], na = 0, ez = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        if (o[a] != 0) ax[na++] = a; else ez = a;
+                    }
+                    const double da = g.h[ax[0]] * G[(v * 3 + ax[0]) * n + nb];
+                    const double db = g.h[ax[1]] * G[(v * 3 + ax[1]) * n + nb];
+                    dv[36 + 2 * e] = (o[ax[0]] * da - o[ax[1]] * db) / std::sqrt(2.0);
+                    dv[36 + 2 * e + 1] = g.h[ez] * G[(v * 3 + ez) * n + nb];
+                }
+                for (int a = 0; a < 3; ++a) dv[60 + a] = g.h[a] * G[(v * 3 + a) * n + c];
+            }
+            recon5_cell(q0, d, g.h[0], g.h[1], g.h[2], P.nonlinear, o, nullptr);
+        } else {
+            double q7[35];
+            for (int v = 0; v < 5; ++v) q7[v] = Q[v * n + c];
+            for (int m = 0; m < 6; ++m) {
+                const long nb = g.idx(i + kFaceOff[m][0], j + kFaceOff[m][1], k + kFaceOff[m][2]);
+                for (int v = 0; v < 5; ++v) q7[5 * (m + 1) + v] = Q[v * n + nb];
+            }
+            recon2_cell(q7, g.h[0], g.h[1], g.h[2], P.nonlinear, o, nullptr);
+        }
+    }
+}
+
+/* Fluxes of all faces, averaged over each face's Gauss points with the
+ * weights of the tensor 2-point rule (1/4 each) or the midpoint rule.
+ * rec[d][30][c], face on c's low-d side; returns first error code.     */
+int face_fluxes(const orc_params &P, const Grid &g, const std::vector<double> &fs,
+                double dt, double *rec) {
+    const int ngp = P.scheme ? 4 : 1;
+    const double wgt = 1.0 / ngp;
+    const long n = g.n;
+    int err = 0;
+    for (int d = 0; d < 3; ++d) {
+#pragma omp parallel for num_threads(nthreads(P)) schedule(static)
+        for (long c = 0; c < n; ++c) {
+            int i, j, k;
+            g.ijk(c, i, j, k);
+            const long left = g.idx(i - (d == 0), j - (d == 1), k - (d == 2));
+            double acc[30];
+            for (int q = 0; q < 30; ++q) acc[q] = 0.0;
+            for (int p = 0; p < ngp; ++p) {
+                const double *sl = &fs[(((size_t)left * 6 + 2 * d + 1) * ngp + p) * 20];
+                const double *sr = &fs[(((size_t)c * 6 + 2 * d) * ngp + p) * 20];
+                double out[30];
+                const int rc = flux_gp(P, sl, sr, dt, out);
+                if (rc) {
+#pragma omp atomic write
+                    err = rc;
+                }
+                for (int q = 0; q < 30; ++q) acc[q] += wgt * out[q];
+            }
+            /* back to the global frame */
+            for (int blk = 0; blk < 6; ++blk) {
+                const double *a = acc + 5 * blk;
+                double gl[5];
+                gl[0] = a[0];
+                gl[4] = a[4];
+                for (int jj = 0; jj < 3; ++jj) gl[1 + frame_axis(d, jj)] = a[1 + jj];
+                for (int v = 0; v < 5; ++v) rec[((size_t)d * 30 + 5 * blk + v) * n + c] = gl[v];
+            }
+        }
+    }
+    return err;
+}
+
+/* L = -(1/|Omega|) sum_faces F.n S (Eq. semi), and its time derivative. */
+void operator_L(const Grid &g, const double *rec, double *L, double *Lt) {
+    const long n = g.n;
+    for (long c = 0; c < n; ++c) {
+        int i, j, k;
+        g.ijk(c, i, j, k);
+        for (int v = 0; v < 5; ++v) {
+            double s = 0.0, st = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const long hi = g.idx(i + (d == 0), j + (d == 1), k + (d == 2));
+                s += (rec[((size_t)d * 30 + v) * n + hi] - rec[((size_t)d * 30 + v) * n + c]) / g.h[d];
+                st += (rec[((size_t)d * 30 + 5 + v) * n + hi] - rec[((size_t)d * 30 + 5 + v) * n + c]) / g.h[d];
+            }
+            L[v * n + c] = -s;
+            Lt[v * n + c] = -st;
+        }
+    }
+}
+
+double viscosity(const orc_params &P, double rho, double p) {
+    if (P.mu_law == 0) return P.mu0;
+    const double th = (p / rho) / P.T_ref;
+    return P.mu0 * 1.4042 * th * std::sqrt(th) / (th + 0.4042);
+}
+
+/* Sec. 4: convective CFL bound and the viscous bound CFL h^2/(3 nu).    */
+double time_step(const orc_params &P, const Grid &g, const double *Q) {
+    const long n = g.n;
+    double rate = 0.0, numax = 0.0;
+    for (long c = 0; c < n; ++c) {
+        double W[5];
+        for (int v = 0; v < 5; ++v) W[v] = Q[v * n + c];
+        const Prim p = primitive(W, P.gamma);
+        const double cs = std::sqrt(P.gamma * p.p / p.rho);
+        const double vel[3] = {p.U, p.V, p.W};
+        for (int d = 0; d < 3; ++d) {
+            const double r = (std::fabs(vel[d]) + cs) / g.h[d];
+            if (r > rate) rate = r;
+        }
+        const double nu = viscosity(P, p.rho, p.p) / p.rho;
+        if (nu > numax) numax = nu;
+    }
+    double dt = P.cfl / rate;
+    if (!P.inviscid && numax > 0.0) {
+        const double hmin = std::fmin(g.h[0], std::fmin(g.h[1], g.h[2]));
+        const double dv = P.cfl * hmin * hmin / (3.0 * numax);
+        if (dv < dt) dt = dv;
+    }
+    return dt;
+}
+
+}  // namespace
+}  // namespace orc
+
+using namespace orc;
+
+extern "C" int orc_face_states(const orc_params *P, const double *Q,
+                               const double *G, double *fs_out) {
+    const Grid g = make_grid(*P);
+    std::vector<double> fs;
+    face_states(*P, g, Q, G, fs);
+    const int ngp = P->scheme ? 4 : 1;
+    /* reorder to [f][k][20][cells] */
+    for (long c = 0; c < g.n; ++c)
+        for (int f = 0; f < 6; ++f)
+            for (int k = 0; k < ngp; ++k)
+                for (int q = 0; q < 20; ++q)
+                    fs_out[(((size_t)f * ngp + k) * 20 + q) * g.n + c] =
+                        fs[(((size_t)c * 6 + f) * ngp + k) * 20 + q];
+    return 0;
+}
+
+extern "C" int orc_stage(const orc_params *P, const double *Q, const double *G,
+                         double dt, double *L, double *Lt, double *faces) {
+    const Grid g = make_grid(*P);
+    std::vector<double> fs;
+    face_states(*P, g, Q, G, fs);
+    std::vector<double> rec((size_t)3 * 30 * g.n);
+    const int rc = face_fluxes(*P, g, fs, dt, rec.data());
+    operator_L(g, rec.data(), L, Lt);
+    if (faces) std::memcpy(faces, rec.data(), sizeof(double) * rec.size());
+    return rc;
+}
+
+extern "C" int orc_dt(const orc_params *P, const double *Q, double *dt) {
+    *dt = time_step(*P, make_grid(*P), Q);
+    return 0;
+}
+
+extern "C" int orc_run(const orc_params *P, double *Q, double *G, int nsteps,
+                       double t_stop, double *t, double *dt_last) {
+    const Grid g = make_grid(*P);
+    const long n = g.n;
+    std::vector<double> fs, rec((size_t)3 * 30 * n), L(5 * n), Lt(5 * n);
+    std::vector<double> Qs, Gs, L1, Lt1, S1;
+    for (int step = 0; step < nsteps; ++step) {
+        double dt = time_step(*P, g, Q);
+        if (*t + dt > t_stop) dt = t_stop - *t;
+        if (!(dt > 0.0)) break;
+        if (P->scheme == 0) {
+            /* GKS-2nd: Q^{n+1} = Q^n + dt L + dt^2/2 dL/dt (Sec. 3.4) */
+            face_states(*P, g, Q, nullptr, fs);
+            const int rc = face_fluxes(*P, g, fs, dt, rec.data());
+            if (rc) return rc;
+            operator_L(g, rec.data(), L.data(), Lt.data());
+            for (long q = 0; q < 5 * n; ++q) Q[q] += dt * L[q] + 0.5 * dt * dt * Lt[q];
+        } else {
+            /* CGKS-5th: two-stage fourth-order update (Sec. 3.4) */
+            face_states(*P, g, Q, G, fs);
+            int rc = face_fluxes(*P, g, fs, dt, rec.data());
+            if (rc) return rc;
+            L1.resize(5 * n);
+            Lt1.resize(5 * n);
+            operator_L(g, rec.data(), L1.data(), Lt1.data());
+            Qs.resize(5 * n);
+            Gs.resize(15 * n);
+            S1.resize(15 * n);
+            for (long q = 0; q < 5 * n; ++q)
+                Qs[q] = Q[q] + 0.5 * dt * L1[q] + 0.125 * dt * dt * Lt1[q];
+            /* interface values: Q* = Q^n + dt/2 dQ^n/dt; the cell gradient by
+             * Gauss's theorem from the face averages (Sec. 3.1)             */
+            for (long c = 0; c < n; ++c) {
+                int i, j, k;
+                g.ijk(c, i, j, k);
+                for (int d = 0; d < 3; ++d) {
+                    const long hi = g.idx(i + (d == 0), j + (d == 1), k + (d == 2));
+                    for (int v = 0; v < 5; ++v) {
+                        const double ql = rec[((size_t)d * 30 + 10 + v) * n + hi];
+                        const double qlt = rec[((size_t)d * 30 + 15 + v) * n + hi];
+                        const double qr = rec[((size_t)d * 30 + 20 + v) * n + c];
+                        const double qrt = rec[((size_t)d * 30 + 25 + v) * n + c];
+                        Gs[(v * 3 + d) * n + c] = ((ql + 0.5 * dt * qlt) - (qr + 0.5 * dt * qrt)) / g.h[d];
+                        S1[(v * 3 + d) * n + c] = (ql - qr) / g.h[d];
+                    }
+                }
+            }
+            face_states(*P, g, Qs.data(), Gs.data(), fs);
+            rc = face_fluxes(*P, g, fs, dt, rec.data());
+            if (rc) return rc;
+            operator_L(g, rec.data(), L.data(), Lt.data());
+            for (long q = 0; q < 5 * n; ++q)
+                Q[q] = Q[q] + dt * L1[q] + dt * dt / 6.0 * (Lt1[q] + 2.0 * Lt[q]);
+            /* Q_G^{n+1} = Q_G^n + dt (dQ_G/dt at the second stage) */
+            for (long c = 0; c < n; ++c) {
+                int i, j, k;
+                g.ijk(c, i, j, k);
+                for (int d = 0; d < 3; ++d) {
+                    const long hi = g.idx(i + (d == 0), j + (d == 1), k + (d == 2));
+                    for (int v = 0; v < 5; ++v) {
+                        const double qlt = rec[((size_t)d * 30 + 15 + v) * n + hi];
+                        const double qrt = rec[((size_t)d * 30 + 25 + v) * n + c];
+                        G[(v * 3 + d) * n + c] = S1[(v * 3 + d) * n + c] + dt * (qlt - qrt) / g.h[d];
+                    }
+                }
+            }
+        }
+        *t += dt;
+        if (dt_last) *dt_last = dt;
+    }
+    return 0;
+}
+
+extern "C" int orc_diagnostics(const orc_params *P, const double *Q,
+                               const double *G, double *out) {
+    const Grid g = make_grid(*P);
+    const long n = g.n;
+    const double vol = g.h[0] * g.h[1] * g.h[2];
+    const double Omega = vol * n;
+    double ek = 0, es = 0, ed = 0, rmin = INFINITY, pmin = INFINITY, bad = 0, smax = 0;
+    double sums[5] = {0, 0, 0, 0, 0};
+    for (long c = 0; c < n; ++c) {
+        int i, j, k;
+        g.ijk(c, i, j, k);
+        double W[5];
+        for (int v = 0; v < 5; ++v) {
+            W[v] = Q[v * n + c];
+            sums[v] += W[v] * vol;
+        }
+        const Prim p = primitive(W, P->gamma);
+        bool ok = std::isfinite(p.rho) && std::isfinite(p.p) && p.rho > 0 && p.p > 0;
+        for (int v = 0; v < 5; ++v) ok = ok && std::isfinite(W[v]);
+        if (!ok) { bad += 1; continue; }
+        rmin = std::fmin(rmin, p.rho);
+        pmin = std::fmin(pmin, p.p);
+        const double vel[3] = {p.U, p.V, p.W};
+        const double cs = std::sqrt(P->gamma * p.p / p.rho);
+        for (int d = 0; d < 3; ++d) smax = std::fmax(smax, std::fabs(vel[d]) + cs);
+        ek += 0.5 * p.rho * (p.U * p.U + p.V * p.V + p.W * p.W) * vol;
+        /* cell gradients of the conserved variables: stored (CGKS-5th) or
+         * central differences of the cell averages (GKS-2nd)             */
+        double dQ[5][3];
+        for (int v = 0; v < 5; ++v)
+            for (int d = 0; d < 3; ++d) {
+                if (G) {
+                    dQ[v][d] = G[(v * 3 + d) * n + c];
+                } else {
+                    const long hi = g.idx(i + (d == 0), j + (d == 1), k + (d == 2));
+                    const long lo = g.idx(i - (d == 0), j - (d == 1), k - (d == 2));
+                    dQ[v][d] = (Q[v * n + hi] - Q[v * n + lo]) / (2.0 * g.h[d]);
+                }
+            }
+        double du[3][3];  /* du[a][d] = d U_a / dx_d */
+        for (int a = 0; a < 3; ++a)
+            for (int d = 0; d < 3; ++d) du[a][d] = (dQ[1 + a][d] - vel[a] * dQ[0][d]) / p.rho;
+        const double wx = du[2][1] - du[1][2], wy = du[0][2] - du[2][0], wz = du[1][0] - du[0][1];
+        const double div = du[0][0] + du[1][1] + du[2][2];
+        const double mu = viscosity(*P, p.rho, p.p);
+        es += mu * (wx * wx + wy * wy + wz * wz) * vol;
+        ed += 4.0 / 3.0 * mu * div * div * vol;
+    }
+    out[0] = ek / Omega;
+    out[1] = es / Omega;
+    out[2] = ed / Omega;
+    out[3] = rmin;
+    out[4] = pmin;
+    for (int v = 0; v < 5; ++v) out[5 + v] = sums[v];
+    out[10] = bad;
+    out[11] = smax;
+    return 0;
+}

@@ -1,0 +1,230 @@
+"""Pins of the oracle's reconstructions (Sec. 3.2 CGKS-5th, Sec. 3.3
+GKS-2nd): exact reproduction of polynomials, the smoothness indicator
+against direct quadrature, and the nonlinear weights' limits."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from numpy.polynomial.legendre import leggauss
+
+FACE = [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+EDGE = [(-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 1, 0), (-1, 0, -1), (1, 0, -1),
+        (-1, 0, 1), (1, 0, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1), (0, 1, 1)]
+GX, GW = leggauss(4)
+
+
+class Poly:
+    """Polynomial in physical coordinates relative to the target cell centre."""
+
+    def __init__(self, coef):
+        self.coef = coef  # dict (a, b, c) -> value
+
+    def __call__(self, x, y, z):
+        return sum(v * x ** a * y ** b * z ** c for (a, b, c), v in self.coef.items())
+
+    def d(self, j):
+        out = {}
+        for e, v in self.coef.items():
+            if e[j] > 0:
+                e2 = list(e)
+                e2[j] -= 1
+                out[tuple(e2)] = out.get(tuple(e2), 0.0) + v * e[j]
+        return Poly(out)
+
+
+def random_poly(rng, deg, scale=1.0):
+    coef = {}
+    for a in range(deg + 1):
+        for b in range(deg + 1 - a):
+            for c in range(deg + 1 - a - b):
+                coef[(a, b, c)] = rng.normal() * scale
+    return Poly(coef)
+
+
+def cell_avg(P, o, h):
+    """Exact cell average (4-point Gauss-Legendre per axis) over the cell at
+    integer offset o, cell sizes h."""
+    xs = [(o[j] + 0.5 * GX) * h[j] for j in range(3)]
+    X, Y, Z = np.meshgrid(*xs, indexing="ij")
+    W = GW[:, None, None] * GW[None, :, None] * GW[None, None, :] / 8.0
+    return float(np.sum(W * P(X, Y, Z)))
+
+
+def data_vector(P, h):
+    """The 63-entry CGKS-5th data vector of the target cell for a field P."""
+    q0 = cell_avg(P, (0, 0, 0), h)
+    d = np.zeros(63)
+    for m, o in enumerate(FACE):
+        d[m] = cell_avg(P, o, h) - q0
+        for j in range(3):
+            d[18 + 3 * m + j] = h[j] * cell_avg(P.d(j), o, h)
+    for n, o in enumerate(EDGE):
+        d[6 + n] = cell_avg(P, o, h) - q0
+        ax = [j for j in range(3) if o[j] != 0]
+        ez = [j for j in range(3) if o[j] == 0][0]
+        da = h[ax[0]] * cell_avg(P.d(ax[0]), o, h)
+        db = h[ax[1]] * cell_avg(P.d(ax[1]), o, h)
+        d[36 + 2 * n] = (o[ax[0]] * da - o[ax[1]] * db) / math.sqrt(2)
+        d[36 + 2 * n + 1] = h[ez] * cell_avg(P.d(ez), o, h)
+    for j in range(3):
+        d[60 + j] = h[j] * cell_avg(P.d(j), (0, 0, 0), h)
+    return q0, d
+
+
+def gauss_point(f, k):
+    d = f // 2
+    g = 0.5 / math.sqrt(3)
+    x = [0.0, 0.0, 0.0]
+    x[d] = 0.5 if f % 2 else -0.5
+    x[(d + 1) % 3] = g if k & 1 else -g
+    x[(d + 2) % 3] = g if k & 2 else -g
+    return x
+
+
+def expected_face_states(polys, h):
+    """Face-frame states (value, d/dn, d/dt1, d/dt2) of five fields."""
+    out = np.zeros((6, 4, 20))
+    for f in range(6):
+        d = f // 2
+        axes = [d, (d + 1) % 3, (d + 2) % 3]
+        for k in range(4):
+            xn = gauss_point(f, k)
+            xp = [xn[j] * h[j] for j in range(3)]
+            for c in range(5):
+                v = 1 + axes[c - 1] if 1 <= c <= 3 else c
+                out[f, k, c] = polys[v](*xp)
+                for j in range(3):
+                    out[f, k, 5 + 5 * j + c] = polys[v].d(axes[j])(*xp)
+    return out
+
+
+@pytest.mark.parametrize("h", [(1.0, 1.0, 1.0), (0.3, 0.5, 0.7)])
+def test_linear_cgks_reproduces_quartics(orc, h):
+    rng = np.random.default_rng(4)
+    polys = [random_poly(rng, 4) for _ in range(5)]
+    q0, d = zip(*[data_vector(P, h) for P in polys])
+    out, chi = orc.recon5_cell(np.array(q0), np.concatenate(d), h, nonlinear=0)
+    exp = expected_face_states(polys, h)
+    scale = np.abs(exp).max()
+    np.testing.assert_allclose(out, exp, rtol=0, atol=1e-11 * scale)
+    assert np.all(chi == 1.0)
+
+
+def test_nonlinear_cgks_reproduces_linear_data_with_chi_one(orc):
+    rng = np.random.default_rng(8)
+    h = (0.2, 0.25, 0.3)
+    polys = [random_poly(rng, 1) for _ in range(5)]
+    q0, d = zip(*[data_vector(P, h) for P in polys])
+    out, chi = orc.recon5_cell(np.array(q0), np.concatenate(d), h, nonlinear=1)
+    np.testing.assert_allclose(chi, 1.0, rtol=0, atol=1e-12)
+    exp = expected_face_states(polys, h)
+    np.testing.assert_allclose(out, exp, rtol=0, atol=1e-12 * np.abs(exp).max())
+
+
+def test_smoothness_indicator_matches_quadrature(orc):
+    """IS_H = sum_{1<=|a|<=4} int_{[-1/2,1/2]^3} (D^a P)^2 for P written in
+    the zero-mean basis p_d = delta^d/d! - mean: coefficient a_d = c_d d!."""
+    H = orc.is_matrix()
+    rng = np.random.default_rng(6)
+    P = random_poly(rng, 4)
+    basis = []
+    for deg in range(1, 5):
+        for i in range(deg, -1, -1):
+            for j in range(deg - i, -1, -1):
+                basis.append((i, j, deg - i - j))
+    a = np.array([P.coef[e] * math.factorial(e[0]) * math.factorial(e[1]) * math.factorial(e[2])
+                  for e in basis])
+    xs = 0.5 * GX
+    X, Y, Z = np.meshgrid(xs, xs, xs, indexing="ij")
+    W = GW[:, None, None] * GW[None, :, None] * GW[None, None, :] / 8.0
+    ref = 0.0
+    for al in itertools.product(range(5), repeat=3):
+        if not 1 <= sum(al) <= 4:
+            continue
+        D = P
+        for j in range(3):
+            for _ in range(al[j]):
+                D = D.d(j)
+        ref += float(np.sum(W * D(X, Y, Z) ** 2))
+    assert a @ H @ a == pytest.approx(ref, rel=1e-12)
+
+
+def test_chi_collapses_across_a_step(orc):
+    """A jump between the target cell and its +x neighbours: chi -> 0 and
+    the values stay within the data range (ENO-like behaviour)."""
+    h = (1.0, 1.0, 1.0)
+    step = Poly({})
+    q0 = np.ones(5)
+    d = np.zeros((5, 63))
+    for m, o in enumerate(FACE):
+        d[:, m] = 1.0 if o[0] > 0 else 0.0
+    for n, o in enumerate(EDGE):
+        d[:, 6 + n] = 1.0 if o[0] > 0 else 0.0
+    out, chi = orc.recon5_cell(q0, d.ravel(), h, nonlinear=1)
+    assert np.all(chi < 1e-2)
+    vals = out[:, :, 0]
+    assert vals.min() > 1.0 - 0.02 and vals.max() < 2.0 + 0.02
+
+
+def test_one_minus_chi_is_at_least_third_order_on_smooth_data(orc):
+    def field(hh):
+        P = Poly({})  # f = sin(1 + x + 2y + 3z) through its Taylor polynomial of degree 8
+        coef = {}
+        for a in range(9):
+            for b in range(9 - a):
+                for c in range(9 - a - b):
+                    n = a + b + c
+                    deriv = math.sin(1 + n * math.pi / 2)
+                    coef[(a, b, c)] = deriv * (1 ** a) * (2 ** b) * (3 ** c) / (
+                        math.factorial(a) * math.factorial(b) * math.factorial(c))
+        P.coef = coef
+        return data_vector(P, (hh, hh, hh))
+
+    vals = []
+    for hh in (0.02, 0.01):
+        q0, d = field(hh)
+        _, chi = orc.recon5_cell(np.full(5, q0), np.tile(d, 5), (hh, hh, hh), nonlinear=1)
+        vals.append(1.0 - chi[0])
+    # at least third order (halving h divides 1 - chi by >= 2^3); on this
+    # field the h^3 terms of opposite sub-stencils cancel and 2^6 is seen
+    ratio = vals[0] / vals[1]
+    assert ratio > 7.0, ratio
+
+
+def test_gks2_reconstruction(orc):
+    rng = np.random.default_rng(12)
+    h = (0.5, 0.4, 0.3)
+    # linear data: exact, limiter inactive
+    polys = [random_poly(rng, 1) for _ in range(5)]
+    q7 = np.zeros((7, 5))
+    for v, P in enumerate(polys):
+        q7[0, v] = cell_avg(P, (0, 0, 0), h)
+        for m, o in enumerate(FACE):
+            q7[m + 1, v] = cell_avg(P, o, h)
+    for nl in (0, 1):
+        out, phi = orc.recon2_cell(q7.ravel(), h, nonlinear=nl)
+        np.testing.assert_allclose(phi, 1.0, rtol=0, atol=1e-12)
+        for f in range(6):
+            d = f // 2
+            axes = [d, (d + 1) % 3, (d + 2) % 3]
+            xf = [0.0, 0.0, 0.0]
+            xf[d] = (0.5 if f % 2 else -0.5) * h[d]
+            for c in range(5):
+                v = 1 + axes[c - 1] if 1 <= c <= 3 else c
+                assert out[f, c] == pytest.approx(polys[v](*xf), rel=1e-12, abs=1e-12)
+                for j in range(3):
+                    assert out[f, 5 + 5 * j + c] == pytest.approx(polys[v].d(axes[j])(0, 0, 0), rel=1e-11)
+    # random data, linear variant: central-difference gradient
+    q7 = rng.uniform(0.5, 1.5, (7, 5))
+    out, _ = orc.recon2_cell(q7.ravel(), h, nonlinear=0)
+    b = np.array([(q7[2] - q7[1]) / 2, (q7[4] - q7[3]) / 2, (q7[6] - q7[5]) / 2])  # [axis][var]
+    assert out[1, 0] == pytest.approx(q7[0, 0] + 0.5 * b[0, 0], rel=1e-14)
+    assert out[1, 5] == pytest.approx(b[0, 0] / h[0], rel=1e-13)
+    # a step activates the limiter; with eps^2 = h^3 small against the jump
+    # the face values stay (almost) inside the data range
+    q7 = np.ones((7, 5))
+    q7[2] = 3.0
+    out, phi = orc.recon2_cell(q7.ravel(), (0.1, 0.1, 0.1), nonlinear=1)
+    assert np.all(phi < 0.01)
+    assert out[:, 0].max() <= 3.0 and out[:, 0].min() >= 0.99

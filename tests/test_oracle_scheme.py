@@ -1,0 +1,208 @@
+"""Pins of the oracle's finite-volume scheme (Sec. 2 Eq. semi, Sec. 3.4,
+Sec. 4): invariants, closed forms of the Taylor-Green initial data, the
+time-step formula, the exact Sod solution and the order of accuracy."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2508_19911_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def P_for(orc, grid, **kw):
+    return orc.params(n=grid.n, L=grid.L, **kw)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_uniform_flow_is_preserved_bitwise(orc, scheme):
+    rng = np.random.default_rng(1)
+    grid = wl.Grid((6, 5, 4), (1.0, 1.3, 0.7))
+    rho, p = 1.3, 0.9
+    U = rng.uniform(-0.5, 0.5, 3)
+    Q = np.zeros((5, 4, 5, 6))
+    Q[0] = rho
+    Q[1:4] = (rho * U)[:, None, None, None]
+    Q[4] = p / 0.4 + 0.5 * rho * U @ U
+    G = np.zeros((5, 3, 4, 5, 6))
+    Q0 = Q.copy()
+    P = P_for(orc, grid, scheme=scheme, nonlinear=1, mu0=1e-3)
+    orc.run(P, Q, G if scheme else None, nsteps=2)
+    assert np.array_equal(Q, Q0)
+    assert np.array_equal(G, np.zeros_like(G))
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_conservation_to_roundoff(orc, scheme):
+    Q, G, grid = wl.taylor_green(8)
+    Q, G = wl.perturb(Q, G, amp=0.05, seed=2)
+    P = P_for(orc, grid, scheme=scheme, nonlinear=1)
+    s0 = np.array([math.fsum(Q[v].ravel()) for v in range(5)])
+    orc.run(P, Q, G if scheme else None, nsteps=2)
+    s1 = np.array([math.fsum(Q[v].ravel()) for v in range(5)])
+    scale = np.array([math.fsum(np.abs(Q[v]).ravel()) for v in range(5)])
+    assert np.all(np.abs(s1 - s0) <= 2e-13 * scale)
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_tgv_initial_energy_and_enstrophy_closed_form(orc, n):
+    """E_k(0) from exact cell averages = sinc^6(h/2)/8; the enstrophy
+    dissipation from cell-averaged gradients = 0.75 mu sinc^6(h/2); the
+    dilatational part vanishes."""
+    Q, G, grid = wl.taylor_green(n)
+    P = P_for(orc, grid, scheme=1, mu0=1.0 / 1600)
+    d = orc.diagnostics(P, Q, G)
+    h = 2 * np.pi / n
+    s6 = (math.sin(h / 2) / (h / 2)) ** 6
+    assert d[0] == pytest.approx(s6 / 8, rel=1e-13)
+    assert d[1] == pytest.approx(0.75 / 1600 * s6, rel=1e-12)
+    assert abs(d[2]) < 1e-25
+    golden = dict(np.loadtxt(GOLDEN + "/tgv_initial_energy.txt"))
+    assert d[0] == pytest.approx(golden[n], abs=5e-8)
+    assert d[10] == 0
+
+
+def test_time_step_formula(orc):
+    grid = wl.Grid((8, 4, 2), (1.0, 1.0, 1.0))
+    rho, p, U = 0.8, 1.1, np.array([0.3, -0.7, 0.2])
+    Q = np.zeros((5, 2, 4, 8))
+    Q[0] = rho
+    Q[1:4] = (rho * U)[:, None, None, None]
+    Q[4] = p / 0.4 + 0.5 * rho * U @ U
+    c = math.sqrt(1.4 * p / rho)
+    h = np.array([1 / 8, 1 / 4, 1 / 2])
+    conv = 0.3 * min(h / (np.abs(U) + c))
+    P = P_for(orc, grid, inviscid=1)
+    assert orc.dt(P, Q) == pytest.approx(conv, rel=1e-14)
+    mu = 0.05
+    P = P_for(orc, grid, mu0=mu)
+    visc = 0.3 * h.min() ** 2 / (3 * mu / rho)
+    assert orc.dt(P, Q) == pytest.approx(min(conv, visc), rel=1e-14)
+
+
+def _mirror_x(Q, G):
+    Qm = Q[..., ::-1].copy()
+    Qm[1] *= -1
+    Gm = None
+    if G is not None:
+        Gm = G[..., ::-1].copy()
+        Gm[:, 0] *= -1          # d/dx flips
+        Gm[1] *= -1             # rho U flips
+    return Qm, Gm
+
+
+def _rot90_z(Q, G):
+    """Rotation by 90 degrees about the axis x = y = pi/2 (parallel to z):
+    point (x, y) -> (pi - y, x), velocity (U, V) -> (-V, U). On the cell
+    grid (n divisible by 4) the new cell (i, j) takes the old cell
+    (j, n/2 - 1 - i)."""
+    n = Q.shape[-1]
+    src_j = (n // 2 - 1 - np.arange(n)) % n   # indexed by the new i
+
+    Qs = np.empty_like(Q)
+    for v in range(5):
+        Qs[v] = np.swapaxes(Q[v][..., src_j, :], -1, -2)
+    Qs[[1, 2]] = np.stack([-Qs[2], Qs[1].copy()])
+    Gs = None
+    if G is not None:
+        Gs = np.empty_like(G)
+        for v in range(5):
+            for d in range(3):
+                Gs[v, d] = np.swapaxes(G[v, d][..., src_j, :], -1, -2)
+        Gx, Gy = Gs[:, 0].copy(), Gs[:, 1].copy()
+        Gs[:, 0], Gs[:, 1] = -Gy, Gx
+        Gs[[1, 2]] = np.stack([-Gs[2], Gs[1].copy()])
+    return Qs, Gs
+
+
+@pytest.mark.parametrize("scheme,steps", [(0, 10), (1, 3)])
+def test_tgv_symmetries_are_kept(orc, scheme, steps):
+    Q, G, grid = wl.taylor_green(12)
+    P = P_for(orc, grid, scheme=scheme, nonlinear=1)
+    Gin = G if scheme else None
+    orc.run(P, Q, Gin, nsteps=steps)
+    for tr in (_mirror_x, _rot90_z):
+        Qt, Gt = tr(Q, Gin)
+        scale = np.abs(Q).max(axis=(1, 2, 3), keepdims=True) + 1e-300
+        assert np.max(np.abs(Qt - Q) / scale) < 1e-12
+        if scheme:
+            gs = np.abs(G).max(axis=(2, 3, 4), keepdims=True) + 1e-300
+            assert np.max(np.abs(Gt - G) / gs) < 1e-11
+
+
+# --- exact Riemann solution (Toro, ch. 4) for the Sod plateaus -------------
+def _exact_star(rl, ul, pl, rr, ur, pr, g=1.4):
+    def fk(p, r, pk):
+        A, B = 2 / ((g + 1) * r), (g - 1) / (g + 1) * pk
+        ck = math.sqrt(g * pk / r)
+        if p > pk:
+            return (p - pk) * math.sqrt(A / (p + B))
+        return 2 * ck / (g - 1) * ((p / pk) ** ((g - 1) / (2 * g)) - 1)
+
+    lo, hi = 1e-8, 10.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if fk(mid, rl, pl) + fk(mid, rr, pr) + ur - ul > 0:
+            hi = mid
+        else:
+            lo = mid
+    ps = 0.5 * (lo + hi)
+    us = 0.5 * (ul + ur) + 0.5 * (fk(ps, rr, pr) - fk(ps, rl, pl))
+    rsl = rl * (ps / pl) ** (1 / g)  # rarefaction on the left
+    q = (g - 1) / (g + 1)
+    rsr = rr * (ps / pr + q) / (q * ps / pr + 1)  # shock on the right
+    return ps, us, rsl, rsr
+
+
+@pytest.mark.parametrize("scheme,nx", [(0, 400), (1, 200)])
+def test_sod_plateaus(orc, scheme, nx):
+    Q, G, grid = wl.double_sod(nx)
+    P = P_for(orc, grid, scheme=scheme, nonlinear=1, inviscid=1, Pr=1.0)
+    t, _ = orc.run(P, Q, G if scheme else None, nsteps=100000, t_stop=0.2)
+    assert t == pytest.approx(0.2, abs=1e-14)
+    ps, us, rsl, rsr = _exact_star(1.0, 0.0, 1.0, 0.125, 0.0, 0.1)
+    golden = np.loadtxt(GOLDEN + "/sod_star_state.txt")
+    np.testing.assert_allclose([ps, us, rsl, rsr], golden, rtol=2e-5)
+    x = (np.arange(nx) + 0.5) * 2.0 / nx
+    rho = Q[0, 0, 0]
+    u = Q[1, 0, 0] / rho
+    p = 0.4 * (Q[4, 0, 0] - 0.5 * rho * u * u)
+    c_l = math.sqrt(1.4)
+    cs_l = c_l * (ps / 1.0) ** (0.2 / 1.4)
+    tail = 1.5 + (us - cs_l) * 0.2
+    contact = 1.5 + us * 0.2
+    shock = 1.5 + 0.2 * us * (rsr / (rsr - 0.125))  # mass balance across the shock
+    for a, b, rho_ref in ((tail, contact, rsl), (contact, shock, rsr)):
+        w = b - a
+        sel = (x > a + 0.25 * w) & (x < b - 0.25 * w)
+        assert sel.sum() >= 5
+        for xs in (sel, sel[::-1]):  # the jump at x = 1.5 and its mirror at x = 0.5
+            assert np.all(np.abs(p[xs] / ps - 1) < 0.01)
+            assert np.all(np.abs(rho[xs] / rho_ref - 1) < 0.01)
+        assert np.all(np.abs(u[sel] / us - 1) < 0.01)
+        assert np.all(np.abs(u[sel[::-1]] / -us - 1) < 0.01)
+
+
+@pytest.mark.parametrize("scheme,sizes,cfl,t_end,lo,hi", [
+    (0, (16, 32, 64), 0.2, 0.5, 1.5, 2.5),
+    (1, (8, 16, 32), 0.5, 2.0, 4.5, 6.5),
+])
+def test_order_of_accuracy_on_smooth_advection(orc, scheme, sizes, cfl, t_end, lo, hi):
+    """Linear variants, tau = 0, 2D smooth advection: every pairwise order
+    of the cell-average density error lies near the design order (2 for
+    GKS-2nd; 5 for CGKS-5th, which this field shows up to ~5.8 at the
+    finest pair). At CFL 0.5 the two-stage time update's own error is
+    large enough that a wrong S2O4 coefficient pulls the finest pair's
+    order down to ~2."""
+    errs = []
+    for n in sizes:
+        Q, G, grid = wl.advection(n, dims=2)
+        P = P_for(orc, grid, scheme=scheme, nonlinear=0, inviscid=1, eps_tau=0.0,
+                  C_tau=0.0, cfl=cfl)
+        t, _ = orc.run(P, Q, G if scheme else None, nsteps=100000, t_stop=t_end)
+        Qe, _, _ = wl.advection(n, dims=2, t=t)
+        errs.append(np.abs(Q[0] - Qe[0]).mean())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(lo < o < hi for o in orders), (errs, orders)
