@@ -1,0 +1,350 @@
+"""Benchmark of the GB300 CGKS-5th / GKS-2nd hot path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full time step of the hot path (dt on the device,
+reconstruction, gas-kinetic flux, cell update; two stages for CGKS-5th) on
+the Taylor-Green vortex (Sec. 4.1; Ma 0.1, Re 1600, gamma 1.4, Pr 0.72,
+CFL 0.3) with synthetic cell-averaged initial data, FP64, nonlinear scheme.
+Metric: cell-stage updates/s (cells x stages x steps / device time).
+
+Multi-GPU: replicas only (the path does not shard on one box): every rank
+advances its own grid, no data-path collective; value = sum over ranks.
+--impl reference times the FP64 CPU oracle on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-stage updates/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_PER_SM = 4   # nominal 1.25 TFLOP/s / (152 SMs x 2.07 GHz)
+SM_MAX_MHZ_NOMINAL = 2070.0
+# FP64 operations (DFMA counted as 2, DADD and DMUL as 1) per unit of work,
+# from ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on on
+# TGV 32^3 (see profiles/); a unit is one face Gauss point for the flux
+# kernel and one cell for the reconstruction kernel.
+FLOPS_PER_UNIT = {
+    "flux_cgks5": None,
+    "recon5": None,
+    "flux_gks2": None,
+}
+LAUNCHES_PER_STEP = {"cgks5": 8, "gks2": 5}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128, help="cells per axis")
+    ap.add_argument("--scheme", default="cgks5", choices=["cgks5", "gks2"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(scheme, seconds_hint=15.0):
+    """The FP64 oracle as it stands, OpenMP over cells on all host cores,
+    on a bounded sample: the same Taylor-Green workload at 24^3 (CGKS-5th)
+    or 48^3 (GKS-2nd), 2 time steps."""
+    import oracle
+    from paper_2508_19911_gb300 import workloads as wl
+    n = 24 if scheme == "cgks5" else 48
+    steps = 2
+    Q, G, grid = wl.taylor_green(n)
+    cores = os.cpu_count() or 1
+    P = oracle.params(n=grid.n, L=grid.L, scheme=1 if scheme == "cgks5" else 0,
+                      nonlinear=1, threads=cores)
+    oracle.run(P, Q.copy(), G.copy() if scheme == "cgks5" else None, nsteps=1)  # warm
+    t0 = time.perf_counter()
+    oracle.run(P, Q, G if scheme == "cgks5" else None, nsteps=steps)
+    el = time.perf_counter() - t0
+    stages = 2 if scheme == "cgks5" else 1
+    return {"value": n ** 3 * stages * steps / el, "unit": METRIC, "cores": cores,
+            "kind": "oracle",
+            "sample": f"TGV {n}^3 {scheme} FP64 nonlinear, {steps} steps ({el:.1f} s)"}
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return None
+    steps_done, el_total = 0, 0.0
+    import oracle
+    from paper_2508_19911_gb300 import workloads as wl
+    n = 24 if args.scheme == "cgks5" else 48
+    Q, G, grid = wl.taylor_green(n)
+    cores = os.cpu_count() or 1
+    cg = args.scheme == "cgks5"
+    P = oracle.params(n=grid.n, L=grid.L, scheme=1 if cg else 0, nonlinear=1, threads=cores)
+    for _ in range(args.warmup):
+        oracle.run(P, Q, G if cg else None, nsteps=1)
+    t0 = time.perf_counter()
+    oracle.run(P, Q, G if cg else None, nsteps=args.steps)
+    el = time.perf_counter() - t0
+    stages = 2 if cg else 1
+    val = n ** 3 * stages * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "cell-stage/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"taylor_green_{n}^3_{args.scheme}_fp64_nonlinear",
+                   "note": "bounded CPU sample of the TGV workload"},
+        "cpu_baseline": {"value": val, "unit": "cell-stage/s", "cores": cores, "kind": "oracle",
+                         "sample": f"TGV {n}^3 {args.scheme} FP64, {args.steps} steps"},
+        "e2e": {"value": val, "unit": "cell-stage/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    return line
+
+
+# ---------------------------------------------------------------------------
+def time_steps(torch, solver, Q, G, steps, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        solver.step(Q, G, nsteps=1, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)  # ms
+
+
+def time_kernel(torch, fn, reps, stream):
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps  # ms per launch
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2508_19911_gb300 import gks
+    from paper_2508_19911_gb300 import workloads as wl
+
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    n = args.n
+    scheme = args.scheme
+    cg = scheme == "cgks5"
+    stages = 2 if cg else 1
+    Qh, Gh, grid = wl.taylor_green(n)
+    cells = n ** 3
+    solver = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=scheme, nonlinear=True), stream)
+    Q = torch.tensor(Qh, device=dev)
+    G = torch.tensor(Gh, device=dev) if cg else None
+    for _ in range(args.warmup):
+        solver.step(Q, G, nsteps=1, sync=False)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    with ClockSampler(local_rank) as clk:
+        ms = time_steps(torch, solver, Q, G, args.steps, stream)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    st = solver.status()
+    if st:
+        raise RuntimeError(f"non-physical state during the benchmark (status {st})")
+    value = world * cells * stages * args.steps / (ms / 1e3)
+
+    # dominant kernel: reconstruction or flux launch timed alone (same inputs)
+    fs = solver.reconstruct(Q, G)
+    dtd = solver.compute_dt(Q)
+    reps = 3
+    t_recon = time_kernel(torch, lambda: solver.reconstruct(Q, G, out=fs), reps, stream)
+    frec = solver.flux(fs, dtd)
+    t_flux = time_kernel(torch, lambda: solver.flux(fs, dtd, out=frec), reps, stream)
+    K = 4 if cg else 1
+    if t_flux >= t_recon:
+        kname, t_k = ("flux_cgks5" if cg else "flux_gks2"), t_flux
+        units = 3 * cells * K
+    else:
+        kname, t_k = "recon5" if cg else "recon2", t_recon
+        units = cells
+    clocks = clk.summary()
+    f_mhz = clocks["sm_max_mhz"] or SM_MAX_MHZ_NOMINAL
+    peak_tflops = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * f_mhz * 1e6 / 1e12
+    fpu = FLOPS_PER_UNIT.get(kname)
+    achieved = (fpu * units / (t_k / 1e3) / 1e12) if fpu else None
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_tflops,
+                "unit": "TFLOP/s (FP64)", "frac": (achieved / peak_tflops) if achieved else None,
+                "traffic": None, "ms_per_launch": t_k,
+                "peak_note": "FP64 ALU peak from unit counts: 152 SMs x 4 FP64 flop/clk x sm_max clock",
+                "other_kernel_ms": {"recon": t_recon, "flux": t_flux}}
+
+    # end to end through the C-ABI with host buffers: pinned H2D of the
+    # state, one step, D2H of the state, every step
+    Qp = torch.from_numpy(Qh).pin_memory()
+    Gp = torch.from_numpy(Gh).pin_memory() if cg else None
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        Q.copy_(Qp, non_blocking=True)
+        if cg:
+            G.copy_(Gp, non_blocking=True)
+        solver.step(Q, G, nsteps=1, sync=False)
+        Qp.copy_(Q, non_blocking=True)
+        if cg:
+            Gp.copy_(G, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    state_bytes = Qh.nbytes + (Gh.nbytes if cg else 0)
+    e2e = {"value": world * cells * stages / (e2e_ms / 1e3), "unit": "cell-stage/s",
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+           "ms_per_step": e2e_ms}
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        other = "gks2" if cg else "cgks5"
+        s2 = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=other, nonlinear=True), stream)
+        Q2 = torch.tensor(Qh, device=dev)
+        G2 = torch.tensor(Gh, device=dev) if other == "cgks5" else None
+        for _ in range(2):
+            s2.step(Q2, G2, nsteps=1, sync=False)
+        ms2 = time_steps(torch, s2, Q2, G2, max(2, args.steps), stream)
+        st2 = 2 if other == "cgks5" else 1
+        variants[f"{other}_fp64_{n}^3"] = {"value": cells * st2 * max(2, args.steps) / (ms2 / 1e3),
+                                           "ms_per_step": ms2 / max(2, args.steps)}
+        s2.close()
+        del Q2, G2
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-stage/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Taylor-Green cell averages)",
+        "config": {"workload": f"taylor_green_{n}^3_{scheme}_fp64_nonlinear", "cells": cells,
+                   "scheme": scheme, "stages_per_step": stages, "Ma": 0.1, "Re": 1600,
+                   "gamma": 1.4, "Pr": 0.72, "cfl": 0.3, "parallelism": f"replicas{world}",
+                   "l2": "working set larger than L2 (state + face buffers > 129 MB)"},
+        "roofline": roofline, "e2e": e2e,
+        "gpu_launches": LAUNCHES_PER_STEP[scheme] * args.steps, "clocks": clocks,
+        "variants": variants,
+    }
+    solver.close()
+    return line
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = reference_arm(args, rank)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(args.scheme)
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

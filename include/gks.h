@@ -1,0 +1,184 @@
+/*
+ * gks.h -- C-ABI of the GB300 (sm_103a) CGKS-5th / GKS-2nd hot path.
+ *
+ * The library advances the compressible Navier-Stokes equations on a
+ * periodic uniform Cartesian grid with the gas-kinetic schemes compared in
+ * Yang, Zhao & Xu, "Performance evaluation of high-order compact and
+ * second-order gas-kinetic schemes in compressible flow simulations":
+ * CGKS-5th (Sec. 3.2: compact fifth-order reconstruction with GENO weights,
+ * two-stage fourth-order time stepping, Sec. 3.4) and GKS-2nd (Sec. 3.3:
+ * least-squares linear reconstruction with the Venkatakrishnan limiter,
+ * second-order time stepping). The interface flux is the time-accurate
+ * gas-kinetic (BGK) flux of Sec. 2.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers to state arrays are DEVICE pointers (CUDA global memory on
+ *     the context's device), 8-byte aligned, owned by the caller.
+ *   - Q     : double[5][nz][ny][nx], x fastest; the cell averages of
+ *             (rho, rho U, rho V, rho W, rho E).
+ *   - gradQ : double[5][3][nz][ny][nx]; the cell-averaged gradient
+ *             (d/dx, d/dy, d/dz) of each conserved variable (CGKS-5th
+ *             only; pass NULL for GKS-2nd).
+ *   - Gas constant R = 1, temperature T = p/rho.
+ *   - All work is enqueued asynchronously on the CUDA stream given to
+ *     gks_init (NULL = the legacy default stream); no entry point
+ *     synchronises unless stated.
+ *   - Return codes: GKS_OK or a negative GKS_ERR_* value; nothing throws
+ *     across the ABI and no kernel traps the GPU. Arguments are checked on
+ *     the host before any launch. Device-side conditions (rho <= 0, p <= 0,
+ *     non-finite values) set a status word that the next synchronising
+ *     call returns as GKS_ERR_NONPHYSICAL.
+ */
+#ifndef GKS_H
+#define GKS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GKS_OK = 0,
+    GKS_ERR_ARG = -1,          /* invalid argument (checked before launch) */
+    GKS_ERR_CUDA = -2,         /* a CUDA runtime call failed                */
+    GKS_ERR_NONPHYSICAL = -3,  /* rho <= 0, p <= 0 or non-finite state seen */
+    GKS_ERR_TIMEOUT = -4,      /* a bounded device wait gave up             */
+    GKS_ERR_STATE = -5,        /* call out of order / wrong scheme          */
+    GKS_ERR_NOMEM = -6         /* device allocation failed                  */
+};
+
+enum { GKS_SCHEME_GKS2 = 0, GKS_SCHEME_CGKS5 = 1 };
+enum { GKS_PREC_FP64 = 0, GKS_PREC_MIXED = 1 };
+
+typedef struct gks_ctx gks_ctx; /* opaque; created by gks_init */
+
+typedef struct {
+    int scheme;      /* GKS_SCHEME_GKS2 or GKS_SCHEME_CGKS5                  */
+    int nonlinear;   /* 1: GENO (CGKS-5th) / Venkatakrishnan (GKS-2nd);
+                        0: the linear variants of Sec. 4 (chi = 1, phi = 1) */
+    int precision;   /* GKS_PREC_FP64 or GKS_PREC_MIXED                      */
+    int indicator;   /* 1: learned smoothness indicator (CGKS-5th, mixed)    */
+    int mu_law;      /* 0: constant mu; 1: Sutherland law of Sec. 4.2 with
+                        T normalised by T_ref                                */
+    int inviscid;    /* 1: tau = eps_tau dt + C_tau |dp/sp| dt (Sec. 4)      */
+    double C_tau;    /* Sec. 4 collision-time constant C (default 10)        */
+    double eps_tau;  /* Sec. 4 inviscid constant epsilon (default 0.05)      */
+    double T_ref;    /* Sutherland reference temperature (default 1)         */
+    double theta;    /* indicator threshold in (0, 1] (default 0.9)          */
+} gks_options;
+
+/* Fill *opt with the defaults: CGKS-5th, nonlinear, FP64, no indicator,
+ * constant mu, viscous tau, C_tau = 10, eps_tau = 0.05, T_ref = 1,
+ * theta = 0.9. */
+void gks_default_options(gks_options *opt);
+
+/* Create a context for one grid (Sec. 4 problem statement: gamma, Pr, mu,
+ * grid and CFL).
+ *   gamma > 1, Pr > 0, mu >= 0 (mu0 of the Sutherland law when mu_law = 1),
+ *   0 < cfl <= 1, nx, ny, nz >= 1, Lx, Ly, Lz > 0 (periodic box).
+ *   opt        : NULL for gks_default_options.
+ *   cuda_stream: a cudaStream_t (or NULL); the context enqueues all of its
+ *                work there.
+ * Allocates the library-owned device workspace (face states, face fluxes,
+ * stage buffers) on the current device; freed by gks_destroy.
+ * Returns GKS_ERR_ARG, GKS_ERR_NOMEM or GKS_ERR_CUDA on failure (then
+ * *out = NULL). */
+int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl,
+             int nx, int ny, int nz, double Lx, double Ly, double Lz,
+             const gks_options *opt, void *cuda_stream);
+
+void gks_destroy(gks_ctx *ctx);
+const char *gks_strerror(int code);
+
+/* Bytes of the face-state buffer written by gks_reconstruct:
+ * 6 faces x K Gauss points x 20 components x nx*ny*nz cells, K = 4
+ * (CGKS-5th) or 1 (GKS-2nd), 8 bytes each (FP64) or 4 (mixed). */
+size_t gks_face_state_bytes(const gks_ctx *ctx);
+/* Bytes of the face-flux records written by gks_flux: 3 x 30 x cells x 8. */
+size_t gks_face_flux_bytes(const gks_ctx *ctx);
+
+/* a0 -- time step of Sec. 4: dt = CFL min( min_{cells,d} h_d/(|U_d| + c),
+ * h_min^2/(3 nu_max) ) (the viscous bound only when the flow is viscous).
+ * Writes the FP64 scalar to *dt_dev (device pointer). Asynchronous. */
+int gks_compute_dt(gks_ctx *ctx, const double *Q, double *dt_dev);
+
+/* a1/a2 -- spatial reconstruction (Sec. 3.2 CGKS-5th: S^data-5th, the
+ * constrained least squares of Eq. compact-big-5, the sub-stencil
+ * polynomials of Eq. compact-sub-2 and the GENO combination of
+ * Eq. weno-new; Sec. 3.3 GKS-2nd: least squares + Venkatakrishnan).
+ * face_states (device, gks_face_state_bytes) receives, for every cell c,
+ * face f (0..5 = -x, +x, -y, +y, -z, +z), Gauss point k and component q,
+ * element ((f*K + k)*20 + q)*cells + c: the reconstructed state in the
+ * face frame (normal axis d = f/2, tangential axes (d+1)%3, (d+2)%3):
+ *   q 0..4   (rho, rho u_n, rho u_t1, rho u_t2, rho E)
+ *   q 5..9   d/dn of the same, q 10..14 d/dt1, q 15..19 d/dt2.
+ * Gauss point k sits at tangential offsets (+-g, +-g) h, g = 1/(2 sqrt 3),
+ * bit 0 of k choosing the sign along t1 and bit 1 along t2 (K = 1: the face
+ * midpoint). face_states = NULL uses the context's own buffer. */
+int gks_reconstruct(gks_ctx *ctx, const double *Q, const double *gradQ,
+                    void *face_states);
+
+/* a3 -- gas-kinetic flux of Sec. 2 (Eq. flux, its time integrals over
+ * [0, dt] and [0, dt/2], F^n and F_t^n of Eq. deri-t-f, the collision time
+ * of Sec. 4, the Prandtl correction of the energy flux, and the interface
+ * values of the update model of Sec. 3.4), averaged over each face's Gauss
+ * points. face_states: as written by gks_reconstruct (NULL = the context's
+ * buffer); dt_dev: device FP64 scalar. face_flux (device,
+ * gks_face_flux_bytes; NULL = the context's buffer) receives for axis d and
+ * the face on the low-d side of cell c, element (d*30 + q)*cells + c:
+ *   F^n(5), F_t^n(5), Q^l(5), dQ^l/dt(5), Q^r(5), dQ^r/dt(5)
+ * in the global frame (the interface values only for CGKS-5th; GKS-2nd
+ * leaves q 10..29 untouched). */
+int gks_flux(gks_ctx *ctx, const void *face_states, const double *dt_dev,
+             double *face_flux);
+
+/* The same flux at n independent Gauss points (unit-testing entry):
+ * s_l, s_r device double[20][n] face-frame states (layout of one Gauss point
+ * of gks_reconstruct), out device double[30][n] in the face frame. */
+int gks_flux_points(gks_ctx *ctx, const double *s_l, const double *s_r,
+                    int n, const double *dt_dev, double *out);
+
+/* a0-a4 -- advance nsteps time steps (or until *t_dev reaches t_stop):
+ * per step dt (a0) on the device, then for GKS-2nd one stage
+ * Q += dt L + dt^2/2 dL/dt, for CGKS-5th the two-stage fourth-order update
+ * of Q and of gradQ through the interface values (Sec. 3.4).
+ * t_dev: device FP64 scalar, advanced in place (NULL: no time tracking and
+ * t_stop is ignored). dt_host_last: if non-NULL
+ * the call synchronises the stream, stores the last dt there and returns
+ * GKS_ERR_NONPHYSICAL if the status word was set; if NULL the call is fully
+ * asynchronous. Q and gradQ are updated in place. */
+int gks_step(gks_ctx *ctx, double *Q, double *gradQ, int nsteps,
+             double t_stop, double *t_dev, double *dt_host_last);
+
+/* a5 -- diagnostics (Sec. 4.1/4.2), synchronising; out (host, 12 doubles):
+ *  [0] E_k  = (1/|Omega|) sum rho |U|^2/2 h^3 (divide by rho0 U0^2 for the
+ *            paper's normalisation)
+ *  [1] eps_S = (1/|Omega|) sum mu |curl U|^2 h^3
+ *  [2] eps_D = (4/3)(1/|Omega|) sum mu (div U)^2 h^3
+ *  [3] min rho, [4] min p, [5..9] sum Q h^3, [10] count of non-physical
+ *  cells, [11] max_d(|U_d| + c).
+ * Velocity gradients from gradQ (CGKS-5th) or central differences of the
+ * cell averages (gradQ = NULL). Returns GKS_ERR_NONPHYSICAL if the status
+ * word was set. */
+int gks_diagnostics(gks_ctx *ctx, const double *Q, const double *gradQ,
+                    double *out);
+
+/* Read and clear the device status word (synchronising): 0 or a bit mask
+ * (1: non-physical state, 2: non-finite value). */
+int gks_status(gks_ctx *ctx, int *status);
+
+/* Host-only, no GPU needed: the CGKS-5th reconstruction matrix R (34 x 63,
+ * row major) with a = R d, the least-squares solution of Eq. compact-big-5
+ * for the normalised data vector d of S^data-5th (column order: the 6
+ * face-neighbour differences, the 12 edge-neighbour differences, the 18
+ * scaled face-neighbour gradients, the 24 scaled edge-neighbour tangential
+ * derivatives, the 3 scaled own gradients) and a over the 34 monomials
+ * x^a y^b z^c/(a! b! c!) minus their cell mean, ordered by degree. R is
+ * caller-owned host memory of 34*63 doubles. */
+int gks_recon_matrix(double *R);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,284 @@
+// C-ABI of the CGKS-5th / GKS-2nd hot path (declared in include/gks.h).
+// Owns the device workspace of one grid and enqueues the kernels of
+// recon.cu, flux.cu and update.cu on the caller's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "basis.h"
+#include "common.cuh"
+#include "../../include/gks.h"
+
+using namespace gks;
+
+struct gks_ctx {
+    int device;
+    cudaStream_t stream;
+    GridDesc g;
+    PhysParams P;
+    gks_options opt;
+    int K;                 // Gauss points per face
+    double *fs;            // face states [6][K][20][n]
+    double *frec;          // face records [3][30][n]
+    double *Qs, *Gs, *Acc, *S1;  // CGKS-5th stage buffers
+    double *scal;          // [0] dt, [1..2] dt reduction words, [3] diagnostics out (12)
+    int *status;
+    double *partials;
+    int diag_blocks;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return GKS_ERR_NOMEM;
+    return GKS_ERR_CUDA;
+}
+
+template <typename T>
+int dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return GKS_OK;
+    const cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return cuda_fail(e);
+    }
+    return GKS_OK;
+}
+
+double *dt_slot(gks_ctx *c) { return c->scal; }
+double *red_slot(gks_ctx *c) { return c->scal + 1; }
+double *diag_slot(gks_ctx *c) { return c->scal + 3; }
+
+int launch_ok(int rc) { return rc == 0 ? GKS_OK : (rc == -1 ? GKS_ERR_ARG : GKS_ERR_CUDA); }
+
+}  // namespace
+
+extern "C" {
+
+void gks_default_options(gks_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->scheme = GKS_SCHEME_CGKS5;
+    opt->nonlinear = 1;
+    opt->precision = GKS_PREC_FP64;
+    opt->indicator = 0;
+    opt->mu_law = 0;
+    opt->inviscid = 0;
+    opt->C_tau = 10.0;
+    opt->eps_tau = 0.05;
+    opt->T_ref = 1.0;
+    opt->theta = 0.9;
+}
+
+const char *gks_strerror(int code) {
+    switch (code) {
+        case GKS_OK: return "ok";
+        case GKS_ERR_ARG: return "invalid argument";
+        case GKS_ERR_CUDA: return "CUDA runtime error";
+        case GKS_ERR_NONPHYSICAL: return "non-physical or non-finite state";
+        case GKS_ERR_TIMEOUT: return "device wait timed out";
+        case GKS_ERR_STATE: return "call out of order or wrong scheme";
+        case GKS_ERR_NOMEM: return "device allocation failed";
+        default: return "unknown error";
+    }
+}
+
+void gks_destroy(gks_ctx *c) {
+    if (!c) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->fs);
+    cudaFree(c->frec);
+    cudaFree(c->Qs);
+    cudaFree(c->Gs);
+    cudaFree(c->Acc);
+    cudaFree(c->S1);
+    cudaFree(c->scal);
+    cudaFree(c->status);
+    cudaFree(c->partials);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete c;
+}
+
+int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int nx, int ny,
+             int nz, double Lx, double Ly, double Lz, const gks_options *opt,
+             void *cuda_stream) {
+    if (!out) return GKS_ERR_ARG;
+    *out = nullptr;
+    gks_options o;
+    if (opt) o = *opt; else gks_default_options(&o);
+    if (!(gamma > 1.0) || !(Pr > 0.0) || !(mu >= 0.0) || !(cfl > 0.0 && cfl <= 1.0)) return GKS_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || !(Lx > 0.0) || !(Ly > 0.0) || !(Lz > 0.0)) return GKS_ERR_ARG;
+    if (o.scheme != GKS_SCHEME_GKS2 && o.scheme != GKS_SCHEME_CGKS5) return GKS_ERR_ARG;
+    if (o.precision != GKS_PREC_FP64) return GKS_ERR_ARG;  // mixed path: not in this build
+    if (o.indicator) return GKS_ERR_ARG;
+    if (o.mu_law < 0 || o.mu_law > 1 || !(o.C_tau >= 0.0) || !(o.eps_tau >= 0.0) ||
+        !(o.T_ref > 0.0))
+        return GKS_ERR_ARG;
+    const long long n = (long long)nx * ny * nz;
+    if (n > (1LL << 31)) return GKS_ERR_ARG;
+
+    gks_ctx *c = new (std::nothrow) gks_ctx;
+    if (!c) return GKS_ERR_NOMEM;
+    std::memset(c, 0, sizeof(*c));
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return GKS_ERR_CUDA; }
+    c->stream = (cudaStream_t)cuda_stream;
+    c->opt = o;
+    c->g.nx = nx; c->g.ny = ny; c->g.nz = nz; c->g.n = n;
+    c->g.h[0] = Lx / nx; c->g.h[1] = Ly / ny; c->g.h[2] = Lz / nz;
+    c->P.gamma = gamma; c->P.Pr = Pr; c->P.mu0 = mu; c->P.cfl = cfl;
+    c->P.C_tau = o.C_tau; c->P.eps_tau = o.eps_tau; c->P.T_ref = o.T_ref;
+    c->P.Nint = (5.0 - 3.0 * gamma) / (gamma - 1.0);
+    c->P.mu_law = o.mu_law; c->P.inviscid = o.inviscid; c->P.nonlinear = o.nonlinear ? 1 : 0;
+    c->P.scheme = o.scheme;
+    c->K = o.scheme == GKS_SCHEME_CGKS5 ? 4 : 1;
+
+    int rc = GKS_OK;
+    if (o.scheme == GKS_SCHEME_CGKS5) {
+        const int t = upload_recon_tables();
+        if (t) { gks_destroy(c); return t == -1 ? GKS_ERR_ARG : GKS_ERR_CUDA; }
+    }
+    c->diag_blocks = diagnostics_blocks(c->g);
+    if ((rc = dalloc(&c->fs, (size_t)6 * c->K * 20 * n)) ||
+        (rc = dalloc(&c->frec, (size_t)90 * n)) ||
+        (rc = dalloc(&c->scal, (size_t)3 + 12)) ||
+        (rc = dalloc(&c->status, 1)) ||
+        (rc = dalloc(&c->partials, (size_t)12 * c->diag_blocks))) {
+        gks_destroy(c);
+        return rc;
+    }
+    if (o.scheme == GKS_SCHEME_CGKS5) {
+        if ((rc = dalloc(&c->Qs, (size_t)5 * n)) || (rc = dalloc(&c->Gs, (size_t)15 * n)) ||
+            (rc = dalloc(&c->Acc, (size_t)5 * n)) || (rc = dalloc(&c->S1, (size_t)15 * n))) {
+            gks_destroy(c);
+            return rc;
+        }
+    }
+    if (cudaMemsetAsync(c->scal, 0, sizeof(double) * 15, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->status, 0, sizeof(int), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->frec, 0, sizeof(double) * 90 * n, c->stream) != cudaSuccess) {
+        gks_destroy(c);
+        return GKS_ERR_CUDA;
+    }
+    *out = c;
+    return GKS_OK;
+}
+
+size_t gks_face_state_bytes(const gks_ctx *c) {
+    return c ? (size_t)6 * c->K * 20 * c->g.n * sizeof(double) : 0;
+}
+
+size_t gks_face_flux_bytes(const gks_ctx *c) {
+    return c ? (size_t)90 * c->g.n * sizeof(double) : 0;
+}
+
+int gks_compute_dt(gks_ctx *c, const double *Q, double *dt_dev) {
+    if (!c || !Q || !dt_dev) return GKS_ERR_ARG;
+    return launch_ok(launch_dt(c->g, c->P, Q, red_slot(c), dt_dev, nullptr, 0.0, c->stream));
+}
+
+int gks_reconstruct(gks_ctx *c, const double *Q, const double *G, void *face_states) {
+    if (!c || !Q) return GKS_ERR_ARG;
+    double *fs = face_states ? (double *)face_states : c->fs;
+    if (c->P.scheme == GKS_SCHEME_CGKS5) {
+        if (!G) return GKS_ERR_ARG;
+        return launch_ok(launch_recon5(c->g, c->P, Q, G, fs, c->stream));
+    }
+    return launch_ok(launch_recon2(c->g, c->P, Q, fs, c->stream));
+}
+
+int gks_flux(gks_ctx *c, const void *face_states, const double *dt_dev, double *face_flux) {
+    if (!c || !dt_dev) return GKS_ERR_ARG;
+    const double *fs = face_states ? (const double *)face_states : c->fs;
+    double *fr = face_flux ? face_flux : c->frec;
+    return launch_ok(launch_flux_faces(c->g, c->P, fs, dt_dev, fr, c->status, c->stream));
+}
+
+int gks_flux_points(gks_ctx *c, const double *s_l, const double *s_r, int n,
+                    const double *dt_dev, double *out) {
+    if (!c || !s_l || !s_r || !dt_dev || !out || n < 0) return GKS_ERR_ARG;
+    if (n == 0) return GKS_OK;
+    return launch_ok(launch_flux_points(c->P, s_l, s_r, n, dt_dev, out, c->status, c->stream));
+}
+
+int gks_step(gks_ctx *c, double *Q, double *G, int nsteps, double t_stop, double *t_dev,
+             double *dt_host_last) {
+    if (!c || !Q || nsteps < 0) return GKS_ERR_ARG;
+    const bool cgks = c->P.scheme == GKS_SCHEME_CGKS5;
+    if (cgks && !G) return GKS_ERR_ARG;
+    double *dt = dt_slot(c);
+    for (int s = 0; s < nsteps; ++s) {
+        int rc = launch_dt(c->g, c->P, Q, red_slot(c), dt, t_dev, t_stop, c->stream);
+        if (rc) return GKS_ERR_CUDA;
+        if (!cgks) {
+            if ((rc = launch_recon2(c->g, c->P, Q, c->fs, c->stream)) ||
+                (rc = launch_flux_faces(c->g, c->P, c->fs, dt, c->frec, c->status, c->stream)) ||
+                (rc = launch_update(c->g, c->P, 0, c->frec, dt, Q, nullptr, nullptr, nullptr,
+                                    nullptr, nullptr, c->status, c->stream)))
+                return GKS_ERR_CUDA;
+        } else {
+            if ((rc = launch_recon5(c->g, c->P, Q, G, c->fs, c->stream)) ||
+                (rc = launch_flux_faces(c->g, c->P, c->fs, dt, c->frec, c->status, c->stream)) ||
+                (rc = launch_update(c->g, c->P, 1, c->frec, dt, Q, G, c->Qs, c->Gs, c->Acc, c->S1,
+                                    c->status, c->stream)) ||
+                (rc = launch_recon5(c->g, c->P, c->Qs, c->Gs, c->fs, c->stream)) ||
+                (rc = launch_flux_faces(c->g, c->P, c->fs, dt, c->frec, c->status, c->stream)) ||
+                (rc = launch_update(c->g, c->P, 2, c->frec, dt, Q, G, c->Qs, c->Gs, c->Acc, c->S1,
+                                    c->status, c->stream)))
+                return GKS_ERR_CUDA;
+        }
+    }
+    if (dt_host_last) {
+        int st = 0;
+        if (cudaMemcpyAsync(dt_host_last, dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return GKS_ERR_CUDA;
+        if (st) return GKS_ERR_NONPHYSICAL;
+    }
+    return GKS_OK;
+}
+
+int gks_diagnostics(gks_ctx *c, const double *Q, const double *G, double *out) {
+    if (!c || !Q || !out) return GKS_ERR_ARG;
+    double *od = diag_slot(c);
+    if (launch_diagnostics(c->g, c->P, Q, G, c->partials, c->diag_blocks, od, c->stream))
+        return GKS_ERR_CUDA;
+    int st = 0;
+    if (cudaMemcpyAsync(out, od, 12 * sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return GKS_ERR_CUDA;
+    return st ? GKS_ERR_NONPHYSICAL : GKS_OK;
+}
+
+int gks_recon_matrix(double *R) {
+    if (!R) return GKS_ERR_ARG;
+    ReconTables *t = new (std::nothrow) ReconTables;
+    if (!t) return GKS_ERR_NOMEM;
+    const int rc = build_recon_tables(t);
+    if (rc == 0) std::memcpy(R, t->R, sizeof(t->R));
+    delete t;
+    return rc == 0 ? GKS_OK : GKS_ERR_ARG;
+}
+
+int gks_status(gks_ctx *c, int *status) {
+    if (!c || !status) return GKS_ERR_ARG;
+    if (cudaMemcpyAsync(status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(c->status, 0, sizeof(int), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return GKS_ERR_CUDA;
+    return GKS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+// Host-side construction of the CGKS-5th reconstruction tables (Sec. 3.2).
+//
+// Eq. compact-big-5 asks for the quartic P4 = Q0 + sum_d a_d p_d that
+// matches the 18 neighbour averages exactly and the 45 derivative data in
+// the least-squares sense (unit weights in normalised coordinates, i.e.
+// h1 = h2 = h3 = h). It is solved here by the null-space method:
+//   C = [R_c^T 0] [Q1 Q2]^T   (Householder QR of C^T),
+//   a = Q1 y + Q2 z,  R_c^T y = d_C,
+//   z = argmin |B Q2 z - (d_B - B Q1 y)|   (Householder QR of B Q2).
+// Applying this to the unit data vectors gives the 34 x 63 matrix R.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "basis.h"
+
+namespace gks {
+namespace {
+
+double factorial(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+// average of x^n over [o - 1/2, o + 1/2]
+double avg1(int o, int n) {
+    return (std::pow(o + 0.5, n + 1) - std::pow(o - 0.5, n + 1)) / (n + 1);
+}
+
+// average over the unit cell at offset o of x^e / e!
+double cell_avg(const int o[3], const int e[3]) {
+    double v = 1.0;
+    for (int j = 0; j < 3; ++j) {
+        if (e[j] < 0) return 0.0;
+        v *= avg1(o[j], e[j]) / factorial(e[j]);
+    }
+    return v;
+}
+
+// average over offset o of d p_i / d x_q
+double cell_avg_deriv(const int o[3], int i, int q) {
+    int e[3] = {kExp[i][0], kExp[i][1], kExp[i][2]};
+    if (e[q] == 0) return 0.0;
+    e[q] -= 1;
+    return cell_avg(o, e);
+}
+
+// Dense column-major helpers ------------------------------------------------
+struct Mat {
+    int r, c;
+    std::vector<double> a;
+    Mat(int rr, int cc) : r(rr), c(cc), a((size_t)rr * cc, 0.0) {}
+    double &operator()(int i, int j) { return a[(size_t)j * r + i]; }
+    double operator()(int i, int j) const { return a[(size_t)j * r + i]; }
+};
+
+// Householder QR: A (m x n, m >= n) -> explicit orthogonal Q (m x m) and the
+// upper-triangular n x n factor Rt.
+void householder_qr(const Mat &A, Mat &Q, Mat &Rt) {
+    const int m = A.r, n = A.c;
+    Mat W = A;
+    Q = Mat(m, m);
+    for (int i = 0; i < m; ++i) Q(i, i) = 1.0;
+    std::vector<double> v(m);
+    for (int k = 0; k < n; ++k) {
+        double norm = 0.0;
+        for (int i = k; i < m; ++i) norm += W(i, k) * W(i, k);
+        norm = std::sqrt(norm);
+        if (norm == 0.0) continue;
+        const double alpha = W(k, k) > 0 ? -norm : norm;
+        for (int i = 0; i < m; ++i) v[i] = (i < k) ? 0.0 : W(i, k);
+        v[k] -= alpha;
+        double vn = 0.0;
+        for (int i = k; i < m; ++i) vn += v[i] * v[i];
+        if (vn == 0.0) continue;
+        // W <- (I - 2 v v^T / vn) W ; Q <- Q (I - 2 v v^T / vn)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int i = k; i < m; ++i) s += v[i] * W(i, j);
+            s = 2.0 * s / vn;
+            for (int i = k; i < m; ++i) W(i, j) -= s * v[i];
+        }
+        for (int i = 0; i < m; ++i) {
+            double s = 0.0;
+            for (int l = k; l < m; ++l) s += Q(i, l) * v[l];
+            s = 2.0 * s / vn;
+            for (int l = k; l < m; ++l) Q(i, l) -= s * v[l];
+        }
+    }
+    Rt = Mat(n, n);
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) Rt(i, j) = W(i, j);
+}
+
+}  // namespace
+
+int build_recon_tables(ReconTables *t) {
+    std::memset(t, 0, sizeof(*t));
+    constexpr int nb = kNumBasis, ne = 18, nl = 45;
+    static const int zero[3] = {0, 0, 0};
+    // constraint rows: neighbour cell averages of p_i (zero mean on Omega_0)
+    Mat C(ne, nb);
+    for (int k = 0; k < ne; ++k) {
+        const int *o = (k < 6) ? kFaceOff[k] : kEdgeOff[k - 6];
+        for (int i = 0; i < nb; ++i) {
+            const int e[3] = {kExp[i][0], kExp[i][1], kExp[i][2]};
+            C(k, i) = cell_avg(o, e) - cell_avg(zero, e);
+        }
+    }
+    // least-squares rows in the order of the data columns 18..62
+    Mat B(nl, nb);
+    int r = 0;
+    for (int m = 0; m < 6; ++m)
+        for (int q = 0; q < 3; ++q, ++r)
+            for (int i = 0; i < nb; ++i) B(r, i) = cell_avg_deriv(kFaceOff[m], i, q);
+    const double rs2 = 1.0 / std::sqrt(2.0);
+    for (int n = 0; n < 12; ++n) {
+        const int *o = kEdgeOff[n];
+        const int a = edge_axis_a(n), b = edge_axis_b(n), e = edge_axis_e(n);
+        for (int i = 0; i < nb; ++i)
+            B(r, i) = rs2 * (o[a] * cell_avg_deriv(o, i, a) - o[b] * cell_avg_deriv(o, i, b));
+        ++r;
+        for (int i = 0; i < nb; ++i) B(r, i) = cell_avg_deriv(o, i, e);
+        ++r;
+    }
+    for (int q = 0; q < 3; ++q, ++r)
+        for (int i = 0; i < nb; ++i) B(r, i) = cell_avg_deriv(zero, i, q);
+
+    // null-space method
+    Mat Ct(nb, ne);
+    for (int k = 0; k < ne; ++k)
+        for (int i = 0; i < nb; ++i) Ct(i, k) = C(k, i);
+    Mat Qc(1, 1), Rc(1, 1);
+    householder_qr(Ct, Qc, Rc);
+    const int nz = nb - ne;  // 16
+    Mat BQ2(nl, nz), BQ1(nl, ne);
+    for (int i = 0; i < nl; ++i) {
+        for (int j = 0; j < nz; ++j) {
+            double s = 0.0;
+            for (int l = 0; l < nb; ++l) s += B(i, l) * Qc(l, ne + j);
+            BQ2(i, j) = s;
+        }
+        for (int j = 0; j < ne; ++j) {
+            double s = 0.0;
+            for (int l = 0; l < nb; ++l) s += B(i, l) * Qc(l, j);
+            BQ1(i, j) = s;
+        }
+    }
+    Mat Qm(1, 1), Rm(1, 1);
+    householder_qr(BQ2, Qm, Rm);
+    for (int i = 0; i < ne; ++i)
+        if (std::fabs(Rc(i, i)) < 1e-12) return -1;
+    for (int i = 0; i < nz; ++i)
+        if (std::fabs(Rm(i, i)) < 1e-12) return -1;
+
+    std::vector<double> dC(ne), dB(nl), y(ne), res(nl), z(nz), rhs(nz);
+    for (int col = 0; col < kNumData; ++col) {
+        for (int k = 0; k < ne; ++k) dC[k] = (col == k) ? 1.0 : 0.0;
+        for (int k = 0; k < nl; ++k) dB[k] = (col == ne + k) ? 1.0 : 0.0;
+        // R_c^T y = d_C (forward substitution)
+        for (int i = 0; i < ne; ++i) {
+            double s = dC[i];
+            for (int j = 0; j < i; ++j) s -= Rc(j, i) * y[j];
+            y[i] = s / Rc(i, i);
+        }
+        for (int i = 0; i < nl; ++i) {
+            double s = dB[i];
+            for (int j = 0; j < ne; ++j) s -= BQ1(i, j) * y[j];
+            res[i] = s;
+        }
+        // z = Rm^{-1} (Qm^T res)[0..nz)
+        for (int j = 0; j < nz; ++j) {
+            double s = 0.0;
+            for (int i = 0; i < nl; ++i) s += Qm(i, j) * res[i];
+            rhs[j] = s;
+        }
+        for (int j = nz - 1; j >= 0; --j) {
+            double s = rhs[j];
+            for (int l = j + 1; l < nz; ++l) s -= Rm(j, l) * z[l];
+            z[j] = s / Rm(j, j);
+        }
+        for (int i = 0; i < nb; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < ne; ++j) s += Qc(i, j) * y[j];
+            for (int j = 0; j < nz; ++j) s += Qc(i, ne + j) * z[j];
+            t->R[i][col] = s;
+        }
+    }
+
+    // smoothness form and means on the unit cell [-1/2, 1/2]^3
+    auto mono_int = [](int n) { return (n % 2) ? 0.0 : std::pow(0.5, n) / (n + 1); };
+    for (int i = 0; i < nb; ++i) {
+        t->mean[i] = 1.0;
+        for (int j = 0; j < 3; ++j) t->mean[i] *= mono_int(kExp[i][j]) / factorial(kExp[i][j]);
+    }
+    for (int i = 0; i < nb; ++i)
+        for (int k = 0; k < nb; ++k) {
+            double s = 0.0;
+            for (int a0 = 0; a0 <= 4; ++a0)
+                for (int a1 = 0; a0 + a1 <= 4; ++a1)
+                    for (int a2 = 0; a0 + a1 + a2 <= 4; ++a2) {
+                        if (a0 + a1 + a2 == 0) continue;
+                        const int al[3] = {a0, a1, a2};
+                        double v = 1.0;
+                        for (int j = 0; j < 3 && v != 0.0; ++j) {
+                            const int ei = kExp[i][j] - al[j], ek = kExp[k][j] - al[j];
+                            if (ei < 0 || ek < 0) { v = 0.0; break; }
+                            v *= mono_int(ei + ek) / (factorial(ei) * factorial(ek));
+                        }
+                        s += v;
+                    }
+            t->H[i][k] = s;
+        }
+
+    // magnitudes of x^e/e! and of its derivatives at the Gauss points of the
+    // faces normal to axis d: |x_d| = 1/2, the two tangential |x| = g
+    const double g = 0.5 / std::sqrt(3.0);
+    for (int d = 0; d < 3; ++d) {
+        double ax[3] = {g, g, g};
+        ax[d] = 0.5;
+        for (int i = 0; i < nb; ++i) {
+            double v = 1.0;
+            for (int j = 0; j < 3; ++j) v *= std::pow(ax[j], kExp[i][j]) / factorial(kExp[i][j]);
+            t->mval[d][i] = v;
+            for (int q = 0; q < 3; ++q) {
+                if (kExp[i][q] == 0) { t->mder[d][q][i] = 0.0; continue; }
+                double w = 1.0;
+                for (int j = 0; j < 3; ++j) {
+                    const int e = kExp[i][j] - (j == q ? 1 : 0);
+                    w *= std::pow(ax[j], e) / factorial(e);
+                }
+                t->mder[d][q][i] = w;
+            }
+        }
+    }
+    return 0;
+}
+
+}  // namespace gks

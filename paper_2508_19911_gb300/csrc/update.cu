@@ -1,0 +1,328 @@
+// Time step, cell update and diagnostics kernels.
+//
+//   dt (Sec. 4): dt = CFL min(min_{cells,d} h_d/(|U_d| + c), h_min^2/(3 nu_max));
+//     warp-shuffle and block reductions of max (|U_d| + c)/h_d and max nu,
+//     combined across blocks with atomicMax on the bit patterns of the
+//     (non-negative) doubles, then one thread forms dt, clamps it to the
+//     remaining time and advances t on the device.
+//   update (Sec. 2 Eq. semi, Sec. 3.1, Sec. 3.4): L = -sum_d (F_d(i+1/2) -
+//     F_d(i-1/2))/h_d from the face-averaged fluxes, the same for dL/dt;
+//     GKS-2nd: Q += dt L + dt^2/2 dL/dt. CGKS-5th: stage 1 writes
+//     Q* = Q + dt/2 L + dt^2/8 dL/dt, grad Q* from the interface values
+//     (Gauss's theorem, Sec. 3.1) advanced by dt/2, and keeps
+//     A = Q + dt L + dt^2/6 dL/dt and S1 = Gauss sum of Q_G^n; stage 2 writes
+//     Q^{n+1} = A + dt^2/3 dL*/dt and grad Q^{n+1} = S1 + dt Gauss sum of
+//     dQ_G*/dt.
+//   diagnostics (Sec. 4.1/4.2): per-block partial sums/minima/maxima in a
+//     fixed order, then one block reduces the partials in a fixed order
+//     (deterministic, no floating-point atomics).
+#include <cmath>
+
+#include "common.cuh"
+
+namespace gks {
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void __launch_bounds__(kBlock) dt_reduce_kernel(GridDesc g, PhysParams P,
+                                                           const double *__restrict__ Q,
+                                                           unsigned long long *red) {
+    const long long n = g.n;
+    double rate = 0.0, numax = 0.0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const double rho = Q[c];
+        const double ir = 1.0 / rho;
+        const double U = Q[n + c] * ir, V = Q[2 * n + c] * ir, W = Q[3 * n + c] * ir;
+        const double p = (P.gamma - 1.0) * (Q[4 * n + c] - 0.5 * rho * (U * U + V * V + W * W));
+        const double cs = sqrt(P.gamma * p * ir);
+        rate = fmax(rate, (fabs(U) + cs) / g.h[0]);
+        rate = fmax(rate, (fabs(V) + cs) / g.h[1]);
+        rate = fmax(rate, (fabs(W) + cs) / g.h[2]);
+        numax = fmax(numax, viscosity(P, rho, p) * ir);
+    }
+    rate = warp_max(rate);
+    numax = warp_max(numax);
+    __shared__ double sr[kBlock / 32], sn[kBlock / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sr[wid] = rate; sn[wid] = numax; }
+    __syncthreads();
+    if (wid == 0) {
+        rate = lane < kBlock / 32 ? sr[lane] : 0.0;
+        numax = lane < kBlock / 32 ? sn[lane] : 0.0;
+        rate = warp_max(rate);
+        numax = warp_max(numax);
+        if (lane == 0) {
+            // non-negative doubles order like their bit patterns
+            atomicMax(red, (unsigned long long)__double_as_longlong(rate));
+            atomicMax(red + 1, (unsigned long long)__double_as_longlong(numax));
+        }
+    }
+}
+
+__global__ void dt_finalize_kernel(GridDesc g, PhysParams P, unsigned long long *red,
+                                   double *dt_dev, double *t_dev, double t_stop) {
+    const double rate = __longlong_as_double((long long)red[0]);
+    const double numax = __longlong_as_double((long long)red[1]);
+    double dt = P.cfl / rate;
+    if (!P.inviscid && numax > 0.0) {
+        const double hmin = fmin(g.h[0], fmin(g.h[1], g.h[2]));
+        dt = fmin(dt, P.cfl * hmin * hmin / (3.0 * numax));
+    }
+    if (t_dev) {
+        const double rem = t_stop - *t_dev;
+        if (dt > rem) dt = rem;
+        if (!(dt > 0.0)) dt = 0.0;
+        *t_dev += dt;
+    }
+    if (!(dt > 0.0) || !isfinite(dt)) dt = 0.0;
+    *dt_dev = dt;
+    red[0] = 0ull;
+    red[1] = 0ull;
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(kBlock) update_kernel(GridDesc g, PhysParams P,
+                                                        const double *__restrict__ fr,
+                                                        const double *__restrict__ dt_dev,
+                                                        double *__restrict__ Q, double *__restrict__ G,
+                                                        double *__restrict__ Qs, double *__restrict__ Gs,
+                                                        double *__restrict__ Acc,
+                                                        double *__restrict__ S1, int *status) {
+    const double dt = *dt_dev;
+    if (!(dt > 0.0)) return;
+    const long long n = g.n;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int i = (int)(c % g.nx);
+    const int j = (int)((c / g.nx) % g.ny);
+    const int k = (int)(c / ((long long)g.nx * g.ny));
+    const long long hi[3] = {cell_index(g, wrap(i + 1, g.nx), j, k),
+                             cell_index(g, i, wrap(j + 1, g.ny), k),
+                             cell_index(g, i, j, wrap(k + 1, g.nz))};
+    const double dt2 = dt * dt;
+    double out[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        double L = 0.0, Lt = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double *F = fr + (long long)d * 30 * n;
+            L += (F[(long long)v * n + hi[d]] - F[(long long)v * n + c]) / g.h[d];
+            Lt += (F[(long long)(5 + v) * n + hi[d]] - F[(long long)(5 + v) * n + c]) / g.h[d];
+        }
+        L = -L;
+        Lt = -Lt;
+        const long long qi = (long long)v * n + c;
+        if (STAGE == 0) {
+            out[v] = Q[qi] + dt * L + 0.5 * dt2 * Lt;
+            Q[qi] = out[v];
+        } else if (STAGE == 1) {
+            const double q = Q[qi];
+            out[v] = q + 0.5 * dt * L + 0.125 * dt2 * Lt;
+            Qs[qi] = out[v];
+            Acc[qi] = q + dt * L + dt2 / 6.0 * Lt;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double *F = fr + (long long)d * 30 * n;
+                const double ql = F[(long long)(10 + v) * n + hi[d]];
+                const double qlt = F[(long long)(15 + v) * n + hi[d]];
+                const double qr = F[(long long)(20 + v) * n + c];
+                const double qrt = F[(long long)(25 + v) * n + c];
+                const long long gi = ((long long)v * 3 + d) * n + c;
+                Gs[gi] = ((ql + 0.5 * dt * qlt) - (qr + 0.5 * dt * qrt)) / g.h[d];
+                S1[gi] = (ql - qr) / g.h[d];
+            }
+        } else {
+            out[v] = Acc[qi] + dt2 / 3.0 * Lt;
+            Q[qi] = out[v];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double *F = fr + (long long)d * 30 * n;
+                const double qlt = F[(long long)(15 + v) * n + hi[d]];
+                const double qrt = F[(long long)(25 + v) * n + c];
+                const long long gi = ((long long)v * 3 + d) * n + c;
+                G[gi] = S1[gi] + dt * (qlt - qrt) / g.h[d];
+            }
+        }
+    }
+    // status word: non-physical or non-finite new state
+    const double rho = out[0];
+    const double ke = 0.5 * (out[1] * out[1] + out[2] * out[2] + out[3] * out[3]) / rho;
+    const double p = (P.gamma - 1.0) * (out[4] - ke);
+    bool finite = true;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) finite = finite && isfinite(out[v]);
+    if (!finite) flag_status(status, kStatusNonfinite);
+    else if (!(rho > 0.0 && p > 0.0)) flag_status(status, kStatusNonphysical);
+}
+
+// ---- diagnostics ---------------------------------------------------------
+// slots: 0 ek, 1 eps_S, 2 eps_D, 3 min rho, 4 min p, 5..9 sum Q, 10 bad,
+// 11 max speed; 3, 4 are minima, 11 a maximum, the rest sums
+constexpr int kDiag = 12;
+
+__device__ __forceinline__ double combine(int s, double a, double b) {
+    if (s == 3 || s == 4) return fmin(a, b);
+    if (s == 11) return fmax(a, b);
+    return a + b;
+}
+
+__device__ __forceinline__ double identity_of(int s) {
+    if (s == 3 || s == 4) return INFINITY;
+    if (s == 11) return 0.0;
+    return 0.0;
+}
+
+__device__ void block_reduce_store(double acc[kDiag], double *dst) {
+    __shared__ double sh[kDiag][kBlock];
+#pragma unroll
+    for (int s = 0; s < kDiag; ++s) sh[s][threadIdx.x] = acc[s];
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+#pragma unroll
+            for (int s = 0; s < kDiag; ++s)
+                sh[s][threadIdx.x] = combine(s, sh[s][threadIdx.x], sh[s][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int s = 0; s < kDiag; ++s) dst[s] = sh[s][0];
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) diag_partial_kernel(GridDesc g, PhysParams P,
+                                                              const double *__restrict__ Q,
+                                                              const double *__restrict__ G,
+                                                              double *partials) {
+    const long long n = g.n;
+    const double vol = g.h[0] * g.h[1] * g.h[2];
+    double acc[kDiag];
+#pragma unroll
+    for (int s = 0; s < kDiag; ++s) acc[s] = identity_of(s);
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        double W[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            W[v] = Q[(long long)v * n + c];
+            acc[5 + v] += W[v] * vol;
+        }
+        const double rho = W[0];
+        const double vel[3] = {W[1] / rho, W[2] / rho, W[3] / rho};
+        const double p = (P.gamma - 1.0) *
+                         (W[4] - 0.5 * rho * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]));
+        bool ok = rho > 0.0 && p > 0.0;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ok = ok && isfinite(W[v]);
+        if (!ok) {
+            acc[10] += 1.0;
+            continue;
+        }
+        acc[3] = fmin(acc[3], rho);
+        acc[4] = fmin(acc[4], p);
+        const double cs = sqrt(P.gamma * p / rho);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc[11] = fmax(acc[11], fabs(vel[d]) + cs);
+        acc[0] += 0.5 * rho * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]) * vol;
+        const int i = (int)(c % g.nx);
+        const int j = (int)((c / g.nx) % g.ny);
+        const int k = (int)(c / ((long long)g.nx * g.ny));
+        double dQ[4][3];  // d(rho), d(rho U), d(rho V), d(rho W)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (G) {
+                    dQ[v][d] = G[((long long)v * 3 + d) * n + c];
+                } else {
+                    const long long hi = cell_index(g, d == 0 ? wrap(i + 1, g.nx) : i,
+                                                    d == 1 ? wrap(j + 1, g.ny) : j,
+                                                    d == 2 ? wrap(k + 1, g.nz) : k);
+                    const long long lo = cell_index(g, d == 0 ? wrap(i - 1, g.nx) : i,
+                                                    d == 1 ? wrap(j - 1, g.ny) : j,
+                                                    d == 2 ? wrap(k - 1, g.nz) : k);
+                    dQ[v][d] = (Q[(long long)v * n + hi] - Q[(long long)v * n + lo]) / (2.0 * g.h[d]);
+                }
+            }
+        double du[3][3];  // du[a][d] = dU_a/dx_d
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) du[a][d] = (dQ[1 + a][d] - vel[a] * dQ[0][d]) / rho;
+        const double wx = du[2][1] - du[1][2], wy = du[0][2] - du[2][0], wz = du[1][0] - du[0][1];
+        const double div = du[0][0] + du[1][1] + du[2][2];
+        const double mu = viscosity(P, rho, p);
+        acc[1] += mu * (wx * wx + wy * wy + wz * wz) * vol;
+        acc[2] += 4.0 / 3.0 * mu * div * div * vol;
+    }
+    block_reduce_store(acc, partials + (long long)blockIdx.x * kDiag);
+}
+
+__global__ void __launch_bounds__(kBlock) diag_final_kernel(const double *partials, int nblocks,
+                                                            double volume, double *out) {
+    double acc[kDiag];
+#pragma unroll
+    for (int s = 0; s < kDiag; ++s) acc[s] = identity_of(s);
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int s = 0; s < kDiag; ++s) acc[s] = combine(s, acc[s], partials[(long long)b * kDiag + s]);
+    __shared__ double res[kDiag];
+    block_reduce_store(acc, res);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kDiag; ++s) out[s] = res[s];
+        out[0] /= volume;
+        out[1] /= volume;
+        out[2] /= volume;
+    }
+}
+
+}  // namespace
+
+int launch_dt(const GridDesc &g, const PhysParams &P, const double *Q, double *red,
+              double *dt_dev, double *t_dev, double t_stop, cudaStream_t s) {
+    long long blocks = (g.n + kBlock - 1) / kBlock;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    dt_reduce_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(g, P, Q, (unsigned long long *)red);
+    dt_finalize_kernel<<<1, 1, 0, s>>>(g, P, (unsigned long long *)red, dt_dev, t_dev, t_stop);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_update(const GridDesc &g, const PhysParams &P, int stage, const double *frec,
+                  const double *dt_dev, double *Q, double *G, double *Qs, double *Gs,
+                  double *Acc, double *S1, int *status, cudaStream_t s) {
+    const long long blocks = (g.n + kBlock - 1) / kBlock;
+    if (stage == 0)
+        update_kernel<0><<<(unsigned)blocks, kBlock, 0, s>>>(g, P, frec, dt_dev, Q, G, Qs, Gs, Acc, S1, status);
+    else if (stage == 1)
+        update_kernel<1><<<(unsigned)blocks, kBlock, 0, s>>>(g, P, frec, dt_dev, Q, G, Qs, Gs, Acc, S1, status);
+    else
+        update_kernel<2><<<(unsigned)blocks, kBlock, 0, s>>>(g, P, frec, dt_dev, Q, G, Qs, Gs, Acc, S1, status);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int diagnostics_blocks(const GridDesc &g) {
+    long long blocks = (g.n + kBlock - 1) / kBlock;
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    return (int)blocks;
+}
+
+int launch_diagnostics(const GridDesc &g, const PhysParams &P, const double *Q, const double *G,
+                       double *partials, int nblocks, double *out_dev, cudaStream_t s) {
+    diag_partial_kernel<<<nblocks, kBlock, 0, s>>>(g, P, Q, G, partials);
+    const double volume = g.h[0] * g.h[1] * g.h[2] * (double)g.n;
+    diag_final_kernel<<<1, kBlock, 0, s>>>(partials, nblocks, volume, out_dev);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+}  // namespace gks

@@ -1,0 +1,228 @@
+"""ctypes binding of libgks.so (include/gks.h).
+
+Argument marshalling only: PyTorch supplies device memory and the CUDA
+stream, every step of the hot path runs in the library's sm_103a kernels.
+There is no CPU fallback: without a built library ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+GKS_OK = 0
+GKS_ERR_ARG = -1
+GKS_ERR_CUDA = -2
+GKS_ERR_NONPHYSICAL = -3
+GKS_ERR_TIMEOUT = -4
+GKS_ERR_STATE = -5
+GKS_ERR_NOMEM = -6
+
+SCHEMES = {"gks2": 0, "cgks5": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+
+class GksError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        msg = lib().gks_strerror(code).decode() if _LIB is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})")
+
+
+class Options(ctypes.Structure):
+    """Mirror of gks_options."""
+
+    _fields_ = [
+        ("scheme", ctypes.c_int), ("nonlinear", ctypes.c_int),
+        ("precision", ctypes.c_int), ("indicator", ctypes.c_int),
+        ("mu_law", ctypes.c_int), ("inviscid", ctypes.c_int),
+        ("C_tau", ctypes.c_double), ("eps_tau", ctypes.c_double),
+        ("T_ref", ctypes.c_double), ("theta", ctypes.c_double),
+    ]
+
+
+_LIB = None
+_VP = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+
+SIGNATURES = {
+    "gks_default_options": (None, [ctypes.POINTER(Options)]),
+    "gks_init": (_I, [ctypes.POINTER(_VP), _D, _D, _D, _D, _I, _I, _I, _D, _D, _D,
+                      ctypes.POINTER(Options), _VP]),
+    "gks_destroy": (None, [_VP]),
+    "gks_strerror": (ctypes.c_char_p, [_I]),
+    "gks_face_state_bytes": (ctypes.c_size_t, [_VP]),
+    "gks_face_flux_bytes": (ctypes.c_size_t, [_VP]),
+    "gks_compute_dt": (_I, [_VP, _VP, _VP]),
+    "gks_reconstruct": (_I, [_VP, _VP, _VP, _VP]),
+    "gks_flux": (_I, [_VP, _VP, _VP, _VP]),
+    "gks_flux_points": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
+    "gks_step": (_I, [_VP, _VP, _VP, _I, _D, _VP, ctypes.POINTER(_D)]),
+    "gks_diagnostics": (_I, [_VP, _VP, _VP, ctypes.POINTER(_D)]),
+    "gks_status": (_I, [_VP, ctypes.POINTER(_I)]),
+    "gks_recon_matrix": (_I, [ctypes.POINTER(_D)]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libgks.so (building it first if asked); raises if unavailable."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgks.so not built ({path}); run "
+                               "python -m paper_2508_19911_gb300.build")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, what):
+    if rc != GKS_OK:
+        raise GksError(rc, what)
+
+
+def recon_matrix() -> np.ndarray:
+    """The library's CGKS-5th reconstruction matrix (34 x 63), host-built."""
+    R = np.zeros((34, 63))
+    _check(lib().gks_recon_matrix(R.ctypes.data_as(ctypes.POINTER(_D))), "gks_recon_matrix")
+    return R
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Config:
+    n: tuple
+    L: tuple
+    gamma: float = 1.4
+    Pr: float = 0.72
+    mu: float = 1.0 / 1600
+    cfl: float = 0.3
+    scheme: str = "cgks5"
+    nonlinear: bool = True
+    precision: str = "fp64"
+    indicator: bool = False
+    mu_law: int = 0
+    inviscid: bool = False
+    C_tau: float = 10.0
+    eps_tau: float = 0.05
+    T_ref: float = 1.0
+    theta: float = 0.9
+
+
+class Solver:
+    """One gks_ctx: a periodic grid with its workspace on the current device."""
+
+    def __init__(self, cfg: Config, stream=None):
+        import torch
+        self.cfg = cfg
+        self.torch = torch
+        L = lib()
+        opt = Options()
+        L.gks_default_options(ctypes.byref(opt))
+        opt.scheme = SCHEMES[cfg.scheme]
+        opt.nonlinear = int(bool(cfg.nonlinear))
+        opt.precision = PRECISIONS[cfg.precision]
+        opt.indicator = int(bool(cfg.indicator))
+        opt.mu_law = int(cfg.mu_law)
+        opt.inviscid = int(bool(cfg.inviscid))
+        opt.C_tau, opt.eps_tau, opt.T_ref, opt.theta = cfg.C_tau, cfg.eps_tau, cfg.T_ref, cfg.theta
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = self.stream.device
+        ctx = _VP()
+        with torch.cuda.device(self.device):
+            _check(L.gks_init(ctypes.byref(ctx), cfg.gamma, cfg.Pr, cfg.mu, cfg.cfl,
+                              int(cfg.n[0]), int(cfg.n[1]), int(cfg.n[2]),
+                              float(cfg.L[0]), float(cfg.L[1]), float(cfg.L[2]),
+                              ctypes.byref(opt), _VP(self.stream.cuda_stream)), "gks_init")
+        self.ctx = ctx
+        self.ncells = int(cfg.n[0]) * int(cfg.n[1]) * int(cfg.n[2])
+        self.K = 4 if cfg.scheme == "cgks5" else 1
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().gks_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- tensors -------------------------------------------------------------
+    def zeros(self, *shape):
+        return self.torch.zeros(*shape, dtype=self.torch.float64, device=self.device)
+
+    def state_shape(self):
+        nx, ny, nz = self.cfg.n
+        return (5, nz, ny, nx), (5, 3, nz, ny, nx)
+
+    # -- entry points ----------------------------------------------------------
+    def compute_dt(self, Q, dt=None):
+        dt = self.zeros(1) if dt is None else dt
+        _check(lib().gks_compute_dt(self.ctx, _ptr(Q), _ptr(dt)), "gks_compute_dt")
+        return dt
+
+    def reconstruct(self, Q, G=None, out=None):
+        if out is None:
+            out = self.zeros(6, self.K, 20, self.ncells)
+        _check(lib().gks_reconstruct(self.ctx, _ptr(Q), _ptr(G), _ptr(out)), "gks_reconstruct")
+        return out
+
+    def flux(self, face_states, dt, out=None):
+        if out is None:
+            out = self.zeros(3, 30, self.ncells)
+        _check(lib().gks_flux(self.ctx, _ptr(face_states), _ptr(dt), _ptr(out)), "gks_flux")
+        return out
+
+    def flux_points(self, s_l, s_r, dt, out=None):
+        n = s_l.shape[1]
+        if out is None:
+            out = self.zeros(30, n)
+        _check(lib().gks_flux_points(self.ctx, _ptr(s_l), _ptr(s_r), n, _ptr(dt), _ptr(out)),
+               "gks_flux_points")
+        return out
+
+    def step(self, Q, G=None, nsteps=1, t_stop=math.inf, t=None, sync=True):
+        """Advance in place. Returns the last dt (sync=True) or None."""
+        last = _D(0.0)
+        rc = lib().gks_step(self.ctx, _ptr(Q), _ptr(G), int(nsteps), float(t_stop), _ptr(t),
+                            ctypes.byref(last) if sync else None)
+        _check(rc, "gks_step")
+        return last.value if sync else None
+
+    def diagnostics(self, Q, G=None):
+        out = (_D * 12)()
+        _check(lib().gks_diagnostics(self.ctx, _ptr(Q), _ptr(G), out), "gks_diagnostics")
+        return np.array(out[:], dtype=np.float64)
+
+    def status(self):
+        st = _I(0)
+        _check(lib().gks_status(self.ctx, ctypes.byref(st)), "gks_status")
+        return st.value
