@@ -38,8 +38,8 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # TGV 32^3 (see profiles/); a unit is one face Gauss point for the flux
 # kernel and one cell for the reconstruction kernel.
 FLOPS_PER_UNIT = {
-    "flux_cgks5": None,
-    "recon5": None,
+    "flux_cgks5": 5218.5,   # per face Gauss point
+    "recon5": 38865.0,      # per cell (5 conserved variables)
     "flux_gks2": None,
 }
 LAUNCHES_PER_STEP = {"cgks5": 8, "gks2": 5}
