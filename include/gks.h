@@ -178,6 +178,36 @@ int gks_status(gks_ctx *ctx, int *status);
  * caller-owned host memory of 34*63 doubles. */
 int gks_recon_matrix(double *R);
 
+/* Diagnostics without any device allocation (the paper has no counterpart:
+ * this serves callers of this library, not the method).
+ * For callers that cannot allocate device memory: a monitor that samples
+ * the diagnostics of a running simulation from outside the solver (another
+ * thread, a checkpoint hook, code that holds only device pointers and no
+ * gks_ctx). Large grids leave little free HBM, so an allocation made just to
+ * sample diagnostics may fail or evict the simulation's own buffers.
+ * Computes the same 12 values as gks_diagnostics (equal up to the order of
+ * the floating-point sums) for the state Q / gradQ (gradQ may be NULL:
+ * central differences) of an nx x ny x nz periodic grid of extents Lx, Ly,
+ * Lz, gas constant gamma, viscosity mu (Sutherland's law when mu_law = 1,
+ * temperature normalised by T_ref). out_dev: caller-owned DEVICE memory for
+ * 12 doubles, written asynchronously on cuda_stream (a cudaStream_t or
+ * NULL); the call does not synchronise and reads no status word.
+ * Scratch: a file-scope device array of 3 MiB (one block of 12 partial
+ * results per 4096 cells) that every GPU which loads the library holds
+ * until the process exits; grids above 2^27 cells (512^3) are rejected with
+ * GKS_ERR_ARG. Every call overwrites the slots it later reads, so nothing
+ * has to be cleared, but all calls on a device share the array: calls that
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller. The first call on each device looks up the
+ * array's device address (with that device current); make that first call
+ * before any stream capture. Calls no cudaMalloc, cudaFree or allocating
+ * library routine. Returns GKS_ERR_ARG for invalid arguments, GKS_ERR_CUDA
+ * if the address lookup or a launch fails. */
+int gks_diagnostics_noalloc(const double *Q, const double *gradQ, int nx, int ny,
+                            int nz, double Lx, double Ly, double Lz, double gamma,
+                            double mu, int mu_law, double T_ref, double *out_dev,
+                            void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

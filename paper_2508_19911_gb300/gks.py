@@ -67,6 +67,7 @@ SIGNATURES = {
     "gks_diagnostics": (_I, [_VP, _VP, _VP, ctypes.POINTER(_D)]),
     "gks_status": (_I, [_VP, ctypes.POINTER(_I)]),
     "gks_recon_matrix": (_I, [ctypes.POINTER(_D)]),
+    "gks_diagnostics_noalloc": (_I, [_VP, _VP, _I, _I, _I, _D, _D, _D, _D, _D, _I, _D, _VP, _VP]),
 }
 
 
