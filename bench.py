@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
     ap.add_argument("--scheme", default="cgks5", choices=["cgks5", "gks2"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -221,7 +222,9 @@ def run_ours(args, rank, world, local_rank):
     stages = 2 if cg else 1
     Qh, Gh, grid = wl.taylor_green(n)
     cells = n ** 3
-    solver = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=scheme, nonlinear=True), stream)
+    prec = args.precision
+    solver = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=scheme, nonlinear=True,
+                                   precision=prec), stream)
     Q = torch.tensor(Qh, device=dev)
     G = torch.tensor(Gh, device=dev) if cg else None
     for _ in range(args.warmup):
@@ -245,14 +248,15 @@ def run_ours(args, rank, world, local_rank):
     dtd = solver.compute_dt(Q)
     reps = 3
     t_recon = time_kernel(torch, lambda: solver.reconstruct(Q, G, out=fs), reps, stream)
-    frec = solver.flux(fs, dtd)
-    t_flux = time_kernel(torch, lambda: solver.flux(fs, dtd, out=frec), reps, stream)
+    frec = solver.flux(fs, dtd, Q=Q)
+    t_flux = time_kernel(torch, lambda: solver.flux(fs, dtd, out=frec, Q=Q), reps, stream)
     K = 4 if cg else 1
+    sfx = "_mixed" if prec == "mixed" else ""
     if t_flux >= t_recon:
-        kname, t_k = ("flux_cgks5" if cg else "flux_gks2"), t_flux
+        kname, t_k = ("flux_cgks5" if cg else "flux_gks2") + sfx, t_flux
         units = 3 * cells * K
     else:
-        kname, t_k = "recon5" if cg else "recon2", t_recon
+        kname, t_k = ("recon5" if cg else "recon2") + sfx, t_recon
         units = cells
     clocks = clk.summary()
     f_mhz = clocks["sm_max_mhz"] or SM_MAX_MHZ_NOMINAL
@@ -290,27 +294,42 @@ def run_ours(args, rank, world, local_rank):
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
            "ms_per_step": e2e_ms}
 
+    solver.close()
+    del fs, frec
     variants = {}
     if not args.no_variants and rank == 0:
-        other = "gks2" if cg else "cgks5"
-        s2 = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=other, nonlinear=True), stream)
-        Q2 = torch.tensor(Qh, device=dev)
-        G2 = torch.tensor(Gh, device=dev) if other == "cgks5" else None
-        for _ in range(2):
-            s2.step(Q2, G2, nsteps=1, sync=False)
-        ms2 = time_steps(torch, s2, Q2, G2, max(2, args.steps), stream)
-        st2 = 2 if other == "cgks5" else 1
-        variants[f"{other}_fp64_{n}^3"] = {"value": cells * st2 * max(2, args.steps) / (ms2 / 1e3),
-                                           "ms_per_step": ms2 / max(2, args.steps)}
-        s2.close()
-        del Q2, G2
+        for other in ("cgks5", "gks2"):
+            for oprec in ("fp64", "mixed"):
+                if (other, oprec) == (scheme, prec):
+                    continue
+                s2 = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=other, nonlinear=True,
+                                           precision=oprec), stream)
+                Q2 = torch.tensor(Qh, device=dev)
+                G2 = torch.tensor(Gh, device=dev) if other == "cgks5" else None
+                for _ in range(2):
+                    s2.step(Q2, G2, nsteps=1, sync=False)
+                k2 = max(2, args.steps)
+                ms2 = time_steps(torch, s2, Q2, G2, k2, stream)
+                st2 = 2 if other == "cgks5" else 1
+                fs2 = s2.reconstruct(Q2, G2)
+                d2 = s2.compute_dt(Q2)
+                tr = time_kernel(torch, lambda: s2.reconstruct(Q2, G2, out=fs2), 2, stream)
+                fr2 = s2.flux(fs2, d2, Q=Q2)
+                tf = time_kernel(torch, lambda: s2.flux(fs2, d2, out=fr2, Q=Q2), 2, stream)
+                variants[f"{other}_{oprec}_{n}^3"] = {
+                    "value": cells * st2 * k2 / (ms2 / 1e3), "unit": "cell-stage/s",
+                    "ms_per_step": ms2 / k2, "recon_ms": tr, "flux_ms": tf}
+                s2.close()
+                del Q2, G2, fs2, fr2
+                torch.cuda.empty_cache()
 
     line = {
         "metric": METRIC, "value": value, "unit": "cell-stage/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f32+f64",
         "data": "synthetic (Taylor-Green cell averages)",
-        "config": {"workload": f"taylor_green_{n}^3_{scheme}_fp64_nonlinear", "cells": cells,
+        "config": {"workload": f"taylor_green_{n}^3_{scheme}_{prec}_nonlinear", "cells": cells,
                    "scheme": scheme, "stages_per_step": stages, "Ma": 0.1, "Re": 1600,
                    "gamma": 1.4, "Pr": 0.72, "cfl": 0.3, "parallelism": f"replicas{world}",
                    "l2": "working set larger than L2 (state + face buffers > 129 MB)"},
@@ -318,7 +337,6 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": LAUNCHES_PER_STEP[scheme] * args.steps, "clocks": clocks,
         "variants": variants,
     }
-    solver.close()
     return line
 
 

@@ -115,7 +115,10 @@ int gks_compute_dt(gks_ctx *ctx, const double *Q, double *dt_dev);
  *   q 5..9   d/dn of the same, q 10..14 d/dt1, q 15..19 d/dt2.
  * Gauss point k sits at tangential offsets (+-g, +-g) h, g = 1/(2 sqrt 3),
  * bit 0 of k choosing the sign along t1 and bit 1 along t2 (K = 1: the face
- * midpoint). face_states = NULL uses the context's own buffer. */
+ * midpoint). Precision GKS_PREC_MIXED stores FP32 values, the components
+ * q 0..4 as offsets from the reconstructing cell's own average (the flux
+ * adds the FP64 average back). face_states = NULL uses the context's own
+ * buffer. */
 int gks_reconstruct(gks_ctx *ctx, const double *Q, const double *gradQ,
                     void *face_states);
 
@@ -123,17 +126,21 @@ int gks_reconstruct(gks_ctx *ctx, const double *Q, const double *gradQ,
  * [0, dt] and [0, dt/2], F^n and F_t^n of Eq. deri-t-f, the collision time
  * of Sec. 4, the Prandtl correction of the energy flux, and the interface
  * values of the update model of Sec. 3.4), averaged over each face's Gauss
- * points. face_states: as written by gks_reconstruct (NULL = the context's
- * buffer); dt_dev: device FP64 scalar. face_flux (device,
+ * points. Q: the cell averages the face states were reconstructed from
+ * (required in mixed precision, ignored in FP64); face_states: as written by
+ * gks_reconstruct (NULL = the context's buffer); dt_dev: device FP64 scalar.
+ * Mixed precision evaluates the Maxwellian slopes and the moments of the
+ * tau-weighted terms in FP32 and everything that carries the pressure or
+ * the time integration in FP64. face_flux (device,
  * gks_face_flux_bytes; NULL = the context's buffer) receives for axis d and
  * the face on the low-d side of cell c, element (d*30 + q)*cells + c:
  *   F^n(5), F_t^n(5), Q^l(5), dQ^l/dt(5), Q^r(5), dQ^r/dt(5)
  * in the global frame (the interface values only for CGKS-5th; GKS-2nd
  * leaves q 10..29 untouched). */
-int gks_flux(gks_ctx *ctx, const void *face_states, const double *dt_dev,
-             double *face_flux);
+int gks_flux(gks_ctx *ctx, const double *Q, const void *face_states,
+             const double *dt_dev, double *face_flux);
 
-/* The same flux at n independent Gauss points (unit-testing entry):
+/* The same flux (FP64 arithmetic) at n independent Gauss points:
  * s_l, s_r device double[20][n] face-frame states (layout of one Gauss point
  * of gks_reconstruct), out device double[30][n] in the face frame. */
 int gks_flux_points(gks_ctx *ctx, const double *s_l, const double *s_r,

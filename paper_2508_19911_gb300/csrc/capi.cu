@@ -19,7 +19,8 @@ struct gks_ctx {
     PhysParams P;
     gks_options opt;
     int K;                 // Gauss points per face
-    double *fs;            // face states [6][K][20][n]
+    void *fs;              // face states [6][K][20][n], FP64 or (mixed) FP32
+    int mixed;             // precision == GKS_PREC_MIXED
     double *frec;          // face records [3][30][n]
     double *Qs, *Gs, *Acc, *S1;  // CGKS-5th stage buffers
     double *scal;          // [0] dt, [1..2] dt reduction words, [3] diagnostics out (12)
@@ -115,7 +116,7 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
     if (!(gamma > 1.0) || !(Pr > 0.0) || !(mu >= 0.0) || !(cfl > 0.0 && cfl <= 1.0)) return GKS_ERR_ARG;
     if (nx < 1 || ny < 1 || nz < 1 || !(Lx > 0.0) || !(Ly > 0.0) || !(Lz > 0.0)) return GKS_ERR_ARG;
     if (o.scheme != GKS_SCHEME_GKS2 && o.scheme != GKS_SCHEME_CGKS5) return GKS_ERR_ARG;
-    if (o.precision != GKS_PREC_FP64) return GKS_ERR_ARG;  // mixed path: not in this build
+    if (o.precision != GKS_PREC_FP64 && o.precision != GKS_PREC_MIXED) return GKS_ERR_ARG;
     if (o.indicator) return GKS_ERR_ARG;
     if (o.mu_law < 0 || o.mu_law > 1 || !(o.C_tau >= 0.0) || !(o.eps_tau >= 0.0) ||
         !(o.T_ref > 0.0))
@@ -137,6 +138,7 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
     c->P.mu_law = o.mu_law; c->P.inviscid = o.inviscid; c->P.nonlinear = o.nonlinear ? 1 : 0;
     c->P.scheme = o.scheme;
     c->K = o.scheme == GKS_SCHEME_CGKS5 ? 4 : 1;
+    c->mixed = o.precision == GKS_PREC_MIXED;
 
     int rc = GKS_OK;
     if (o.scheme == GKS_SCHEME_CGKS5) {
@@ -144,7 +146,7 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
         if (t) { gks_destroy(c); return t == -1 ? GKS_ERR_ARG : GKS_ERR_CUDA; }
     }
     c->diag_blocks = diagnostics_blocks(c->g);
-    if ((rc = dalloc(&c->fs, (size_t)6 * c->K * 20 * n)) ||
+    if ((rc = dalloc((char **)&c->fs, (size_t)6 * c->K * 20 * n * (c->mixed ? 4 : 8))) ||
         (rc = dalloc(&c->frec, (size_t)90 * n)) ||
         (rc = dalloc(&c->scal, (size_t)3 + 12)) ||
         (rc = dalloc(&c->status, 1)) ||
@@ -170,7 +172,7 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
 }
 
 size_t gks_face_state_bytes(const gks_ctx *c) {
-    return c ? (size_t)6 * c->K * 20 * c->g.n * sizeof(double) : 0;
+    return c ? (size_t)6 * c->K * 20 * c->g.n * (c->mixed ? 4 : 8) : 0;
 }
 
 size_t gks_face_flux_bytes(const gks_ctx *c) {
@@ -182,21 +184,36 @@ int gks_compute_dt(gks_ctx *c, const double *Q, double *dt_dev) {
     return launch_ok(launch_dt(c->g, c->P, Q, red_slot(c), dt_dev, nullptr, 0.0, c->stream));
 }
 
+namespace {
+int recon_any(gks_ctx *c, const double *Q, const double *G, void *fs) {
+    const bool cg = c->P.scheme == GKS_SCHEME_CGKS5;
+    if (c->mixed)
+        return cg ? launch_recon5_mixed(c->g, c->P, Q, G, (float *)fs, c->stream)
+                  : launch_recon2_mixed(c->g, c->P, Q, (float *)fs, c->stream);
+    return cg ? launch_recon5(c->g, c->P, Q, G, (double *)fs, c->stream)
+              : launch_recon2(c->g, c->P, Q, (double *)fs, c->stream);
+}
+int flux_any(gks_ctx *c, const double *Q, const void *fs, const double *dt, double *fr) {
+    if (c->mixed)
+        return launch_flux_faces_mixed(c->g, c->P, (const float *)fs, Q, dt, fr, c->status,
+                                       c->stream);
+    return launch_flux_faces(c->g, c->P, (const double *)fs, dt, fr, c->status, c->stream);
+}
+}  // namespace
+
 int gks_reconstruct(gks_ctx *c, const double *Q, const double *G, void *face_states) {
     if (!c || !Q) return GKS_ERR_ARG;
-    double *fs = face_states ? (double *)face_states : c->fs;
-    if (c->P.scheme == GKS_SCHEME_CGKS5) {
-        if (!G) return GKS_ERR_ARG;
-        return launch_ok(launch_recon5(c->g, c->P, Q, G, fs, c->stream));
-    }
-    return launch_ok(launch_recon2(c->g, c->P, Q, fs, c->stream));
+    if (c->P.scheme == GKS_SCHEME_CGKS5 && !G) return GKS_ERR_ARG;
+    return launch_ok(recon_any(c, Q, G, face_states ? face_states : c->fs));
 }
 
-int gks_flux(gks_ctx *c, const void *face_states, const double *dt_dev, double *face_flux) {
+int gks_flux(gks_ctx *c, const double *Q, const void *face_states, const double *dt_dev,
+             double *face_flux) {
     if (!c || !dt_dev) return GKS_ERR_ARG;
-    const double *fs = face_states ? (const double *)face_states : c->fs;
+    if (c->mixed && !Q) return GKS_ERR_ARG;
+    const void *fs = face_states ? face_states : c->fs;
     double *fr = face_flux ? face_flux : c->frec;
-    return launch_ok(launch_flux_faces(c->g, c->P, fs, dt_dev, fr, c->status, c->stream));
+    return launch_ok(flux_any(c, Q, fs, dt_dev, fr));
 }
 
 int gks_flux_points(gks_ctx *c, const double *s_l, const double *s_r, int n,
@@ -216,18 +233,18 @@ int gks_step(gks_ctx *c, double *Q, double *G, int nsteps, double t_stop, double
         int rc = launch_dt(c->g, c->P, Q, red_slot(c), dt, t_dev, t_stop, c->stream);
         if (rc) return GKS_ERR_CUDA;
         if (!cgks) {
-            if ((rc = launch_recon2(c->g, c->P, Q, c->fs, c->stream)) ||
-                (rc = launch_flux_faces(c->g, c->P, c->fs, dt, c->frec, c->status, c->stream)) ||
+            if ((rc = recon_any(c, Q, nullptr, c->fs)) ||
+                (rc = flux_any(c, Q, c->fs, dt, c->frec)) ||
                 (rc = launch_update(c->g, c->P, 0, c->frec, dt, Q, nullptr, nullptr, nullptr,
                                     nullptr, nullptr, c->status, c->stream)))
                 return GKS_ERR_CUDA;
         } else {
-            if ((rc = launch_recon5(c->g, c->P, Q, G, c->fs, c->stream)) ||
-                (rc = launch_flux_faces(c->g, c->P, c->fs, dt, c->frec, c->status, c->stream)) ||
+            if ((rc = recon_any(c, Q, G, c->fs)) ||
+                (rc = flux_any(c, Q, c->fs, dt, c->frec)) ||
                 (rc = launch_update(c->g, c->P, 1, c->frec, dt, Q, G, c->Qs, c->Gs, c->Acc, c->S1,
                                     c->status, c->stream)) ||
-                (rc = launch_recon5(c->g, c->P, c->Qs, c->Gs, c->fs, c->stream)) ||
-                (rc = launch_flux_faces(c->g, c->P, c->fs, dt, c->frec, c->status, c->stream)) ||
+                (rc = recon_any(c, c->Qs, c->Gs, c->fs)) ||
+                (rc = flux_any(c, c->Qs, c->fs, dt, c->frec)) ||
                 (rc = launch_update(c->g, c->P, 2, c->frec, dt, Q, G, c->Qs, c->Gs, c->Acc, c->S1,
                                     c->status, c->stream)))
                 return GKS_ERR_CUDA;

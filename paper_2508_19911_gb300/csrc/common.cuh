@@ -50,6 +50,13 @@ int launch_recon2(const GridDesc &g, const PhysParams &P, const double *Q, doubl
 int upload_recon_tables(void);
 int launch_flux_faces(const GridDesc &g, const PhysParams &P, const double *fs,
                       const double *dt_dev, double *frec, int *status, cudaStream_t s);
+int launch_flux_faces_mixed(const GridDesc &g, const PhysParams &P, const float *fs,
+                            const double *Q, const double *dt_dev, double *frec, int *status,
+                            cudaStream_t s);
+int launch_recon5_mixed(const GridDesc &g, const PhysParams &P, const double *Q, const double *G,
+                        float *fs, cudaStream_t s);
+int launch_recon2_mixed(const GridDesc &g, const PhysParams &P, const double *Q, float *fs,
+                        cudaStream_t s);
 int launch_flux_points(const PhysParams &P, const double *sl, const double *sr, int n,
                        const double *dt_dev, double *out, int *status, cudaStream_t s);
 int launch_dt(const GridDesc &g, const PhysParams &P, const double *Q, double *red,

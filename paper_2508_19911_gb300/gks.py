@@ -61,7 +61,7 @@ SIGNATURES = {
     "gks_face_flux_bytes": (ctypes.c_size_t, [_VP]),
     "gks_compute_dt": (_I, [_VP, _VP, _VP]),
     "gks_reconstruct": (_I, [_VP, _VP, _VP, _VP]),
-    "gks_flux": (_I, [_VP, _VP, _VP, _VP]),
+    "gks_flux": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "gks_flux_points": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
     "gks_step": (_I, [_VP, _VP, _VP, _I, _D, _VP, ctypes.POINTER(_D)]),
     "gks_diagnostics": (_I, [_VP, _VP, _VP, ctypes.POINTER(_D)]),
@@ -106,13 +106,13 @@ def recon_matrix() -> np.ndarray:
     return R
 
 
-def _ptr(t):
+def _ptr(t, dtype=None):
     if t is None:
         return None
     import torch
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
-            and t.is_contiguous()):
-        raise TypeError("expected a contiguous float64 CUDA tensor")
+    want = torch.float64 if dtype is None else dtype
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == want and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous {want} CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -164,6 +164,7 @@ class Solver:
         self.ctx = ctx
         self.ncells = int(cfg.n[0]) * int(cfg.n[1]) * int(cfg.n[2])
         self.K = 4 if cfg.scheme == "cgks5" else 1
+        self.fs_dtype = torch.float32 if cfg.precision == "mixed" else torch.float64
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -192,14 +193,16 @@ class Solver:
 
     def reconstruct(self, Q, G=None, out=None):
         if out is None:
-            out = self.zeros(6, self.K, 20, self.ncells)
-        _check(lib().gks_reconstruct(self.ctx, _ptr(Q), _ptr(G), _ptr(out)), "gks_reconstruct")
+            out = self.torch.zeros(6, self.K, 20, self.ncells, dtype=self.fs_dtype, device=self.device)
+        _check(lib().gks_reconstruct(self.ctx, _ptr(Q), _ptr(G), _ptr(out, self.fs_dtype)),
+               "gks_reconstruct")
         return out
 
-    def flux(self, face_states, dt, out=None):
+    def flux(self, face_states, dt, out=None, Q=None):
         if out is None:
             out = self.zeros(3, 30, self.ncells)
-        _check(lib().gks_flux(self.ctx, _ptr(face_states), _ptr(dt), _ptr(out)), "gks_flux")
+        _check(lib().gks_flux(self.ctx, _ptr(Q), _ptr(face_states, self.fs_dtype), _ptr(dt),
+                              _ptr(out)), "gks_flux")
         return out
 
     def flux_points(self, s_l, s_r, dt, out=None):
