@@ -21,7 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["moments.cpp", "flux.cpp", "recon.cpp", "scheme.cpp"]
+_SOURCES = ["moments.cpp", "flux.cpp", "recon.cpp", "scheme.cpp", "mlp.cpp"]
 _LOCK = threading.Lock()
 _LIB = None
 
@@ -96,7 +96,13 @@ def lib():
                 "orc_run": [_P, _D, _D, ctypes.c_int, ctypes.c_double, _D, _D],
                 "orc_stage": [_P, _D, _D, ctypes.c_double, _D, _D, _D],
                 "orc_face_states": [_P, _D, _D, _D],
+                "orc_face_states_at": [_P, _D, _D, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.c_longlong, _D],
+                "orc_face_record": [_P, ctypes.c_int, _D, _D, ctypes.c_double, _D],
                 "orc_diagnostics": [_P, _D, _D, _D],
+                "orc_mlp_nparams": [],
+                "orc_mlp_loss_grad": [_D, _D, _D, ctypes.c_int, ctypes.c_longlong,
+                                      ctypes.c_double, _D, _D],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -209,7 +215,42 @@ def face_states(P, Q, G):
     return fs
 
 
+def face_states_at(P, Q, G, cells):
+    """Face states of the listed cells: [m][6][ngp][20]."""
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    ngp = 4 if P.scheme else 1
+    out = np.zeros((cells.size, 6, ngp, 20))
+    _check(lib().orc_face_states_at(ctypes.byref(P), _ptr(Q), _ptr(G),
+                                    cells.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                    cells.size, _ptr(out)), "face_states_at")
+    return out
+
+
+def face_record(P, d, sl, sr, dt_):
+    """Record of one face normal to axis d from sl, sr [ngp][20] (face
+    frame): 30 values, global frame."""
+    out = np.zeros(30)
+    _check(lib().orc_face_record(ctypes.byref(P), int(d),
+                                 _ptr(np.ascontiguousarray(sl, float)),
+                                 _ptr(np.ascontiguousarray(sr, float)), dt_, _ptr(out)),
+           "face_record")
+    return out
+
+
 def diagnostics(P, Q, G=None):
     out = np.zeros(12)
     _check(lib().orc_diagnostics(ctypes.byref(P), _ptr(Q), _ptr(G), _ptr(out)), "diagnostics")
     return out
+
+
+def mlp_loss_grad(params, x, y, neg_weight=1.0):
+    """Indicator network loss and gradient in FP64 (x: [63][n] samples)."""
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n = y.shape[0]
+    loss = np.zeros(1)
+    grad = np.zeros(lib().orc_mlp_nparams())
+    _check(lib().orc_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(y), n, x.shape[1], neg_weight,
+                                   _ptr(loss), _ptr(grad)), "mlp_loss_grad")
+    return float(loss[0]), grad

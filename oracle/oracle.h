@@ -109,10 +109,25 @@ int orc_stage(const orc_params *P, const double *Q, const double *G,
  * [6][1][20][cells] (GKS-2nd).                                            */
 int orc_face_states(const orc_params *P, const double *Q, const double *G,
                     double *fs);
+/* The same for the m listed cells only: out [m][6][ngp][20] (cell-major;
+ * ngp = 4 for CGKS-5th, 1 for GKS-2nd). Returns -1 for a cell out of range. */
+int orc_face_states_at(const orc_params *P, const double *Q, const double *G,
+                       const long long *cells, long long m, double *out);
+/* Record of one face normal to axis d from the left cell's high-face
+ * states sl [ngp][20] and the right cell's low-face states sr [ngp][20]
+ * (face frame): the Gauss-point average of the flux, global frame,
+ * rec30 = F^n, F_t^n, Q^l, dQ^l/dt, Q^r, dQ^r/dt (5 each).               */
+int orc_face_record(const orc_params *P, int d, const double *sl, const double *sr,
+                    double dt, double *rec30);
 /* out[12]: Ek, eps_S, eps_D, min rho, min p, sum Q h^3 (5), bad cells,
  * max(|U_d|+c).                                                           */
 int orc_diagnostics(const orc_params *P, const double *Q, const double *G,
                     double *out12);
+
+/* --- Learned indicator network (an extension; see mlp.cpp) ---------- */
+int orc_mlp_nparams(void);
+int orc_mlp_loss_grad(const double *params, const double *x, const double *y, int n,
+                      long long ld, double neg_weight, double *loss, double *grad);
 
 #ifdef __cplusplus
 }

@@ -51,6 +51,51 @@ const int kEdgeOff[12][3] = {{-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0},
 
 int nthreads(const orc_params &P) { return P.threads > 0 ? P.threads : 1; }
 
+/* Face states of cell c (Sec. 3.2 / 3.3): o[6][ngp][20]. */
+void cell_face_states(const orc_params &P, const Grid &g, const double *Q,
+                      const double *G, long c, double *o) {
+    const long n = g.n;
+    int i, j, k;
+    g.ijk(c, i, j, k);
+    if (P.scheme) {
+        double q0[5], d[5 * 63];
+        for (int v = 0; v < 5; ++v) {
+            q0[v] = Q[v * n + c];
+            double *dv = d + 63 * v;
+            for (int m = 0; m < 6; ++m) {
+                const long nb = g.idx(i + kFaceOff[m][0], j + kFaceOff[m][1], k + kFaceOff[m][2]);
+                dv[m] = Q[v * n + nb] - q0[v];
+                for (int a = 0; a < 3; ++a)
+                    dv[18 + 3 * m + a] = g.h[a] * G[(v * 3 + a) * n + nb];
+            }
+            for (int e = 0; e < 12; ++e) {
+                const long nb = g.idx(i + kEdgeOff[e][0], j + kEdgeOff[e][1], k + kEdgeOff[e][2]);
+                dv[6 + e] = Q[v * n + nb] - q0[v];
+                /* tangential derivatives of the edge neighbour (R2) */
+                const int *o = kEdgeOff[e];
+                int ax[2], na = 0, ez = 0;
+                for (int a = 0; a < 3; ++a) {
+                    if (o[a] != 0) ax[na++] = a; else ez = a;
+                }
+                const double da = g.h[ax[0]] * G[(v * 3 + ax[0]) * n + nb];
+                const double db = g.h[ax[1]] * G[(v * 3 + ax[1]) * n + nb];
+                dv[36 + 2 * e] = (o[ax[0]] * da - o[ax[1]] * db) / std::sqrt(2.0);
+                dv[36 + 2 * e + 1] = g.h[ez] * G[(v * 3 + ez) * n + nb];
+            }
+            for (int a = 0; a < 3; ++a) dv[60 + a] = g.h[a] * G[(v * 3 + a) * n + c];
+        }
+        recon5_cell(q0, d, g.h[0], g.h[1], g.h[2], P.nonlinear, o, nullptr);
+    } else {
+        double q7[35];
+        for (int v = 0; v < 5; ++v) q7[v] = Q[v * n + c];
+        for (int m = 0; m < 6; ++m) {
+            const long nb = g.idx(i + kFaceOff[m][0], j + kFaceOff[m][1], k + kFaceOff[m][2]);
+            for (int v = 0; v < 5; ++v) q7[5 * (m + 1) + v] = Q[v * n + nb];
+        }
+        recon2_cell(q7, g.h[0], g.h[1], g.h[2], P.nonlinear, o, nullptr);
+    }
+}
+
 /* Reconstructed face states of every cell: fs[c][f][k][20]. */
 void face_states(const orc_params &P, const Grid &g, const double *Q,
                  const double *G, std::vector<double> &fs) {
@@ -58,57 +103,40 @@ void face_states(const orc_params &P, const Grid &g, const double *Q,
     fs.assign((size_t)g.n * 6 * ngp * 20, 0.0);
     const long n = g.n;
 #pragma omp parallel for num_threads(nthreads(P)) schedule(static)
-    for (long c = 0; c < n; ++c) {
-        int i, j, k;
-        g.ijk(c, i, j, k);
-        double *o = &fs[(size_t)c * 6 * ngp * 20];
-        if (P.scheme) {
-            double q0[5], d[5 * 63];
-            for (int v = 0; v < 5; ++v) {
-                q0[v] = Q[v * n + c];
-                double *dv = d + 63 * v;
-                for (int m = 0; m < 6; ++m) {
-                    const long nb = g.idx(i + kFaceOff[m][0], j + kFaceOff[m][1], k + kFaceOff[m][2]);
-                    dv[m] = Q[v * n + nb] - q0[v];
-                    for (int a = 0; a < 3; ++a)
-                        dv[18 + 3 * m + a] = g.h[a] * G[(v * 3 + a) * n + nb];
-                }
-                for (int e = 0; e < 12; ++e) {
-                    const long nb = g.idx(i + kEdgeOff[e][0], j + kEdgeOff[e][1], k + kEdgeOff[e][2]);
-                    dv[6 + e] = Q[v * n + nb] - q0[v];
-                    /* tangential derivatives of the edge neighbour (R2) */
-                    const int *o = kEdgeOff[e];
-                    int ax[2], na = 0, ez = 0;
-                    for (int a = 0; a < 3; ++a) {
-                        if (o[a] != 0) ax[na++] = a; else ez = a;
-                    }
-                    const double da = g.h[ax[0]] * G[(v * 3 + ax[0]) * n + nb];
-                    const double db = g.h[ax[1]] * G[(v * 3 + ax[1]) * n + nb];
-                    dv[36 + 2 * e] = (o[ax[0]] * da - o[ax[1]] * db) / std::sqrt(2.0);
-                    dv[36 + 2 * e + 1] = g.h[ez] * G[(v * 3 + ez) * n + nb];
-                }
-                for (int a = 0; a < 3; ++a) dv[60 + a] = g.h[a] * G[(v * 3 + a) * n + c];
-            }
-            recon5_cell(q0, d, g.h[0], g.h[1], g.h[2], P.nonlinear, o, nullptr);
-        } else {
-            double q7[35];
-            for (int v = 0; v < 5; ++v) q7[v] = Q[v * n + c];
-            for (int m = 0; m < 6; ++m) {
-                const long nb = g.idx(i + kFaceOff[m][0], j + kFaceOff[m][1], k + kFaceOff[m][2]);
-                for (int v = 0; v < 5; ++v) q7[5 * (m + 1) + v] = Q[v * n + nb];
-            }
-            recon2_cell(q7, g.h[0], g.h[1], g.h[2], P.nonlinear, o, nullptr);
-        }
-    }
+    for (long c = 0; c < n; ++c) cell_face_states(P, g, Q, G, c, &fs[(size_t)c * 6 * ngp * 20]);
 }
 
-/* Fluxes of all faces, averaged over each face's Gauss points with the
- * weights of the tensor 2-point rule (1/4 each) or the midpoint rule.
- * rec[d][30][c], face on c's low-d side; returns first error code.     */
+/* Record of one face normal to axis d (Sec. 2, 3.4): the Gauss-point
+ * fluxes of the left cell's high face sl[ngp][20] and the right cell's low
+ * face sr[ngp][20] averaged over the face, in the global frame: rec30 =
+ * (F^n, F_t^n, Q^l, dQ^l/dt, Q^r, dQ^r/dt). */
+int face_record(const orc_params &P, int d, const double *sl_all, const double *sr_all,
+                double dt, double rec30[30]) {
+    const int ngp = P.scheme ? 4 : 1;
+    const double wgt = 1.0 / ngp;
+    int err = 0;
+    double acc[30];
+    for (int q = 0; q < 30; ++q) acc[q] = 0.0;
+    for (int p = 0; p < ngp; ++p) {
+        double out[30];
+        const int rc = flux_gp(P, sl_all + 20 * p, sr_all + 20 * p, dt, out);
+        if (rc) err = rc;
+        for (int q = 0; q < 30; ++q) acc[q] += wgt * out[q];
+    }
+    /* back to the global frame */
+    for (int blk = 0; blk < 6; ++blk) {
+        const double *a = acc + 5 * blk;
+        double *gl = rec30 + 5 * blk;
+        gl[0] = a[0];
+        gl[4] = a[4];
+        for (int jj = 0; jj < 3; ++jj) gl[1 + frame_axis(d, jj)] = a[1 + jj];
+    }
+    return err;
+}
+
 int face_fluxes(const orc_params &P, const Grid &g, const std::vector<double> &fs,
                 double dt, double *rec) {
     const int ngp = P.scheme ? 4 : 1;
-    const double wgt = 1.0 / ngp;
     const long n = g.n;
     int err = 0;
     for (int d = 0; d < 3; ++d) {
@@ -117,28 +145,14 @@ int face_fluxes(const orc_params &P, const Grid &g, const std::vector<double> &f
             int i, j, k;
             g.ijk(c, i, j, k);
             const long left = g.idx(i - (d == 0), j - (d == 1), k - (d == 2));
-            double acc[30];
-            for (int q = 0; q < 30; ++q) acc[q] = 0.0;
-            for (int p = 0; p < ngp; ++p) {
-                const double *sl = &fs[(((size_t)left * 6 + 2 * d + 1) * ngp + p) * 20];
-                const double *sr = &fs[(((size_t)c * 6 + 2 * d) * ngp + p) * 20];
-                double out[30];
-                const int rc = flux_gp(P, sl, sr, dt, out);
-                if (rc) {
+            double r30[30];
+            const int rc = face_record(P, d, &fs[((size_t)left * 6 + 2 * d + 1) * ngp * 20],
+                                       &fs[((size_t)c * 6 + 2 * d) * ngp * 20], dt, r30);
+            if (rc) {
 #pragma omp atomic write
-                    err = rc;
-                }
-                for (int q = 0; q < 30; ++q) acc[q] += wgt * out[q];
+                err = rc;
             }
-            /* back to the global frame */
-            for (int blk = 0; blk < 6; ++blk) {
-                const double *a = acc + 5 * blk;
-                double gl[5];
-                gl[0] = a[0];
-                gl[4] = a[4];
-                for (int jj = 0; jj < 3; ++jj) gl[1 + frame_axis(d, jj)] = a[1 + jj];
-                for (int v = 0; v < 5; ++v) rec[((size_t)d * 30 + 5 * blk + v) * n + c] = gl[v];
-            }
+            for (int q = 0; q < 30; ++q) rec[((size_t)d * 30 + q) * n + c] = r30[q];
         }
     }
     return err;
@@ -214,6 +228,23 @@ extern "C" int orc_face_states(const orc_params *P, const double *Q,
                     fs_out[(((size_t)f * ngp + k) * 20 + q) * g.n + c] =
                         fs[(((size_t)c * 6 + f) * ngp + k) * 20 + q];
     return 0;
+}
+
+extern "C" int orc_face_states_at(const orc_params *P, const double *Q, const double *G,
+                                  const long long *cells, long long m, double *out) {
+    const Grid g = make_grid(*P);
+    const int ngp = P->scheme ? 4 : 1;
+    for (long long s = 0; s < m; ++s) {
+        if (cells[s] < 0 || cells[s] >= g.n) return -1;
+        cell_face_states(*P, g, Q, G, (long)cells[s], out + (size_t)s * 6 * ngp * 20);
+    }
+    return 0;
+}
+
+extern "C" int orc_face_record(const orc_params *P, int d, const double *sl, const double *sr,
+                               double dt, double *rec30) {
+    if (d < 0 || d > 2) return -1;
+    return face_record(*P, d, sl, sr, dt, rec30);
 }
 
 extern "C" int orc_stage(const orc_params *P, const double *Q, const double *G,

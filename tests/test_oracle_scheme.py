@@ -206,3 +206,26 @@ def test_order_of_accuracy_on_smooth_advection(orc, scheme, sizes, cfl, t_end, l
         errs.append(np.abs(Q[0] - Qe[0]).mean())
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert all(lo < o < hi for o in orders), (errs, orders)
+
+
+def test_sampled_entry_points_equal_the_full_grid_ones(orc):
+    """orc_face_states_at / orc_face_record (used at sizes where the full
+    oracle is too slow) restrict the full-grid computation: same numbers."""
+    Q, G, grid = wl.taylor_green((10, 9, 8))
+    Q, G = wl.perturb(Q, G, amp=0.02, seed=8)
+    P = orc.params(n=grid.n, L=grid.L)
+    fs = orc.face_states(P, Q, G)
+    cells = np.array([0, 9, 89, 719, 333])
+    at = orc.face_states_at(P, Q, G, cells)
+    assert np.array_equal(at, np.moveaxis(fs[..., cells], -1, 0))
+    dt = 2e-3
+    _, _, faces = orc.stage(P, Q, G, dt)
+    nx, ny, nz = grid.n
+    for c in cells:
+        i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+        for d in range(3):
+            o = [i, j, k]
+            o[d] = (o[d] - 1) % grid.n[d]
+            left = o[0] + nx * (o[1] + ny * o[2])
+            rec = orc.face_record(P, d, fs[2 * d + 1, :, :, left], fs[2 * d, :, :, c], dt)
+            assert np.array_equal(rec, faces[d, :, c])
