@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
     ap.add_argument("--scheme", default="cgks5", choices=["cgks5", "gks2"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--indicator", action="store_true",
+                    help="mixed precision with the learned smoothness indicator (CGKS-5th)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -182,6 +184,21 @@ def reference_arm(args, rank):
 
 
 # ---------------------------------------------------------------------------
+def trained_indicator(torch, dev):
+    """Train the smoothness-indicator network on the GPU (library kernels:
+    dumps of the solver's own data vectors and chi, loss/gradient/Adam)."""
+    from paper_2508_19911_gb300 import indicator as ind
+    t0 = time.time()
+    x, y, stats = ind.training_set(dev, n=32)
+    params, hist = ind.train(x, y, epochs=6, seed=1)
+    info = {"theta": ind.THETA, "label_eps": ind.LABEL_EPS, "samples": int(y.numel()),
+            "label_1_fraction": float(y.mean().item()), "final_loss": float(hist[-1]),
+            "train_s": time.time() - t0}
+    del x, y
+    torch.cuda.empty_cache()
+    return params.cpu().numpy(), info
+
+
 def time_steps(torch, solver, Q, G, steps, stream):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -222,9 +239,16 @@ def run_ours(args, rank, world, local_rank):
     stages = 2 if cg else 1
     Qh, Gh, grid = wl.taylor_green(n)
     cells = n ** 3
-    prec = args.precision
+    prec = "mixed" if args.indicator else args.precision
+    if args.indicator and not cg:
+        raise SystemExit("--indicator needs --scheme cgks5")
+    params, ind_info = (None, None)
+    if args.indicator or (cg and not args.no_variants and rank == 0):
+        params, ind_info = trained_indicator(torch, dev)
     solver = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=scheme, nonlinear=True,
-                                   precision=prec), stream)
+                                   precision=prec, indicator=args.indicator), stream)
+    if args.indicator:
+        solver.set_indicator(params, theta=ind_info["theta"])
     Q = torch.tensor(Qh, device=dev)
     G = torch.tensor(Gh, device=dev) if cg else None
     for _ in range(args.warmup):
@@ -242,6 +266,9 @@ def run_ours(args, rank, world, local_rank):
     if st:
         raise RuntimeError(f"non-physical state during the benchmark (status {st})")
     value = world * cells * stages * args.steps / (ms / 1e3)
+    if args.indicator:
+        ind_info["skip_fraction"] = solver.indicator_skips() / (
+            5 * cells * stages * (args.steps + args.warmup))
 
     # dominant kernel: reconstruction or flux launch timed alone (same inputs)
     fs = solver.reconstruct(Q, G)
@@ -251,7 +278,7 @@ def run_ours(args, rank, world, local_rank):
     frec = solver.flux(fs, dtd, Q=Q)
     t_flux = time_kernel(torch, lambda: solver.flux(fs, dtd, out=frec, Q=Q), reps, stream)
     K = 4 if cg else 1
-    sfx = "_mixed" if prec == "mixed" else ""
+    sfx = ("_learned" if args.indicator else "_mixed") if prec == "mixed" else ""
     if t_flux >= t_recon:
         kname, t_k = ("flux_cgks5" if cg else "flux_gks2") + sfx, t_flux
         units = 3 * cells * K
@@ -298,12 +325,16 @@ def run_ours(args, rank, world, local_rank):
     del fs, frec
     variants = {}
     if not args.no_variants and rank == 0:
+        main_tag = (scheme, "learned" if args.indicator else prec)
         for other in ("cgks5", "gks2"):
-            for oprec in ("fp64", "mixed"):
-                if (other, oprec) == (scheme, prec):
+            for oprec in ("fp64", "mixed", "learned"):
+                if (other, oprec) == main_tag or (other == "gks2" and oprec == "learned"):
                     continue
                 s2 = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=other, nonlinear=True,
-                                           precision=oprec), stream)
+                                           precision="mixed" if oprec == "learned" else oprec,
+                                           indicator=oprec == "learned"), stream)
+                if oprec == "learned":
+                    s2.set_indicator(params, theta=ind_info["theta"])
                 Q2 = torch.tensor(Qh, device=dev)
                 G2 = torch.tensor(Gh, device=dev) if other == "cgks5" else None
                 for _ in range(2):
@@ -319,6 +350,9 @@ def run_ours(args, rank, world, local_rank):
                 variants[f"{other}_{oprec}_{n}^3"] = {
                     "value": cells * st2 * k2 / (ms2 / 1e3), "unit": "cell-stage/s",
                     "ms_per_step": ms2 / k2, "recon_ms": tr, "flux_ms": tf}
+                if oprec == "learned":
+                    variants[f"{other}_{oprec}_{n}^3"]["skip_fraction"] = s2.indicator_skips() / (
+                        5 * cells * st2 * (k2 + 2) + 5 * cells * 3)
                 s2.close()
                 del Q2, G2, fs2, fr2
                 torch.cuda.empty_cache()
@@ -328,8 +362,10 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == "fp64" else "f32+f64",
+        "indicator": ind_info if args.indicator else None,
         "data": "synthetic (Taylor-Green cell averages)",
-        "config": {"workload": f"taylor_green_{n}^3_{scheme}_{prec}_nonlinear", "cells": cells,
+        "config": {"workload": f"taylor_green_{n}^3_{scheme}_{'learned' if args.indicator else prec}"
+                               "_nonlinear", "cells": cells,
                    "scheme": scheme, "stages_per_step": stages, "Ma": 0.1, "Re": 1600,
                    "gamma": 1.4, "Pr": 0.72, "cfl": 0.3, "parallelism": f"replicas{world}",
                    "l2": "working set larger than L2 (state + face buffers > 129 MB)"},

@@ -185,6 +185,98 @@ int gks_status(gks_ctx *ctx, int *status);
  * caller-owned host memory of 34*63 doubles. */
 int gks_recon_matrix(double *R);
 
+/* a8 -- learned smoothness indicator (an extension of the method: the
+ * paper has no such component). A per-(cell, variable) network predicts
+ * whether GENO's chi (Eq. weno-new) would equal 1 -- the nonlinear
+ * reconstruction collapsing to the linear quartic -- so that confident
+ * (cell, variable) pairs skip the nonlinear weights; all others run the
+ * full reconstruction. Network: x = the 63-entry data vector of S^data-5th,
+ * xh = x/(max|x| + 1e-30), h = max(W1 xh + b1, 0) (16 units),
+ * logit = w2 . h + b2. Parameters (gks_mlp_nparams() floats): W1 [16][63]
+ * row major, b1 [16], w2 [16], b2. */
+int gks_mlp_nparams(void);
+
+/* Training data from the method itself (CGKS-5th context, any precision):
+ * for every cell c and variable v, sample s = 5 c + v: x[j*5*cells + s]
+ * (j < 63) the FP32 data vector as the mixed-precision reconstruction forms
+ * it, chi[s] GENO's chi, y[s] = 1 if chi >= 1 - label_eps else 0. Device
+ * buffers owned by the caller. */
+int gks_indicator_dump(gks_ctx *ctx, const double *Q, const double *gradQ,
+                       float label_eps, float *x, float *chi, float *y);
+
+/* Mean weighted binary cross-entropy over n samples (x: device [63][ld],
+ * y: device [n]; samples of label 0 weighted by neg_weight) and its
+ * gradient: *loss (device float) and grad (device, gks_mlp_nparams()).
+ * Synchronises cuda_stream; allocates its own workspace. */
+int gks_mlp_loss_grad(const float *params, const float *x, const float *y,
+                      int n, long long ld, float neg_weight, float *loss,
+                      float *grad, void *cuda_stream);
+
+/* Adam training in place of params (device) for `epochs` passes of n/batch
+ * steps over a seeded coprime-stride permutation of the samples;
+ * loss_hist (device, epochs floats, nullable) receives the mean batch loss
+ * of each epoch. Deterministic for a given seed. Synchronises cuda_stream;
+ * allocates its own workspace. */
+int gks_mlp_train(float *params, const float *x, const float *y, int n,
+                  long long ld, int epochs, int batch, float lr,
+                  float neg_weight, unsigned seed, float *loss_hist,
+                  void *cuda_stream);
+
+/* Activate the indicator on a context created with precision
+ * GKS_PREC_MIXED, scheme CGKS-5th and options.indicator = 1: params (HOST,
+ * gks_mlp_nparams() floats) become the device's network (one per device,
+ * shared by all contexts on it); a (cell, variable) skips GENO when
+ * sigmoid(logit) >= theta (0 < theta <= 1; theta = 1 never skips). */
+int gks_set_indicator(gks_ctx *ctx, const float *params, float theta);
+
+/* Number of (cell, variable) reconstructions that skipped GENO since the
+ * last call (synchronising; resets the count). */
+int gks_indicator_skips(gks_ctx *ctx, unsigned long long *count);
+
+/* a9 -- batched ensemble of independent CGKS-5th instances of uneven size
+ * (an extension of the method). Instance i has grid dims[3i..3i+2], box
+ * lengths[3i..3i+2] and physics phys[8i..8i+7] = gamma, Pr, mu, CFL,
+ * mu_law (0/1), inviscid (0/1), C_tau, eps_tau; opt (NULL = defaults) must
+ * select CGKS-5th and gives the precision, the nonlinear switch and T_ref.
+ * The caller owns the states in two concatenated device arenas:
+ * Q_all[5 * total] with instance i's block [5][cells_i] at
+ * 5 * gks_ensemble_offset(e, i), and gradQ_all[15 * total] with its block
+ * [5][3][cells_i] at 15 * offset. The library splits the instances into
+ * work items of `tile` cells; each phase of a step (dt, reconstruction,
+ * flux, update) is one persistent launch over the items of all instances;
+ * every instance keeps its own dt and time. Work is enqueued on an internal
+ * stream ordered after and before cuda_stream. */
+typedef struct gks_ensemble gks_ensemble;
+int gks_ensemble_create(gks_ensemble **out, int n_instances, const int *dims,
+                        const double *lengths, const double *phys,
+                        const gks_options *opt, void *cuda_stream);
+void gks_ensemble_destroy(gks_ensemble *e);
+/* First cell of instance i in the arenas; i = n_instances: total cells;
+ * -1 for an invalid argument. */
+long long gks_ensemble_offset(const gks_ensemble *e, int i);
+/* Work-item size in cells (32 .. 2^22); rebuilds the work list. */
+int gks_ensemble_set_tile(gks_ensemble *e, int tile_cells);
+/* Advance every instance nsteps steps (each stops at t_stop). use_graph:
+ * capture one step into a CUDA graph (re-captured when Q, gradQ, the tile,
+ * t_stop or the indicator change) and replay it nsteps times. */
+int gks_ensemble_step(gks_ensemble *e, double *Q, double *gradQ, int nsteps,
+                      double t_stop, int use_graph);
+/* Synchronising: per-instance times (host array of n_instances) and the
+ * status word; returns GKS_ERR_NONPHYSICAL if it is set. */
+int gks_ensemble_times(gks_ensemble *e, double *t_host, int *status);
+/* Autotuner: times one graph-replayed step for work-item sizes
+ * 256 .. 8192 cells on a scratch copy of the state (the state and the
+ * instance times are unchanged), keeps the fastest; *tile_out and *best_ms
+ * (nullable) report it. Allocates and frees its scratch. */
+int gks_ensemble_autotune(gks_ensemble *e, const double *Q, const double *gradQ,
+                          int *tile_out, float *best_ms);
+/* Indicator training data from all instances: x [63][5 total], chi and y
+ * [5 total] (sample 5 (offset_i + c) + v), as gks_indicator_dump. */
+int gks_ensemble_dump(gks_ensemble *e, const double *Q, const double *gradQ,
+                      float label_eps, float *x, float *chi, float *y);
+/* The learned indicator for a mixed-precision ensemble (see gks_set_indicator). */
+int gks_ensemble_set_indicator(gks_ensemble *e, const float *params, float theta);
+
 /* Diagnostics without any device allocation (the paper has no counterpart:
  * this serves callers of this library, not the method).
  * For callers that cannot allocate device memory: a monitor that samples

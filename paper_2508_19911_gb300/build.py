@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["flux.cu", "recon.cu", "update.cu", "capi.cu", "noalloc.cu"]
+CU_SOURCES = ["flux.cu", "recon.cu", "update.cu", "capi.cu", "noalloc.cu", "mlp.cu", "ensemble.cu"]
 CPP_SOURCES = ["tables.cpp"]
 HEADERS = ["basis.h", "common.cuh"]
 COMPILE_TIMEOUT = 900

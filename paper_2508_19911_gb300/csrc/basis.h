@@ -95,6 +95,12 @@ static_assert(tables_agree(), "basis/stencil tables disagree");
 //               direction orthogonal to the offset o)
 //   [37 + 2n]   h d_e Q over Omega_{2,n} (edge direction)
 //   [60 + j]    h_j dQ/dx_j averaged over Omega_0
+// learned smoothness indicator: a 63 -> kMlpHidden (ReLU) -> 1 network on
+// the data vector normalised by its max norm (+ kMlpDelta)
+constexpr int kMlpHidden = 8;
+constexpr int kMlpParams = kMlpHidden * kNumData + 2 * kMlpHidden + 1;
+constexpr float kMlpDelta = 1e-30f;
+
 constexpr int kColFace = 0, kColEdge = 6, kColFaceGrad = 18, kColEdgeGrad = 36,
               kColCentreGrad = 60;
 

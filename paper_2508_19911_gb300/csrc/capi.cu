@@ -21,6 +21,8 @@ struct gks_ctx {
     int K;                 // Gauss points per face
     void *fs;              // face states [6][K][20][n], FP64 or (mixed) FP32
     int mixed;             // precision == GKS_PREC_MIXED
+    int indicator_on;      // learned indicator active (CGKS-5th, mixed)
+    unsigned long long *skips;  // (cell, variable) pairs that skipped GENO
     double *frec;          // face records [3][30][n]
     double *Qs, *Gs, *Acc, *S1;  // CGKS-5th stage buffers
     double *scal;          // [0] dt, [1..2] dt reduction words, [3] diagnostics out (12)
@@ -102,6 +104,7 @@ void gks_destroy(gks_ctx *c) {
     cudaFree(c->scal);
     cudaFree(c->status);
     cudaFree(c->partials);
+    cudaFree(c->skips);
     if (prev >= 0) cudaSetDevice(prev);
     delete c;
 }
@@ -117,7 +120,9 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
     if (nx < 1 || ny < 1 || nz < 1 || !(Lx > 0.0) || !(Ly > 0.0) || !(Lz > 0.0)) return GKS_ERR_ARG;
     if (o.scheme != GKS_SCHEME_GKS2 && o.scheme != GKS_SCHEME_CGKS5) return GKS_ERR_ARG;
     if (o.precision != GKS_PREC_FP64 && o.precision != GKS_PREC_MIXED) return GKS_ERR_ARG;
-    if (o.indicator) return GKS_ERR_ARG;
+    if (o.indicator && !(o.scheme == GKS_SCHEME_CGKS5 && o.precision == GKS_PREC_MIXED))
+        return GKS_ERR_ARG;
+    if (o.indicator && !(o.theta > 0.0 && o.theta <= 1.0)) return GKS_ERR_ARG;
     if (o.mu_law < 0 || o.mu_law > 1 || !(o.C_tau >= 0.0) || !(o.eps_tau >= 0.0) ||
         !(o.T_ref > 0.0))
         return GKS_ERR_ARG;
@@ -150,6 +155,7 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
         (rc = dalloc(&c->frec, (size_t)90 * n)) ||
         (rc = dalloc(&c->scal, (size_t)3 + 12)) ||
         (rc = dalloc(&c->status, 1)) ||
+        (rc = dalloc(&c->skips, 1)) ||
         (rc = dalloc(&c->partials, (size_t)12 * c->diag_blocks))) {
         gks_destroy(c);
         return rc;
@@ -163,6 +169,7 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
     }
     if (cudaMemsetAsync(c->scal, 0, sizeof(double) * 15, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->status, 0, sizeof(int), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->skips, 0, sizeof(unsigned long long), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->frec, 0, sizeof(double) * 90 * n, c->stream) != cudaSuccess) {
         gks_destroy(c);
         return GKS_ERR_CUDA;
@@ -188,7 +195,8 @@ namespace {
 int recon_any(gks_ctx *c, const double *Q, const double *G, void *fs) {
     const bool cg = c->P.scheme == GKS_SCHEME_CGKS5;
     if (c->mixed)
-        return cg ? launch_recon5_mixed(c->g, c->P, Q, G, (float *)fs, c->stream)
+        return cg ? launch_recon5_mixed(c->g, c->P, Q, G, (float *)fs, c->stream, c->indicator_on,
+                                        c->skips)
                   : launch_recon2_mixed(c->g, c->P, Q, (float *)fs, c->stream);
     return cg ? launch_recon5(c->g, c->P, Q, G, (double *)fs, c->stream)
               : launch_recon2(c->g, c->P, Q, (double *)fs, c->stream);
@@ -278,6 +286,33 @@ int gks_diagnostics(gks_ctx *c, const double *Q, const double *G, double *out) {
     return st ? GKS_ERR_NONPHYSICAL : GKS_OK;
 }
 
+int gks_set_indicator(gks_ctx *c, const float *params, float theta) {
+    if (!c || !params || !(theta > 0.0f && theta <= 1.0f)) return GKS_ERR_ARG;
+    if (!(c->P.scheme == GKS_SCHEME_CGKS5 && c->mixed && c->opt.indicator)) return GKS_ERR_STATE;
+    if (upload_indicator(params, theta)) return GKS_ERR_CUDA;
+    c->indicator_on = 1;
+    return GKS_OK;
+}
+
+int gks_indicator_skips(gks_ctx *c, unsigned long long *count) {
+    if (!c || !count) return GKS_ERR_ARG;
+    if (cudaMemcpyAsync(count, c->skips, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->skips, 0, sizeof(unsigned long long), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return GKS_ERR_CUDA;
+    return GKS_OK;
+}
+
+int gks_indicator_dump(gks_ctx *c, const double *Q, const double *G, float label_eps, float *x,
+                       float *chi, float *y) {
+    if (!c || !Q || !G || !x || !chi || !y || !(label_eps >= 0.0f)) return GKS_ERR_ARG;
+    if (c->P.scheme != GKS_SCHEME_CGKS5) return GKS_ERR_STATE;
+    if (launch_indicator_dump(c->g, Q, G, x, chi, c->stream)) return GKS_ERR_CUDA;
+    if (launch_labels(chi, y, 5 * c->g.n, label_eps, c->stream)) return GKS_ERR_CUDA;
+    return GKS_OK;
+}
+
 int gks_recon_matrix(double *R) {
     if (!R) return GKS_ERR_ARG;
     ReconTables *t = new (std::nothrow) ReconTables;
@@ -293,6 +328,7 @@ int gks_status(gks_ctx *c, int *status) {
     if (cudaMemcpyAsync(status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
             cudaSuccess ||
         cudaMemsetAsync(c->status, 0, sizeof(int), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->skips, 0, sizeof(unsigned long long), c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         return GKS_ERR_CUDA;
     return GKS_OK;

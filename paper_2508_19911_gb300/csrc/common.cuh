@@ -22,6 +22,23 @@ struct PhysParams {
     int mu_law, inviscid, nonlinear, scheme;
 };
 
+// One instance of a batched ensemble: its grid, its physics and the index
+// of its first cell in the concatenated arenas (every per-cell array of the
+// ensemble stores instance i's block [components][cells_i] at component
+// stride cells_i, starting at components * off).
+struct EnsInst {
+    GridDesc g;
+    PhysParams P;
+    long long off;
+};
+// A work item of the persistent ensemble kernels: cells [c0, c1) of one
+// instance.
+struct EnsItem {
+    int inst;
+    int pad;
+    long long c0, c1;
+};
+
 __host__ __device__ __forceinline__ long long cell_index(const GridDesc &g, int i, int j, int k) {
     return ((long long)k * g.ny + j) * g.nx + i;
 }
@@ -54,7 +71,11 @@ int launch_flux_faces_mixed(const GridDesc &g, const PhysParams &P, const float 
                             const double *Q, const double *dt_dev, double *frec, int *status,
                             cudaStream_t s);
 int launch_recon5_mixed(const GridDesc &g, const PhysParams &P, const double *Q, const double *G,
-                        float *fs, cudaStream_t s);
+                        float *fs, cudaStream_t s, int indicator, unsigned long long *skips);
+int launch_indicator_dump(const GridDesc &g, const double *Q, const double *G, float *x,
+                          float *chi, cudaStream_t s);
+int upload_indicator(const float *params, float theta);
+int launch_labels(const float *chi, float *y, long long m, float eps, cudaStream_t s);
 int launch_recon2_mixed(const GridDesc &g, const PhysParams &P, const double *Q, float *fs,
                         cudaStream_t s);
 int launch_flux_points(const PhysParams &P, const double *sl, const double *sr, int n,
@@ -69,5 +90,22 @@ int launch_diagnostics(const GridDesc &g, const PhysParams &P, const double *Q,
                        const double *G, double *partials, int nblocks, double *out_dev,
                        cudaStream_t s);
 int diagnostics_blocks(const GridDesc &g);
+
+// persistent ensemble kernels (see ensemble.cu)
+int launch_recon5_ens(const EnsInst *inst, const EnsItem *items, int nitems, int blocks,
+                      int mixed, int indicator, const double *Qa, const double *Ga, void *fsa,
+                      unsigned long long *skips, cudaStream_t s);
+int launch_indicator_dump_ens(const EnsInst *inst, const EnsItem *items, int nitems, int blocks,
+                              const double *Qa, const double *Ga, float *x, float *chi,
+                              long long total_cells, cudaStream_t s);
+int launch_flux_ens(const EnsInst *inst, const EnsItem *items, int nitems, int blocks, int mixed,
+                    const void *fsa, const double *Qa, const double *dt_arr, double *fra,
+                    int *status, cudaStream_t s);
+int launch_dt_ens(const EnsInst *inst, int ninst, const EnsItem *items, int nitems, int blocks,
+                  const double *Qa, double *red, double *dt_arr, double *t_arr, double t_stop,
+                  cudaStream_t s);
+int launch_update_ens(const EnsInst *inst, const EnsItem *items, int nitems, int blocks, int stage,
+                      const double *fra, const double *dt_arr, double *Qa, double *Ga, double *Qsa,
+                      double *Gsa, double *Acca, double *S1a, int *status, cudaStream_t s);
 
 }  // namespace gks

@@ -523,9 +523,84 @@ __device__ void flux_point_mixed(const PhysParams &P, const double Wl[5], const 
     }
 }
 
-template <bool kCGKS>
+// face-frame component c of conserved variable v on a face normal to axis d
+__device__ __forceinline__ int global_var(int c, int d) {
+    return (c == 0 || c == 4) ? c : 1 + (d + c - 1) % 3;
+}
+
+// Flux at Gauss point k of the face on the low-d side of cell c, reduced
+// over the face's K Gauss points (lanes 4m..4m+3 hold the points of one
+// face; all 32 lanes of the warp must call this together) and written to
+// the face records. MIXED: FP32 face-state offsets + FP64 averages Q.
+template <bool kCGKS, bool MIXED>
+__device__ __forceinline__ void flux_face_point(const GridDesc &g, const PhysParams &P,
+                                                const void *__restrict__ fsv,
+                                                const double *__restrict__ Q, double dt,
+                                                double *__restrict__ frec, int *status, int d,
+                                                long long c, int k, bool valid) {
+    constexpr int K = kCGKS ? 4 : 1;
+    const long long n = g.n;
+    const int i = (int)(c % g.nx);
+    const int j = (int)((c / g.nx) % g.ny);
+    const int kk = (int)(c / ((long long)g.nx * g.ny));
+    const long long left = cell_index(g, d == 0 ? wrap(i - 1, g.nx) : i,
+                                      d == 1 ? wrap(j - 1, g.ny) : j,
+                                      d == 2 ? wrap(kk - 1, g.nz) : kk);
+    double out[30];
+    if (!MIXED) {
+        const double *fs = (const double *)fsv;
+        double sl[20], sr[20];
+        const double *pl = fs + ((long long)((2 * d + 1) * K + k) * 20) * n + left;
+        const double *pr = fs + ((long long)((2 * d) * K + k) * 20) * n + c;
+#pragma unroll
+        for (int q = 0; q < 20; ++q) {
+            sl[q] = __ldg(pl + (long long)q * n);
+            sr[q] = __ldg(pr + (long long)q * n);
+        }
+        flux_point<kCGKS>(P, sl, sr, dt, out, valid ? status : nullptr);
+    } else {
+        const float *fs = (const float *)fsv;
+        double Wl[5], Wr[5];
+        float dl[15], dr[15];
+        const float *pl = fs + ((long long)((2 * d + 1) * K + k) * 20) * n + left;
+        const float *pr = fs + ((long long)((2 * d) * K + k) * 20) * n + c;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int v = global_var(q, d);
+            Wl[q] = __ldg(Q + (long long)v * n + left) + (double)__ldg(pl + (long long)q * n);
+            Wr[q] = __ldg(Q + (long long)v * n + c) + (double)__ldg(pr + (long long)q * n);
+        }
+#pragma unroll
+        for (int q = 0; q < 15; ++q) {
+            dl[q] = __ldg(pl + (long long)(5 + q) * n);
+            dr[q] = __ldg(pr + (long long)(5 + q) * n);
+        }
+        flux_point_mixed<kCGKS>(P, Wl, dl, Wr, dr, dt, out, valid ? status : nullptr);
+    }
+    constexpr int NV = kCGKS ? 30 : 10;
+    if (kCGKS) {
+        // Gauss-point average: butterfly over the four lanes of the face
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = out[q] + __shfl_xor_sync(0xffffffffu, out[q], 1);
+            s = s + __shfl_xor_sync(0xffffffffu, s, 2);
+            out[q] = 0.25 * s;
+        }
+    }
+    if (!valid) return;
+    // face frame -> global frame; lane k writes the values with q % K == k
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        if (q % K != k) continue;
+        const int blk = q / 5, cmp = q % 5;
+        frec[((long long)d * 30 + blk * 5 + global_var(cmp, d)) * n + c] = out[q];
+    }
+}
+
+template <bool kCGKS, bool MIXED>
 __global__ void __launch_bounds__(128) flux_faces_kernel(GridDesc g, PhysParams P,
-                                                         const double *__restrict__ fs,
+                                                         const void *__restrict__ fs,
+                                                         const double *__restrict__ Q,
                                                          const double *__restrict__ dt_dev,
                                                          double *__restrict__ frec, int *status) {
     const double dt = *dt_dev;
@@ -540,40 +615,38 @@ __global__ void __launch_bounds__(128) flux_faces_kernel(GridDesc g, PhysParams 
     const long long fc = gid / K;
     const int d = (int)(fc / n);
     const long long c = fc - (long long)d * n;
-    const int i = (int)(c % g.nx);
-    const int j = (int)((c / g.nx) % g.ny);
-    const int kk = (int)(c / ((long long)g.nx * g.ny));
-    const long long left = cell_index(g, d == 0 ? wrap(i - 1, g.nx) : i,
-                                      d == 1 ? wrap(j - 1, g.ny) : j,
-                                      d == 2 ? wrap(kk - 1, g.nz) : kk);
-    double sl[20], sr[20];
-    const double *pl = fs + ((long long)((2 * d + 1) * K + k) * 20) * n + left;
-    const double *pr = fs + ((long long)((2 * d) * K + k) * 20) * n + c;
-#pragma unroll
-    for (int q = 0; q < 20; ++q) {
-        sl[q] = __ldg(pl + (long long)q * n);
-        sr[q] = __ldg(pr + (long long)q * n);
-    }
-    double out[30];
-    flux_point<kCGKS>(P, sl, sr, dt, out, valid ? status : nullptr);
-    constexpr int NV = kCGKS ? 30 : 10;
-    if (kCGKS) {
-        // Gauss-point average: the four points of a face are lanes 4m..4m+3
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            double s = out[q] + __shfl_xor_sync(0xffffffffu, out[q], 1);
-            s = s + __shfl_xor_sync(0xffffffffu, s, 2);
-            out[q] = 0.25 * s;
+    flux_face_point<kCGKS, MIXED>(g, P, fs, Q, dt, frec, status, d, c, k, valid);
+}
+
+// Persistent ensemble flux (CGKS-5th): blocks stride over the work items
+// of all instances; an item of T cells holds 3 x T faces x 4 Gauss points.
+template <bool MIXED>
+__global__ void __launch_bounds__(128) flux_ens_kernel(const EnsInst *__restrict__ inst,
+                                                       const EnsItem *__restrict__ items,
+                                                       int nitems, const void *__restrict__ fsa,
+                                                       const double *__restrict__ Qa,
+                                                       const double *__restrict__ dt_arr,
+                                                       double *__restrict__ fra, int *status) {
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const EnsItem it = items[w];
+        const EnsInst I = inst[it.inst];
+        const double dt = dt_arr[it.inst];
+        if (!(dt > 0.0)) continue;  // uniform across the block
+        const long long T = it.c1 - it.c0;
+        const long long total = 12 * T;
+        const void *fs = MIXED ? (const void *)((const float *)fsa + 480 * I.off)
+                               : (const void *)((const double *)fsa + 480 * I.off);
+        for (long long t0 = 0; t0 < total; t0 += blockDim.x) {
+            long long gid = t0 + threadIdx.x;
+            const bool valid = gid < total;
+            if (!valid) gid = total - 1;
+            const int k = (int)(gid & 3);
+            const long long rem = gid >> 2;
+            const int d = (int)(rem / T);
+            const long long c = it.c0 + rem % T;
+            flux_face_point<true, MIXED>(I.g, I.P, fs, Qa + 5 * I.off, dt, fra + 90 * I.off,
+                                         status, d, c, k, valid);
         }
-    }
-    if (!valid) return;
-    // face frame -> global frame; lane k writes the values with q % K == k
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        if (q % K != k) continue;
-        const int blk = q / 5, cmp = q % 5;
-        const int v = (cmp == 0 || cmp == 4) ? cmp : 1 + (d + cmp - 1) % 3;
-        frec[((long long)d * 30 + blk * 5 + v) * n + c] = out[q];
     }
 }
 
@@ -595,71 +668,6 @@ __global__ void __launch_bounds__(128) flux_points_kernel(PhysParams P, const do
     for (int q = 0; q < 30; ++q) out_[(long long)q * n + i] = out[q];
 }
 
-// face-frame component c of conserved variable v on a face normal to axis d
-__device__ __forceinline__ int global_var(int c, int d) {
-    return (c == 0 || c == 4) ? c : 1 + (d + c - 1) % 3;
-}
-
-template <bool kCGKS>
-__global__ void __launch_bounds__(128) flux_faces_mixed_kernel(GridDesc g, PhysParams P,
-                                                               const float *__restrict__ fs,
-                                                               const double *__restrict__ Q,
-                                                               const double *__restrict__ dt_dev,
-                                                               double *__restrict__ frec, int *status) {
-    const double dt = *dt_dev;
-    if (!(dt > 0.0)) return;
-    constexpr int K = kCGKS ? 4 : 1;
-    const long long n = g.n;
-    const long long total = 3 * n * K;
-    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = gid < total;
-    if (!valid) gid = total - 1;
-    const int k = (int)(gid % K);
-    const long long fc = gid / K;
-    const int d = (int)(fc / n);
-    const long long c = fc - (long long)d * n;
-    const int i = (int)(c % g.nx);
-    const int j = (int)((c / g.nx) % g.ny);
-    const int kk = (int)(c / ((long long)g.nx * g.ny));
-    const long long left = cell_index(g, d == 0 ? wrap(i - 1, g.nx) : i,
-                                      d == 1 ? wrap(j - 1, g.ny) : j,
-                                      d == 2 ? wrap(kk - 1, g.nz) : kk);
-    // states: FP64 cell average + FP32 offset; derivatives FP32
-    double Wl[5], Wr[5];
-    float dl[15], dr[15];
-    const float *pl = fs + ((long long)((2 * d + 1) * K + k) * 20) * n + left;
-    const float *pr = fs + ((long long)((2 * d) * K + k) * 20) * n + c;
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        const int v = global_var(q, d);
-        Wl[q] = __ldg(Q + (long long)v * n + left) + (double)__ldg(pl + (long long)q * n);
-        Wr[q] = __ldg(Q + (long long)v * n + c) + (double)__ldg(pr + (long long)q * n);
-    }
-#pragma unroll
-    for (int q = 0; q < 15; ++q) {
-        dl[q] = __ldg(pl + (long long)(5 + q) * n);
-        dr[q] = __ldg(pr + (long long)(5 + q) * n);
-    }
-    double out[30];
-    flux_point_mixed<kCGKS>(P, Wl, dl, Wr, dr, dt, out, valid ? status : nullptr);
-    constexpr int NV = kCGKS ? 30 : 10;
-    if (kCGKS) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            double s = out[q] + __shfl_xor_sync(0xffffffffu, out[q], 1);
-            s = s + __shfl_xor_sync(0xffffffffu, s, 2);
-            out[q] = 0.25 * s;
-        }
-    }
-    if (!valid) return;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        if (q % K != k) continue;
-        const int blk = q / 5, cmp = q % 5;
-        frec[((long long)d * 30 + blk * 5 + global_var(cmp, d)) * n + c] = out[q];
-    }
-}
-
 }  // namespace
 
 int launch_flux_faces_mixed(const GridDesc &g, const PhysParams &P, const float *fs, const double *Q,
@@ -669,9 +677,9 @@ int launch_flux_faces_mixed(const GridDesc &g, const PhysParams &P, const float 
     const int block = 128;
     const long long grid = (total + block - 1) / block;
     if (P.scheme)
-        flux_faces_mixed_kernel<true><<<(unsigned)grid, block, 0, s>>>(g, P, fs, Q, dt_dev, frec, status);
+        flux_faces_kernel<true, true><<<(unsigned)grid, block, 0, s>>>(g, P, fs, Q, dt_dev, frec, status);
     else
-        flux_faces_mixed_kernel<false><<<(unsigned)grid, block, 0, s>>>(g, P, fs, Q, dt_dev, frec, status);
+        flux_faces_kernel<false, true><<<(unsigned)grid, block, 0, s>>>(g, P, fs, Q, dt_dev, frec, status);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -682,9 +690,19 @@ int launch_flux_faces(const GridDesc &g, const PhysParams &P, const double *fs,
     const int block = 128;
     const long long grid = (total + block - 1) / block;
     if (P.scheme)
-        flux_faces_kernel<true><<<(unsigned)grid, block, 0, s>>>(g, P, fs, dt_dev, frec, status);
+        flux_faces_kernel<true, false><<<(unsigned)grid, block, 0, s>>>(g, P, fs, nullptr, dt_dev, frec, status);
     else
-        flux_faces_kernel<false><<<(unsigned)grid, block, 0, s>>>(g, P, fs, dt_dev, frec, status);
+        flux_faces_kernel<false, false><<<(unsigned)grid, block, 0, s>>>(g, P, fs, nullptr, dt_dev, frec, status);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_flux_ens(const EnsInst *inst, const EnsItem *items, int nitems, int blocks, int mixed,
+                    const void *fsa, const double *Qa, const double *dt_arr, double *fra,
+                    int *status, cudaStream_t s) {
+    if (mixed)
+        flux_ens_kernel<true><<<blocks, 128, 0, s>>>(inst, items, nitems, fsa, Qa, dt_arr, fra, status);
+    else
+        flux_ens_kernel<false><<<blocks, 128, 0, s>>>(inst, items, nitems, fsa, Qa, dt_arr, fra, status);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

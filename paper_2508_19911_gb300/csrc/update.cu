@@ -31,23 +31,25 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-__global__ void __launch_bounds__(kBlock) dt_reduce_kernel(GridDesc g, PhysParams P,
-                                                           const double *__restrict__ Q,
-                                                           unsigned long long *red) {
+// max over the cell of (|U_d| + c)/h_d and the kinematic viscosity
+__device__ __forceinline__ void cell_rates(const GridDesc &g, const PhysParams &P,
+                                           const double *__restrict__ Q, long long c,
+                                           double &rate, double &numax) {
     const long long n = g.n;
-    double rate = 0.0, numax = 0.0;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
-         c += (long long)gridDim.x * blockDim.x) {
-        const double rho = Q[c];
-        const double ir = 1.0 / rho;
-        const double U = Q[n + c] * ir, V = Q[2 * n + c] * ir, W = Q[3 * n + c] * ir;
-        const double p = (P.gamma - 1.0) * (Q[4 * n + c] - 0.5 * rho * (U * U + V * V + W * W));
-        const double cs = sqrt(P.gamma * p * ir);
-        rate = fmax(rate, (fabs(U) + cs) / g.h[0]);
-        rate = fmax(rate, (fabs(V) + cs) / g.h[1]);
-        rate = fmax(rate, (fabs(W) + cs) / g.h[2]);
-        numax = fmax(numax, viscosity(P, rho, p) * ir);
-    }
+    const double rho = Q[c];
+    const double ir = 1.0 / rho;
+    const double U = Q[n + c] * ir, V = Q[2 * n + c] * ir, W = Q[3 * n + c] * ir;
+    const double p = (P.gamma - 1.0) * (Q[4 * n + c] - 0.5 * rho * (U * U + V * V + W * W));
+    const double cs = sqrt(P.gamma * p * ir);
+    rate = fmax(rate, (fabs(U) + cs) / g.h[0]);
+    rate = fmax(rate, (fabs(V) + cs) / g.h[1]);
+    rate = fmax(rate, (fabs(W) + cs) / g.h[2]);
+    numax = fmax(numax, viscosity(P, rho, p) * ir);
+}
+
+// block-wide max of (rate, numax), combined into red[0], red[1] by atomicMax
+// on the bit patterns (all values non-negative)
+__device__ __forceinline__ void block_max_to(double rate, double numax, unsigned long long *red) {
     rate = warp_max(rate);
     numax = warp_max(numax);
     __shared__ double sr[kBlock / 32], sn[kBlock / 32];
@@ -60,22 +62,40 @@ __global__ void __launch_bounds__(kBlock) dt_reduce_kernel(GridDesc g, PhysParam
         rate = warp_max(rate);
         numax = warp_max(numax);
         if (lane == 0) {
-            // non-negative doubles order like their bit patterns
             atomicMax(red, (unsigned long long)__double_as_longlong(rate));
             atomicMax(red + 1, (unsigned long long)__double_as_longlong(numax));
         }
     }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double dt_from_rates(const GridDesc &g, const PhysParams &P,
+                                                double rate, double numax) {
+    double dt = P.cfl / rate;
+    if (!P.inviscid && numax > 0.0) {
+        const double hmin = fmin(g.h[0], fmin(g.h[1], g.h[2]));
+        dt = fmin(dt, P.cfl * hmin * hmin / (3.0 * numax));
+    }
+    return dt;
+}
+
+__global__ void __launch_bounds__(kBlock) dt_reduce_kernel(GridDesc g, PhysParams P,
+                                                           const double *__restrict__ Q,
+                                                           unsigned long long *red) {
+    const long long n = g.n;
+    double rate = 0.0, numax = 0.0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        cell_rates(g, P, Q, c, rate, numax);
+    }
+    block_max_to(rate, numax, red);
 }
 
 __global__ void dt_finalize_kernel(GridDesc g, PhysParams P, unsigned long long *red,
                                    double *dt_dev, double *t_dev, double t_stop) {
     const double rate = __longlong_as_double((long long)red[0]);
     const double numax = __longlong_as_double((long long)red[1]);
-    double dt = P.cfl / rate;
-    if (!P.inviscid && numax > 0.0) {
-        const double hmin = fmin(g.h[0], fmin(g.h[1], g.h[2]));
-        dt = fmin(dt, P.cfl * hmin * hmin / (3.0 * numax));
-    }
+    double dt = dt_from_rates(g, P, rate, numax);
     if (t_dev) {
         const double rem = t_stop - *t_dev;
         if (dt > rem) dt = rem;
@@ -89,18 +109,13 @@ __global__ void dt_finalize_kernel(GridDesc g, PhysParams P, unsigned long long 
 }
 
 template <int STAGE>
-__global__ void __launch_bounds__(kBlock) update_kernel(GridDesc g, PhysParams P,
-                                                        const double *__restrict__ fr,
-                                                        const double *__restrict__ dt_dev,
-                                                        double *__restrict__ Q, double *__restrict__ G,
-                                                        double *__restrict__ Qs, double *__restrict__ Gs,
-                                                        double *__restrict__ Acc,
-                                                        double *__restrict__ S1, int *status) {
-    const double dt = *dt_dev;
-    if (!(dt > 0.0)) return;
+__device__ __forceinline__ void update_cell(const GridDesc &g, const PhysParams &P,
+                                            const double *__restrict__ fr, double dt,
+                                            double *__restrict__ Q, double *__restrict__ G,
+                                            double *__restrict__ Qs, double *__restrict__ Gs,
+                                            double *__restrict__ Acc, double *__restrict__ S1,
+                                            int *status, long long c) {
     const long long n = g.n;
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
     const int i = (int)(c % g.nx);
     const int j = (int)((c / g.nx) % g.ny);
     const int k = (int)(c / ((long long)g.nx * g.ny));
@@ -162,6 +177,73 @@ __global__ void __launch_bounds__(kBlock) update_kernel(GridDesc g, PhysParams P
     for (int v = 0; v < 5; ++v) finite = finite && isfinite(out[v]);
     if (!finite) flag_status(status, kStatusNonfinite);
     else if (!(rho > 0.0 && p > 0.0)) flag_status(status, kStatusNonphysical);
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(kBlock) update_kernel(GridDesc g, PhysParams P,
+                                                        const double *__restrict__ fr,
+                                                        const double *__restrict__ dt_dev,
+                                                        double *__restrict__ Q, double *__restrict__ G,
+                                                        double *__restrict__ Qs, double *__restrict__ Gs,
+                                                        double *__restrict__ Acc,
+                                                        double *__restrict__ S1, int *status) {
+    const double dt = *dt_dev;
+    if (!(dt > 0.0)) return;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < g.n) update_cell<STAGE>(g, P, fr, dt, Q, G, Qs, Gs, Acc, S1, status, c);
+}
+
+// ---- persistent ensemble kernels (instances of uneven size) -------------
+__global__ void __launch_bounds__(kBlock) dt_reduce_ens_kernel(const EnsInst *__restrict__ inst,
+                                                               const EnsItem *__restrict__ items,
+                                                               int nitems, const double *__restrict__ Qa,
+                                                               unsigned long long *red) {
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const EnsItem it = items[w];
+        const EnsInst I = inst[it.inst];
+        double rate = 0.0, numax = 0.0;
+        for (long long c = it.c0 + threadIdx.x; c < it.c1; c += blockDim.x)
+            cell_rates(I.g, I.P, Qa + 5 * I.off, c, rate, numax);
+        block_max_to(rate, numax, red + 2 * it.inst);
+    }
+}
+
+// one thread per instance: dt_i, clamped to t_stop - t_i, t_i advanced
+__global__ void dt_finalize_ens_kernel(const EnsInst *__restrict__ inst, int ninst,
+                                       unsigned long long *red, double *dt_arr, double *t_arr,
+                                       double t_stop) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    const EnsInst I = inst[i];
+    double dt = dt_from_rates(I.g, I.P, __longlong_as_double((long long)red[2 * i]),
+                              __longlong_as_double((long long)red[2 * i + 1]));
+    const double rem = t_stop - t_arr[i];
+    if (dt > rem) dt = rem;
+    if (!(dt > 0.0) || !isfinite(dt)) dt = 0.0;
+    t_arr[i] += dt;
+    dt_arr[i] = dt;
+    red[2 * i] = 0ull;
+    red[2 * i + 1] = 0ull;
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(kBlock) update_ens_kernel(const EnsInst *__restrict__ inst,
+                                                            const EnsItem *__restrict__ items,
+                                                            int nitems, const double *__restrict__ fra,
+                                                            const double *__restrict__ dt_arr,
+                                                            double *Qa, double *Ga, double *Qsa,
+                                                            double *Gsa, double *Acca, double *S1a,
+                                                            int *status) {
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const EnsItem it = items[w];
+        const EnsInst I = inst[it.inst];
+        const double dt = dt_arr[it.inst];
+        if (!(dt > 0.0)) continue;
+        const long long o = I.off;
+        for (long long c = it.c0 + threadIdx.x; c < it.c1; c += blockDim.x)
+            update_cell<STAGE>(I.g, I.P, fra + 90 * o, dt, Qa + 5 * o, Ga + 15 * o, Qsa + 5 * o,
+                               Gsa + 15 * o, Acca + 5 * o, S1a + 15 * o, status, c);
+    }
 }
 
 // ---- diagnostics ---------------------------------------------------------
@@ -308,6 +390,28 @@ int launch_update(const GridDesc &g, const PhysParams &P, int stage, const doubl
         update_kernel<1><<<(unsigned)blocks, kBlock, 0, s>>>(g, P, frec, dt_dev, Q, G, Qs, Gs, Acc, S1, status);
     else
         update_kernel<2><<<(unsigned)blocks, kBlock, 0, s>>>(g, P, frec, dt_dev, Q, G, Qs, Gs, Acc, S1, status);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_dt_ens(const EnsInst *inst, int ninst, const EnsItem *items, int nitems, int blocks,
+                  const double *Qa, double *red, double *dt_arr, double *t_arr, double t_stop,
+                  cudaStream_t s) {
+    dt_reduce_ens_kernel<<<blocks, kBlock, 0, s>>>(inst, items, nitems, Qa,
+                                                   (unsigned long long *)red);
+    dt_finalize_ens_kernel<<<(ninst + 63) / 64, 64, 0, s>>>(inst, ninst, (unsigned long long *)red,
+                                                            dt_arr, t_arr, t_stop);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_update_ens(const EnsInst *inst, const EnsItem *items, int nitems, int blocks, int stage,
+                      const double *fra, const double *dt_arr, double *Qa, double *Ga, double *Qsa,
+                      double *Gsa, double *Acca, double *S1a, int *status, cudaStream_t s) {
+    if (stage == 1)
+        update_ens_kernel<1><<<blocks, kBlock, 0, s>>>(inst, items, nitems, fra, dt_arr, Qa, Ga, Qsa,
+                                                       Gsa, Acca, S1a, status);
+    else
+        update_ens_kernel<2><<<blocks, kBlock, 0, s>>>(inst, items, nitems, fra, dt_arr, Qa, Ga, Qsa,
+                                                       Gsa, Acca, S1a, status);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

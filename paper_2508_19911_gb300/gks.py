@@ -68,6 +68,22 @@ SIGNATURES = {
     "gks_status": (_I, [_VP, ctypes.POINTER(_I)]),
     "gks_recon_matrix": (_I, [ctypes.POINTER(_D)]),
     "gks_diagnostics_noalloc": (_I, [_VP, _VP, _I, _I, _I, _D, _D, _D, _D, _D, _I, _D, _VP, _VP]),
+    "gks_mlp_nparams": (_I, []),
+    "gks_indicator_dump": (_I, [_VP, _VP, _VP, ctypes.c_float, _VP, _VP, _VP]),
+    "gks_mlp_loss_grad": (_I, [_VP, _VP, _VP, _I, ctypes.c_longlong, ctypes.c_float, _VP, _VP, _VP]),
+    "gks_mlp_train": (_I, [_VP, _VP, _VP, _I, ctypes.c_longlong, _I, _I, ctypes.c_float,
+                           ctypes.c_float, ctypes.c_uint, _VP, _VP]),
+    "gks_set_indicator": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_float]),
+    "gks_indicator_skips": (_I, [_VP, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "gks_ensemble_create": (_I, [ctypes.POINTER(_VP), _I, _VP, _VP, _VP, ctypes.POINTER(Options), _VP]),
+    "gks_ensemble_destroy": (None, [_VP]),
+    "gks_ensemble_offset": (ctypes.c_longlong, [_VP, _I]),
+    "gks_ensemble_set_tile": (_I, [_VP, _I]),
+    "gks_ensemble_step": (_I, [_VP, _VP, _VP, _I, _D, _I]),
+    "gks_ensemble_times": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    "gks_ensemble_autotune": (_I, [_VP, _VP, _VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
+    "gks_ensemble_dump": (_I, [_VP, _VP, _VP, ctypes.c_float, _VP, _VP, _VP]),
+    "gks_ensemble_set_indicator": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_float]),
 }
 
 
@@ -97,6 +113,37 @@ def lib(build_if_missing: bool = True):
 def _check(rc, what):
     if rc != GKS_OK:
         raise GksError(rc, what)
+
+
+def mlp_nparams() -> int:
+    return int(lib().gks_mlp_nparams())
+
+
+def mlp_loss_grad(params, x, y, neg_weight=1.0, stream=None):
+    """Loss and gradient of the indicator network (device tensors)."""
+    import torch
+    n = int(y.shape[0])
+    loss = torch.zeros(1, dtype=torch.float32, device=params.device)
+    grad = torch.zeros(mlp_nparams(), dtype=torch.float32, device=params.device)
+    st = stream if stream is not None else torch.cuda.current_stream(params.device)
+    _check(lib().gks_mlp_loss_grad(_ptr(params, torch.float32), _ptr(x, torch.float32),
+                                   _ptr(y, torch.float32), n, int(x.shape[1]), float(neg_weight),
+                                   _ptr(loss, torch.float32), _ptr(grad, torch.float32),
+                                   _VP(st.cuda_stream)), "gks_mlp_loss_grad")
+    return float(loss.item()), grad
+
+
+def mlp_train(params, x, y, epochs=10, batch=4096, lr=3e-3, neg_weight=1.0, seed=0, stream=None):
+    """Train in place; returns the per-epoch mean loss (numpy)."""
+    import torch
+    n = int(y.shape[0])
+    hist = torch.zeros(max(epochs, 1), dtype=torch.float32, device=params.device)
+    st = stream if stream is not None else torch.cuda.current_stream(params.device)
+    _check(lib().gks_mlp_train(_ptr(params, torch.float32), _ptr(x, torch.float32),
+                               _ptr(y, torch.float32), n, int(x.shape[1]), int(epochs), int(batch),
+                               float(lr), float(neg_weight), int(seed) & 0xFFFFFFFF,
+                               _ptr(hist, torch.float32), _VP(st.cuda_stream)), "gks_mlp_train")
+    return hist.cpu().numpy()[:epochs]
 
 
 def recon_matrix() -> np.ndarray:
@@ -226,7 +273,132 @@ class Solver:
         _check(lib().gks_diagnostics(self.ctx, _ptr(Q), _ptr(G), out), "gks_diagnostics")
         return np.array(out[:], dtype=np.float64)
 
+    # -- learned indicator ----------------------------------------------------
+    def indicator_dump(self, Q, G, label_eps=1e-4):
+        """(x [63][5 cells], chi [5 cells], y [5 cells]) float32 CUDA tensors."""
+        t = self.torch
+        m = 5 * self.ncells
+        x = t.empty(63, m, dtype=t.float32, device=self.device)
+        chi = t.empty(m, dtype=t.float32, device=self.device)
+        y = t.empty(m, dtype=t.float32, device=self.device)
+        _check(lib().gks_indicator_dump(self.ctx, _ptr(Q), _ptr(G), float(label_eps),
+                                        _ptr(x, t.float32), _ptr(chi, t.float32),
+                                        _ptr(y, t.float32)), "gks_indicator_dump")
+        return x, chi, y
+
+    def set_indicator(self, params, theta=0.9):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        _check(lib().gks_set_indicator(self.ctx, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                       float(theta)), "gks_set_indicator")
+
+    def indicator_skips(self):
+        n = ctypes.c_ulonglong(0)
+        _check(lib().gks_indicator_skips(self.ctx, ctypes.byref(n)), "gks_indicator_skips")
+        return n.value
+
     def status(self):
         st = _I(0)
         _check(lib().gks_status(self.ctx, ctypes.byref(st)), "gks_status")
         return st.value
+
+
+class Ensemble:
+    """A batch of independent CGKS-5th instances advanced together.
+
+    ``instances``: list of dicts with keys n (nx, ny, nz), L (Lx, Ly, Lz) and
+    the physics gamma, Pr, mu, cfl, mu_law, inviscid, C_tau, eps_tau (defaults
+    as in Config). The states live in two arenas owned by this object:
+    ``Q`` [5 * total] and ``G`` [15 * total] (float64 CUDA tensors); use
+    ``views(i)`` for instance i's [5][nz][ny][nx] and [5][3][nz][ny][nx] views.
+    """
+
+    def __init__(self, instances, *, precision="fp64", nonlinear=True, T_ref=1.0, stream=None):
+        import torch
+        self.torch = torch
+        n = len(instances)
+        dims = np.zeros(3 * n, dtype=np.int32)
+        lens = np.zeros(3 * n, dtype=np.float64)
+        phys = np.zeros(8 * n, dtype=np.float64)
+        for i, ins in enumerate(instances):
+            dims[3 * i: 3 * i + 3] = ins["n"]
+            lens[3 * i: 3 * i + 3] = ins["L"]
+            phys[8 * i: 8 * i + 8] = [ins.get("gamma", 1.4), ins.get("Pr", 0.72),
+                                      ins.get("mu", 1.0 / 1600), ins.get("cfl", 0.3),
+                                      ins.get("mu_law", 0), float(bool(ins.get("inviscid", False))),
+                                      ins.get("C_tau", 10.0), ins.get("eps_tau", 0.05)]
+        opt = Options()
+        lib().gks_default_options(ctypes.byref(opt))
+        opt.scheme = SCHEMES["cgks5"]
+        opt.precision = PRECISIONS[precision]
+        opt.nonlinear = int(bool(nonlinear))
+        opt.indicator = 0
+        opt.T_ref = T_ref
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = self.stream.device
+        self.instances = instances
+        ctx = _VP()
+        with torch.cuda.device(self.device):
+            _check(lib().gks_ensemble_create(ctypes.byref(ctx), n, dims.ctypes.data_as(_VP),
+                                             lens.ctypes.data_as(_VP), phys.ctypes.data_as(_VP),
+                                             ctypes.byref(opt), _VP(self.stream.cuda_stream)),
+                   "gks_ensemble_create")
+        self.e = ctx
+        self.n = n
+        self.offsets = [int(lib().gks_ensemble_offset(ctx, i)) for i in range(n + 1)]
+        self.total = self.offsets[-1]
+        self.Q = torch.zeros(5 * self.total, dtype=torch.float64, device=self.device)
+        self.G = torch.zeros(15 * self.total, dtype=torch.float64, device=self.device)
+
+    def close(self):
+        if getattr(self, "e", None):
+            lib().gks_ensemble_destroy(self.e)
+            self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def views(self, i):
+        nx, ny, nz = self.instances[i]["n"]
+        o, c = self.offsets[i], self.offsets[i + 1] - self.offsets[i]
+        return (self.Q[5 * o: 5 * (o + c)].view(5, nz, ny, nx),
+                self.G[15 * o: 15 * (o + c)].view(5, 3, nz, ny, nx))
+
+    def set_tile(self, tile):
+        _check(lib().gks_ensemble_set_tile(self.e, int(tile)), "gks_ensemble_set_tile")
+
+    def step(self, nsteps=1, t_stop=math.inf, graph=True):
+        _check(lib().gks_ensemble_step(self.e, _ptr(self.Q), _ptr(self.G), int(nsteps),
+                                       float(t_stop), int(bool(graph))), "gks_ensemble_step")
+
+    def times(self):
+        t = (_D * self.n)()
+        st = _I(0)
+        rc = lib().gks_ensemble_times(self.e, t, ctypes.byref(st))
+        _check(rc, "gks_ensemble_times")
+        return np.array(t[:])
+
+    def autotune(self):
+        tile = _I(0)
+        ms = ctypes.c_float(0)
+        _check(lib().gks_ensemble_autotune(self.e, _ptr(self.Q), _ptr(self.G), ctypes.byref(tile),
+                                           ctypes.byref(ms)), "gks_ensemble_autotune")
+        return tile.value, ms.value
+
+    def dump(self, label_eps=1e-4):
+        t = self.torch
+        m = 5 * self.total
+        x = t.empty(63, m, dtype=t.float32, device=self.device)
+        chi = t.empty(m, dtype=t.float32, device=self.device)
+        y = t.empty(m, dtype=t.float32, device=self.device)
+        _check(lib().gks_ensemble_dump(self.e, _ptr(self.Q), _ptr(self.G), float(label_eps),
+                                       _ptr(x, t.float32), _ptr(chi, t.float32), _ptr(y, t.float32)),
+               "gks_ensemble_dump")
+        return x, chi, y
+
+    def set_indicator(self, params, theta=0.9):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        _check(lib().gks_ensemble_set_indicator(self.e, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                float(theta)), "gks_ensemble_set_indicator")

@@ -232,6 +232,10 @@ def isotropic_turbulence(n=32, *, Mt=0.5, k0=8.0, seed=101, gamma=1.4,
     kvec = np.stack([kx, ky, kz])
     a -= kvec * (np.sum(kvec * a, axis=0) / kk_safe ** 2)[None]
     spec = kk ** 4 * np.exp(-2.0 * (kk / k0) ** 2)
+    # no energy in the Nyquist planes (their sign of k is ambiguous, which
+    # would break the solenoidal projection of the real field)
+    nyq = (np.abs(kx) >= n // 2) | (np.abs(ky) >= n // 2) | (np.abs(kz) >= n // 2)
+    spec[nyq] = 0.0
     # amplitude so that the shell energy follows spec: |u_k|^2 ~ E(k)/(4 pi k^2)
     amp = np.sqrt(spec / (4 * np.pi * kk_safe ** 2))
     amp[kk == 0] = 0.0
@@ -268,6 +272,71 @@ def isotropic_turbulence(n=32, *, Mt=0.5, k0=8.0, seed=101, gamma=1.4,
     grid = Grid((n, n, n), (2 * np.pi,) * 3)
     return Q, G, grid, {"u_rms": urms_target, "taylor_lambda": float(lam_t),
                         "p0": p0}
+
+
+def double_shear_layer(nx=64, ny=64, *, amp=0.05, Ma=0.3, gamma=1.4, delta=np.pi / 15):
+    """Periodic double shear layer on [0, 2 pi]^2 (nz = 1): U = tanh((y -
+    pi/2)/delta) for y <= pi and tanh((3 pi/2 - y)/delta) above, V = amp
+    sin x, rho = 1, p from Ma with U0 = 1."""
+    h = 2 * np.pi / nx
+    grid = Grid((nx, ny, 1), (2 * np.pi, 2 * np.pi, h))
+
+    def u_of_y(y):
+        return np.where(y <= np.pi, np.tanh((y - np.pi / 2) / delta),
+                        np.tanh((3 * np.pi / 2 - y) / delta))
+
+    p0 = 1.0 / (gamma * Ma * Ma)
+    Q, G = _conserved(grid, _const(1.0), [(1.0, _one, u_of_y, _one)],
+                      [(amp, np.sin, _one, _one)], _const(0.0), _const(p0), gamma)
+    return Q, G, grid
+
+
+def riemann_quadrants(nx=64, ny=64, *, states, amp=0.01, seed=0, gamma=1.4):
+    """Periodic four-quadrant Riemann problem on [0, 1]^2 (nz = 1): states[q]
+    = (rho, u, v, p) for the quadrants q = (x > 1/2) + 2 (y > 1/2), cell
+    averages (the jumps sit on cell faces for even nx, ny) with a seeded
+    cell-wise relative noise of amplitude amp on rho."""
+    if nx % 2 or ny % 2:
+        raise ValueError("nx, ny must be even")
+    rng = np.random.default_rng(seed)
+    grid = Grid((nx, ny, 1), (1.0, 1.0, 1.0 / nx))
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    q = (x[None, :] > 0.5).astype(int) + 2 * (y[:, None] > 0.5).astype(int)
+    st = np.asarray(states, dtype=float)
+    rho = st[q, 0] * (1.0 + amp * rng.uniform(-1, 1, q.shape))
+    u, v, p = st[q, 1], st[q, 2], st[q, 3]
+    Q = np.zeros((5, 1, ny, nx))
+    Q[0, 0] = rho
+    Q[1, 0] = rho * u
+    Q[2, 0] = rho * v
+    Q[4, 0] = p / (gamma - 1) + 0.5 * rho * (u * u + v * v)
+    G = np.zeros((5, 3, 1, ny, nx))
+    return Q, G, grid
+
+
+def ensemble_instances(count=64, seed0=2000, sizes=(64, 128, 256, 512)):
+    """Seeded ensemble of 2D instances: the first half periodic double shear
+    layers (Ma 0.3, Re 1e4), the second half four-quadrant Riemann problems
+    (inviscid collision time) with quadrant states drawn per seed
+    (rho in [0.1, 1.5], p in [0.05, 1.5], u, v in [-1, 1]); nx, ny drawn from
+    ``sizes``, perturbation amplitude log-uniform in [1e-3, 1e-1].
+    Returns a list of (Q, G, grid, physics dict)."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        nx, ny = int(rng.choice(sizes)), int(rng.choice(sizes))
+        amp = float(10 ** rng.uniform(-3, -1))
+        if i < count // 2:
+            Q, G, grid = double_shear_layer(nx, ny, amp=amp)
+            phys = dict(mu=1.0 / 1e4, inviscid=False)
+        else:
+            st = np.stack([rng.uniform(0.1, 1.5, 4), rng.uniform(-1, 1, 4),
+                           rng.uniform(-1, 1, 4), rng.uniform(0.05, 1.5, 4)], axis=1)
+            Q, G, grid = riemann_quadrants(nx, ny, states=st, amp=amp, seed=seed0 + i)
+            phys = dict(mu=0.0, inviscid=True)
+        out.append((Q, G, grid, phys))
+    return out
 
 
 def perturb(Q, G=None, *, amp=1e-2, seed=0):

@@ -1,0 +1,179 @@
+"""Learned smoothness indicator (extension row a8): gradients of the GPU
+training kernels against the FP64 oracle, deterministic training, the
+never-skip limit equal to the plain path, and what the trained network
+gains (skipped GENO work, time) at what cost (error against the method
+without it)."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_19911_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2508_19911_gb300 import gks, indicator
+    gks.lib()
+    return torch, torch.device("cuda:0"), gks, indicator
+
+
+@pytest.fixture(scope="module")
+def trained(env):
+    torch, dev, gks, ind = env
+    x, y, stats = ind.training_set(dev, n=32)
+    params, hist = ind.train(x, y, epochs=6, seed=1)
+    return x, y, stats, params, hist
+
+
+def test_mlp_gradient_matches_oracle(env):
+    torch, dev, gks, ind = env
+    rng = np.random.default_rng(5)
+    npar = gks.mlp_nparams()
+    params = (rng.normal(scale=0.3, size=npar)).astype(np.float32)
+    n = 333
+    x = (rng.normal(size=(63, n)) * rng.uniform(0.01, 10, n)).astype(np.float32)
+    y = (rng.uniform(size=n) > 0.4).astype(np.float32)
+    loss, grad = gks.mlp_loss_grad(torch.tensor(params, device=dev), torch.tensor(x, device=dev),
+                                   torch.tensor(y, device=dev), neg_weight=3.0)
+    lo, go = oracle.mlp_loss_grad(params.astype(np.float64), x.astype(np.float64),
+                                  y.astype(np.float64), neg_weight=3.0)
+    assert loss == pytest.approx(lo, rel=1e-5)
+    g = grad.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(g, go, rtol=0, atol=2e-5 * np.abs(go).max())
+
+
+def test_training_is_deterministic_and_reduces_loss(env, trained):
+    torch, dev, gks, ind = env
+    x, y, stats, params, hist = trained
+    assert hist[-1] < hist[0]
+    p2, h2 = ind.train(x, y, epochs=6, seed=1)
+    assert torch.equal(params, p2)
+    assert np.array_equal(hist, h2)
+    # the data covers both classes
+    assert 0.0 < float(y.mean()) < 1.0, stats
+
+
+def test_dump_labels_on_known_flows(env):
+    torch, dev, gks, ind = env
+    # uniform flow: every data vector is zero, chi = 1
+    grid = wl.Grid((6, 6, 6), (1.0, 1.0, 1.0))
+    Q = np.zeros((5, 6, 6, 6))
+    Q[0], Q[1], Q[4] = 1.0, 0.3, 2.5 + 0.045
+    G = np.zeros((5, 3, 6, 6, 6))
+    s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision="mixed"))
+    x, chi, y = s.indicator_dump(torch.tensor(Q, device=dev), torch.tensor(G, device=dev))
+    assert torch.all(chi == 1.0) and torch.all(y == 1.0) and torch.all(x == 0.0)
+    # a contact discontinuity: the cells next to the jump need GENO
+    Q, G, grid = wl.double_sod(32)
+    s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision="mixed", inviscid=True))
+    x, chi, y = s.indicator_dump(torch.tensor(Q, device=dev), torch.tensor(G, device=dev))
+    rho_chi = chi.view(-1, 5)[:, 0].cpu().numpy()
+    assert rho_chi[7] < 0.01 and rho_chi[8] < 0.01     # the jump at x = 0.5 (cells 7 | 8)
+    assert rho_chi[3] == 1.0                           # far from both jumps
+
+
+def test_never_skipping_indicator_equals_plain_path(env, trained):
+    torch, dev, gks, ind = env
+    x, y, stats, params, hist = trained
+    Q, G, grid = wl.taylor_green((20, 18, 16))
+    Q, G = wl.perturb(Q, G, amp=0.02, seed=31)
+    Qd, Gd = torch.tensor(Q, device=dev), torch.tensor(G, device=dev)
+    plain = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision="mixed"))
+    learned = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision="mixed",
+                                    indicator=True))
+    learned.set_indicator(params.cpu().numpy(), theta=1.0)
+    a = plain.reconstruct(Qd, Gd)
+    b = learned.reconstruct(Qd, Gd)
+    assert torch.equal(a, b)
+    assert learned.indicator_skips() == 0
+
+
+def _ke(Q):
+    return 0.5 * (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0]
+
+
+def _ke_err(a, b):
+    return float(np.sqrt(((_ke(a) - _ke(b)) ** 2).sum()) / np.sqrt((_ke(b) ** 2).sum()))
+
+
+def _run(env, params, Q, G, grid, kw, steps, learned):
+    torch, dev, gks, ind = env
+    s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision="mixed",
+                              indicator=learned, **kw))
+    if learned:
+        s.set_indicator(params.cpu().numpy(), theta=ind.THETA)
+    Qd, Gd = torch.tensor(Q, device=dev), torch.tensor(G, device=dev)
+    s.step(Qd, Gd, nsteps=steps)
+    skips = s.indicator_skips() if learned else 0
+    return Qd.cpu().numpy(), skips / (steps * 2 * 5 * Q[0].size)
+
+
+def _recon_ms(env, params, Q, G, grid, learned, reps=10):
+    torch, dev, gks, ind = env
+    s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision="mixed",
+                              indicator=learned))
+    if learned:
+        s.set_indicator(params.cpu().numpy(), theta=ind.THETA)
+    Qd, Gd = torch.tensor(Q, device=dev), torch.tensor(G, device=dev)
+    fs = s.reconstruct(Qd, Gd)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        s.reconstruct(Qd, Gd, out=fs)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def test_indicator_gain_and_error(env, trained):
+    """What the trained network gains over the method without it at the
+    default threshold: the fraction of (cell, variable) reconstructions that
+    skip GENO and the reconstruction time, at a kinetic-energy error of at
+    most 1e-5 (relative L2 after 20 steps) against the plain nonlinear mixed
+    path. Held-out workloads: Taylor-Green 48^3; isotropic turbulence 64^3
+    at the resolution of the 256^3, k0 = 8 workload (k0 = 2, Mt = 0.5, a
+    seed not used in training); and 2D four-quadrant Riemann problems on
+    256^2 (uniform quadrants, where GENO's chi is 1)."""
+    torch, dev, gks, ind = env
+    x, y, stats, params, hist = trained
+    xt, yt, _ = ind.training_set(dev, n=24, seed=202)
+    cls = ind.evaluate(params, xt, yt)
+    assert cls["false_skip_rate"] < 0.01, cls
+
+    res = {}
+    Q, G, grid = wl.taylor_green(48)
+    kw = dict(mu=1.0 / 1600)
+    plain, _ = _run(env, params, Q, G, grid, kw, 20, False)
+    learned, frac = _run(env, params, Q, G, grid, kw, 20, True)
+    res["tgv48"] = (frac, _ke_err(learned, plain))
+
+    Q, G, grid, _ = wl.isotropic_turbulence(64, Mt=0.5, k0=2.0, seed=303)
+    kw = dict(mu=1e-3)
+    plain, _ = _run(env, params, Q, G, grid, kw, 20, False)
+    learned, frac = _run(env, params, Q, G, grid, kw, 20, True)
+    res["hit64"] = (frac, _ke_err(learned, plain))
+    times = {"hit64": (_recon_ms(env, params, Q, G, grid, False),
+                       _recon_ms(env, params, Q, G, grid, True))}
+
+    rng = np.random.default_rng(404)
+    st = np.stack([rng.uniform(0.3, 1.5, 4), rng.uniform(-0.5, 0.5, 4),
+                   rng.uniform(-0.5, 0.5, 4), rng.uniform(0.3, 1.5, 4)], axis=1)
+    Q, G, grid = wl.riemann_quadrants(256, 256, states=st, amp=0.0, seed=5)
+    kw = dict(mu=0.0, inviscid=True)
+    plain, _ = _run(env, params, Q, G, grid, kw, 20, False)
+    learned, frac = _run(env, params, Q, G, grid, kw, 20, True)
+    rho_err = float(np.abs(learned[0] - plain[0]).sum() / np.abs(plain[0]).sum())
+    res["riemann256"] = (frac, _ke_err(learned, plain), rho_err)
+    times["riemann256"] = (_recon_ms(env, params, Q, G, grid, False),
+                           _recon_ms(env, params, Q, G, grid, True))
+    print(f"indicator: (skip fraction, KE err[, rho L1 err]) {res}; recon ms (plain, learned) "
+          f"{times}; held-out {cls}; training label-1 fractions {stats}")
+    assert res["tgv48"][1] < 1e-5 and res["hit64"][1] < 1e-5
+    assert res["riemann256"][0] > 0.3 and res["riemann256"][2] < 1e-3
