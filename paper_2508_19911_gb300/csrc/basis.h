@@ -104,8 +104,129 @@ constexpr float kMlpDelta = 1e-30f;
 constexpr int kColFace = 0, kColEdge = 6, kColFaceGrad = 18, kColEdgeGrad = 36,
               kColCentreGrad = 60;
 
+// ---- reflection structure of the data vector ---------------------------
+// The stencil and the least-squares problem are invariant under the eight
+// reflections x_j -> -x_j (s: bit j set when axis j is reflected). A
+// reflection maps data column k to a column of the same kind at the
+// mirrored site, times a sign: +1 for averages and for the in-plane edge
+// combination, s_j for a derivative along axis j. Symmetrising each orbit
+// of columns with the characters of the group gives 63 combinations
+// d^s_r = sum_m T[r][m] d_m (T[r][m] in {-1, 0, 1}) of definite parity
+// class; R then maps class-c combinations only to class-c monomials, so
+// a = R d is 303 products instead of 34 x 63.
+GKS_HD constexpr int data_kind(int k) {  // 0 average, 1 derivative, 2 edge in-plane
+    return k < kColFaceGrad ? 0 : (k < kColEdgeGrad ? 1 : (k < kColCentreGrad ? ((k - kColEdgeGrad) % 2 ? 1 : 2) : 1));
+}
+// derivative axis of a kind-1 column
+GKS_HD constexpr int data_axis(int k) {
+    return k < kColEdgeGrad ? (k - kColFaceGrad) % 3
+                            : (k < kColCentreGrad ? edge_axis_e((k - kColEdgeGrad) / 2) : k - kColCentreGrad);
+}
+GKS_HD constexpr int data_off(int k, int j) {
+    return k < kColEdge ? face_off(k, j)
+         : k < kColFaceGrad ? edge_off(k - kColEdge, j)
+         : k < kColEdgeGrad ? face_off((k - kColFaceGrad) / 3, j)
+         : k < kColCentreGrad ? edge_off((k - kColEdgeGrad) / 2, j) : 0;
+}
+GKS_HD constexpr int refl(int s, int j) { return (s >> j) & 1 ? -1 : 1; }
+// column reached from k by reflection s
+GKS_HD constexpr int data_reflect(int k, int s) {
+    for (int m = 0; m < kNumData; ++m) {
+        if (data_kind(m) != data_kind(k)) continue;
+        if (data_kind(k) == 1 && data_axis(m) != data_axis(k)) continue;
+        bool same = true;
+        for (int j = 0; j < 3; ++j)
+            if (data_off(m, j) != refl(s, j) * data_off(k, j)) same = false;
+        if (same) return m;
+    }
+    return -1;
+}
+GKS_HD constexpr int data_reflect_sign(int k, int s) {
+    return data_kind(k) == 1 ? refl(s, data_axis(k)) : 1;
+}
+struct SymTable {
+    int cls[kNumData];     // parity class of combination r
+    int nm[kNumData];      // its number of columns (1, 2 or 4)
+    int mem[kNumData][8];  // the columns
+    int sgn[kNumData][8];  // their signs T[r][m]
+    int orbit[kNumData];   // first combination of r's orbit
+};
+constexpr SymTable make_sym_table() {
+    SymTable t{};
+    bool seen[kNumData] = {};
+    int r = 0;
+    for (int k = 0; k < kNumData; ++k) {
+        if (seen[k]) continue;
+        const int first = r;
+        for (int s = 0; s < 8; ++s) seen[data_reflect(k, s)] = true;
+        for (int c = 0; c < 8; ++c) {
+            int coef[kNumData] = {};
+            for (int s = 0; s < 8; ++s) {
+                int chi = 1;
+                for (int j = 0; j < 3; ++j)
+                    if ((c >> j) & 1) chi *= refl(s, j);
+                coef[data_reflect(k, s)] += chi * data_reflect_sign(k, s);
+            }
+            int n = 0;
+            for (int m = 0; m < kNumData; ++m)
+                if (coef[m] != 0) {
+                    t.mem[r][n] = m;
+                    t.sgn[r][n] = coef[m] > 0 ? 1 : -1;
+                    ++n;
+                }
+            if (n == 0) continue;
+            t.cls[r] = c;
+            t.nm[r] = n;
+            t.orbit[r] = first;
+            ++r;
+        }
+    }
+    return t;
+}
+constexpr SymTable kSym = make_sym_table();
+// basis monomials of each parity class, in order: kClassMember[c][j]
+constexpr int kMaxClass = 9;
+struct ClassTable {
+    int n[8];
+    int member[8][kMaxClass];
+    int pos[kNumBasis];  // position of monomial i within its class
+};
+constexpr ClassTable make_class_table() {
+    ClassTable t{};
+    for (int i = 0; i < kNumBasis; ++i) {
+        const int c = parity_class(kExp[i][0], kExp[i][1], kExp[i][2]);
+        t.pos[i] = t.n[c];
+        t.member[c][t.n[c]++] = i;
+    }
+    return t;
+}
+constexpr ClassTable kClass = make_class_table();
+constexpr bool sym_table_ok() {
+    int covered[kNumData] = {};
+    int per_class[8] = {};
+    for (int r = 0; r < kNumData; ++r) {
+        if (kSym.nm[r] < 1 || kSym.nm[r] > 8) return false;
+        for (int q = 0; q < kSym.nm[r]; ++q) covered[kSym.mem[r][q]] += 1;
+        per_class[kSym.cls[r]] += 1;
+    }
+    for (int m = 0; m < kNumData; ++m)
+        if (covered[m] < 1) return false;
+    for (int c = 0; c < 8; ++c)
+        if (kClass.n[c] > kMaxClass) return false;
+    // every combination of an orbit uses the orbit's columns, in one order
+    for (int r = 0; r < kNumData; ++r) {
+        const int f = kSym.orbit[r];
+        if (kSym.nm[r] != kSym.nm[f]) return false;
+        for (int q = 0; q < kSym.nm[r]; ++q)
+            if (kSym.mem[r][q] != kSym.mem[f][q]) return false;
+    }
+    return true;
+}
+static_assert(sym_table_ok(), "reflection table of the data vector is incomplete");
+
 struct ReconTables {
     double R[kNumBasis][kNumData];      // coefficients a = R d
+    double Rs[kNumData][kMaxClass];     // a_{class(r), j} += Rs[r][j] d^s_r
     double H[kNumBasis][kNumBasis];     // IS_H = a^T H a
     double mean[kNumBasis];             // mean of delta^d/d! over Omega_0
     double mval[3][kNumBasis];          // |value| factors at the Gauss points

@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace gks {
 namespace {
@@ -190,6 +191,42 @@ __device__ __forceinline__ void time_integrals_pair(double dt, double tau, doubl
     }
 }
 
+// Coefficients of terms 2..6 (k = 1..5) in F^n = sum_k al_k X_k and
+// F_t = sum_k be_k X_k, al_k = (4 C_k(dt/2) - C_k(dt))/dt, be_k =
+// 4 (C_k(dt) - 2 C_k(dt/2))/dt^2. For dt >= 2 tau they are written out in
+// b = exp(-dt/(2 tau)) and a = 1 - b (>= 1 - 1/e: no cancellation),
+// e.g. al_4 = tau a (3 - b)/dt, be_4 = -4 tau a^2/dt^2; otherwise they
+// come from the time integrals (Taylor series for small dt/tau).
+__device__ __forceinline__ void time_coefficients(double dt, double tau, double al[6], double be[6]) {
+    if (tau > 0.0 && dt >= 2.0 * tau) {
+        const double b = exp(-0.5 * dt / tau), a = 1.0 - b;
+        const double idt = 1.0 / dt;
+        const double t2 = tau * tau;
+        const double g = a * (3.0 - b) * idt;          // (4 E_h - E)/dt
+        const double h = 4.0 * a * a * idt * idt;      // -4 (E - 2 E_h)/dt^2
+        al[1] = 2.0 * t2 * g - tau * (1.0 + 2.0 * b - b * b);
+        be[1] = 4.0 * tau * a * (b * dt - 2.0 * tau * a) * idt * idt;
+        al[2] = t2 * g - tau;
+        be[2] = 1.0 - t2 * h;
+        al[3] = tau * g;
+        be[3] = -tau * h;
+        al[4] = tau * b * (2.0 - b) - 2.0 * t2 * g;
+        be[4] = -be[1];
+        al[5] = -t2 * g;
+        be[5] = t2 * h;
+    } else {
+        double cA[6], cH[6];
+        time_integrals(dt, tau, cA);
+        time_integrals(0.5 * dt, tau, cH);
+        const double idt = 1.0 / dt, idt2 = idt * idt;
+#pragma unroll
+        for (int k = 1; k < 6; ++k) {
+            al[k] = (4.0 * cH[k] - cA[k]) * idt;
+            be[k] = 4.0 * (cA[k] - 2.0 * cH[k]) * idt2;
+        }
+    }
+}
+
 template <typename T>
 struct PrimT {
     T rho, U, V, W, p, lam;
@@ -206,13 +243,6 @@ __device__ __forceinline__ Prim to_prim(const double *s, double gamma) {
     P.p = (gamma - 1.0) * (s[4] - 0.5 * P.rho * (P.U * P.U + P.V * P.V + P.W * P.W));
     P.lam = 0.5 * P.rho / P.p;
     return P;
-}
-
-__device__ __forceinline__ PrimT<float> to_float(const Prim &P) {
-    PrimT<float> f;
-    f.rho = (float)P.rho; f.U = (float)P.U; f.V = (float)P.V; f.W = (float)P.W;
-    f.p = (float)P.p; f.lam = (float)P.lam;
-    return f;
 }
 
 // Contribution of one side (SGN = +1: left state over u > 0; -1: right
@@ -331,13 +361,11 @@ __device__ __forceinline__ void equilibrium_terms(const PrimT<T> &Z, T N, const 
     q[2] = heat(X[2], Y, Z.U, Z.V, Z.W);
 }
 
-// W0 = rho_l <psi>_{u>0} + rho_r <psi>_{u<0} (FP64), the half-line
-// starting moments of both sides and, if asked, the term-4 flux moments
-// X4 = rho_l <u psi>_{u>0} + rho_r <u psi>_{u<0} (FP64)
-template <bool kX4>
+// W0 = rho_l <psi>_{u>0} + rho_r <psi>_{u<0} and the half-line starting
+// moments of both sides
 __device__ __forceinline__ void interface_state(const Prim &L, const Prim &R, double N,
-                                                double W0[5], double X4[5], double &ul0,
-                                                double &ul1, double &ur0, double &ur1) {
+                                                double W0[5], double &ul0, double &ul1,
+                                                double &ur0, double &ur1) {
     half_start(L.U, L.lam, 1.0, ul0, ul1);
     half_start(R.U, R.lam, -1.0, ur0, ur1);
     double u[4], v[3], w[3], o[5];
@@ -348,32 +376,18 @@ __device__ __forceinline__ void interface_state(const Prim &L, const Prim &R, do
     psi_m<0, 0, 0>(u, v, w, N * il, o);
 #pragma unroll
     for (int i = 0; i < 5; ++i) W0[i] = L.rho * o[i];
-    if (kX4) {
-        psi_m<1, 0, 0>(u, v, w, N * il, o);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) X4[i] = L.rho * o[i];
-    }
     half_line<4>(R.U, ir, ur0, ur1, u);
     full_line<3>(R.V, ir, v);
     full_line<3>(R.W, ir, w);
     psi_m<0, 0, 0>(u, v, w, N * ir, o);
 #pragma unroll
     for (int i = 0; i < 5; ++i) W0[i] += R.rho * o[i];
-    if (kX4) {
-        psi_m<1, 0, 0>(u, v, w, N * ir, o);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) X4[i] += R.rho * o[i];
-    }
 }
 
 // collision time (Sec. 4) and F^n, F_t^n from the six term moments
-// (X1, X4: optional FP64 replacements of terms 1 and 4, whose time
-// coefficients are large and cancel in F_t: beta_1 + beta_4 = 0)
-template <typename TX>
 __device__ __forceinline__ void combine_terms(const PhysParams &P, const Prim &L, const Prim &R,
-                                              const Prim &Z, double dt, const TX X[6][5],
-                                              const TX q[6], const double X1[5], const double X4[5],
-                                              double out[10], double &dpr) {
+                                              const Prim &Z, double dt, const double X[6][5],
+                                              const double q[6], double out[10], double &dpr) {
     dpr = fabs((L.p - R.p) / (L.p + R.p));
     const double tau = P.inviscid ? (P.eps_tau * dt + P.C_tau * dpr * dt)
                                   : (viscosity(P, Z.rho, Z.p) / Z.p + P.C_tau * dpr * dt);
@@ -390,12 +404,11 @@ __device__ __forceinline__ void combine_terms(const PhysParams &P, const Prim &L
         const double be = 4.0 * (cA[k] - 2.0 * cH[k]) * idt2;
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            const double x = (k == 0 && X1) ? X1[i] : ((k == 3 && X4) ? X4[i] : (double)X[k][i]);
-            out[i] += al * x;
-            out[5 + i] += be * x;
+            out[i] += al * X[k][i];
+            out[5 + i] += be * X[k][i];
         }
-        qn += al * (double)q[k];
-        qt += be * (double)q[k];
+        qn += al * q[k];
+        qt += be * q[k];
     }
     out[4] += prfix * qn;
     out[9] += prfix * qt;
@@ -423,7 +436,7 @@ __device__ void flux_point(const PhysParams &P, const double *sl, const double *
         return;
     }
     double W0[5], ul0, ul1, ur0, ur1;
-    interface_state<false>(L, R, N, W0, nullptr, ul0, ul1, ur0, ur1);
+    interface_state(L, R, N, W0, ul0, ul1, ur0, ur1);
     const Prim Z = to_prim(W0, P.gamma);
     if (!(Z.rho > 0.0 && Z.p > 0.0)) {
         flag_status(status, kStatusNonphysical);
@@ -444,7 +457,7 @@ __device__ void flux_point(const PhysParams &P, const double *sl, const double *
     side_terms<-1>(sr + 5, R, N, ur0, ur1, Z.U, Z.V, Z.W, dW0, X[3], X[4], X[5], q + 3, dtWr);
     equilibrium_terms<true>(Z, N, dW0, X, q, dtW0);
     double dpr;
-    combine_terms<double>(P, L, R, Z, dt, X, q, nullptr, nullptr, out, dpr);
+    combine_terms(P, L, R, Z, dt, X, q, out, dpr);
     if (kInterface) {
         const double e = (P.C_tau * dpr > 0.0) ? exp(-1.0 / (P.C_tau * dpr)) : 0.0;
 #pragma unroll
@@ -457,44 +470,178 @@ __device__ void flux_point(const PhysParams &P, const double *sl, const double *
     }
 }
 
-// Mixed precision (FP32 core, FP64 shell): the states W_l, W_r, the
-// interface equilibrium W0 with its half-line moments, the Euler flux of
-// W0 (term 1) and the half-space fluxes of g_l, g_r (term 4) -- the two
-// terms that carry the pressure and whose large time coefficients cancel
-// in F_t -- the collision time, the time integrals, the combinations F^n,
-// F_t^n and the interface values are FP64; the Maxwellian slopes and the
-// moment compositions of terms 2, 3, 5, 6 (multiplied by coefficients of
-// order tau or tau^2/dt^2) are FP32.
+// ---- mixed precision: float-float shell, FP32 core ----------------------
+// Of the six terms of Eq. flux only three quantities need more than FP32:
+// the interface equilibrium W0 (its pressure enters the Euler flux), the
+// Euler flux X1 of W0 (term 1, which carries the pressure), and the
+// difference D = X1 - X4 with X4 the half-space flux of the initial states
+// (term 4): the time coefficients of terms 1 and 4 satisfy al1 + al4 = 1
+// and be1 + be4 = 0 exactly (the time functions c1 + c4 integrate to T), so
+//   F^n  = X1 - al4 D + sum_{k=2,3,5,6} al_k X_k,
+//   F_t^n =    - be4 D + sum_{k=2,3,5,6} be_k X_k,
+// and D is small where the flow is smooth. These three are computed in
+// float-float arithmetic (ff.cuh) from W = Q0 + offset; the half-line
+// starting values (erfc, exp) and the time integrals stay FP64, their
+// products with moments FP32; the slopes and moments of terms 2, 3, 5, 6
+// are the FP32 core shared with the FP32 part of the previous design.
+struct PrimFF {
+    ff rho, U, V, W, p, lam;
+};
+
+__device__ __forceinline__ ff ff_half(ff a) { return ff_make(0.5f * a.hi, 0.5f * a.lo); }
+
+__device__ __forceinline__ PrimFF to_prim_ff(const ff s[5], ff gm1) {
+    PrimFF P;
+    P.rho = s[0];
+    const ff ir = ff_recip(s[0]);
+    P.U = ff_mul(s[1], ir);
+    P.V = ff_mul(s[2], ir);
+    P.W = ff_mul(s[3], ir);
+    const ff q2 = ff_add(ff_add(ff_mul(P.U, P.U), ff_mul(P.V, P.V)), ff_mul(P.W, P.W));
+    P.p = ff_mul(gm1, ff_sub(s[4], ff_half(ff_mul(P.rho, q2))));
+    P.lam = ff_div(ff_half(P.rho), P.p);
+    return P;
+}
+
+// Half-line starting moments of one side (SGN = +1: u > 0; -1: u < 0):
+// with y = sqrt(lam) U, m0 = (1 + SGN erf(y))/2 and m1 = U m0 + SGN
+// e^{-y^2}/(2 sqrt(pi lam)). For |y| <= 1 (subsonic states) erf and the
+// exponential come from one series in t_n = (-y^2)^n/n!:
+// e^{-y^2} = sum t_n, erf(y) = 2y/sqrt(pi) sum t_n/(2n+1), in float-float
+// (|t_n| <= 1/n!: 18 terms reach 2^-50); otherwise the FP64 erfc and exp.
+constexpr int kSeriesTerms = 18;
+__device__ __forceinline__ ffc series_inv(int n) {  // 1/n, n = 1..18
+    constexpr ffc t[kSeriesTerms + 1] = {
+        ff_const(0.0), ff_const(1.0), ff_const(1.0 / 2), ff_const(1.0 / 3), ff_const(1.0 / 4),
+        ff_const(1.0 / 5), ff_const(1.0 / 6), ff_const(1.0 / 7), ff_const(1.0 / 8),
+        ff_const(1.0 / 9), ff_const(1.0 / 10), ff_const(1.0 / 11), ff_const(1.0 / 12),
+        ff_const(1.0 / 13), ff_const(1.0 / 14), ff_const(1.0 / 15), ff_const(1.0 / 16),
+        ff_const(1.0 / 17), ff_const(1.0 / 18)};
+    return t[n];
+}
+__device__ __forceinline__ ffc series_inv_odd(int n) {  // 1/(2n+1), n = 1..18
+    constexpr ffc t[kSeriesTerms + 1] = {
+        ff_const(1.0), ff_const(1.0 / 3), ff_const(1.0 / 5), ff_const(1.0 / 7), ff_const(1.0 / 9),
+        ff_const(1.0 / 11), ff_const(1.0 / 13), ff_const(1.0 / 15), ff_const(1.0 / 17),
+        ff_const(1.0 / 19), ff_const(1.0 / 21), ff_const(1.0 / 23), ff_const(1.0 / 25),
+        ff_const(1.0 / 27), ff_const(1.0 / 29), ff_const(1.0 / 31), ff_const(1.0 / 33),
+        ff_const(1.0 / 35), ff_const(1.0 / 37)};
+    return t[n];
+}
+
+template <int SGN>
+__device__ __forceinline__ void half_start_ff(const PrimFF &S, ff &m0, ff &m1) {
+    const ff sl = ff_sqrt(S.lam);
+    const ff y = ff_mul(sl, S.U);
+    if (fabsf(y.hi) <= 1.0f) {
+        const ff w = ff_neg(ff_mul(y, y));
+        ff t = ff_make(1.0f, 0.0f), se = t, sf = t;
+#pragma unroll
+        for (int n = 1; n <= kSeriesTerms; ++n) {
+            t = ff_mul(ff_mul(t, w), ff_of(series_inv(n)));
+            se = ff_add(se, t);
+            sf = ff_add(sf, ff_mul(t, ff_of(series_inv_odd(n))));
+            if (fabsf(t.hi) < 1e-16f) break;
+        }
+        constexpr ffc k2rpi = ff_const(1.1283791670955125739);   // 2/sqrt(pi)
+        constexpr ffc krpi = ff_const(0.56418958354775628695);   // 1/sqrt(pi)
+        const ff erf = ff_mul(ff_mul(y, ff_of(k2rpi)), sf);
+        m0 = ff_half(SGN > 0 ? ff_add_f(erf, 1.0f) : ff_sub(ff_make(1.0f, 0.0f), erf));
+        const ff edge = ff_half(ff_div(ff_mul(se, ff_of(krpi)), sl));
+        m1 = SGN > 0 ? ff_add(ff_mul(S.U, m0), edge) : ff_sub(ff_mul(S.U, m0), edge);
+    } else {
+        double d0, d1;
+        half_start(ff_to_double(S.U), ff_to_double(S.lam), (double)SGN, d0, d1);
+        m0 = ff_from_double(d0);
+        m1 = ff_from_double(d1);
+    }
+}
+
+// rho <psi> and rho <u psi> of one side over its half line, added to W0 and
+// X4; returns the half-line starting moments for the FP32 core
+template <int SGN>
+__device__ __forceinline__ void half_side_ff(const PrimFF &S, ff N, ff W0[5], ff X4[5],
+                                             float &m0f, float &m1f) {
+    ff u[4];
+    half_start_ff<SGN>(S, u[0], u[1]);
+    m0f = u[0].hi;
+    m1f = u[1].hi;
+    const ff inv2l = ff_half(ff_recip(S.lam));
+    u[2] = ff_add(ff_mul(S.U, u[1]), ff_mul(inv2l, u[0]));
+    u[3] = ff_add(ff_mul(S.U, u[2]), ff_mul(ff_add(inv2l, inv2l), u[1]));
+    // <v^2> + <w^2> + <xi^2> of the full lines
+    const ff s2 = ff_add(ff_add(ff_mul(S.V, S.V), ff_mul(S.W, S.W)),
+                         ff_mul(ff_add_f(N, 2.0f), inv2l));
+#pragma unroll
+    for (int A = 0; A < 2; ++A) {
+        ff o[5];
+        o[0] = u[A];
+        o[1] = u[A + 1];
+        o[2] = ff_mul(u[A], S.V);
+        o[3] = ff_mul(u[A], S.W);
+        o[4] = ff_half(ff_add(u[A + 2], ff_mul(u[A], s2)));
+        ff *acc = A == 0 ? W0 : X4;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) acc[i] = ff_add(acc[i], ff_mul(S.rho, o[i]));
+    }
+}
+
+__device__ __forceinline__ PrimT<float> prim_f(const PrimFF &P) {
+    PrimT<float> f;
+    f.rho = P.rho.hi; f.U = P.U.hi; f.V = P.V.hi; f.W = P.W.hi; f.p = P.p.hi; f.lam = P.lam.hi;
+    return f;
+}
+
+// One Gauss point's record in float-float: F^n, F_t^n and, with
+// kInterface, Q^l, dQ^l/dt, Q^r, dQ^r/dt (out[0..29], face frame); the
+// FP32 entries have lo = 0.
 template <bool kInterface>
-__device__ void flux_point_mixed(const PhysParams &P, const double Wl[5], const float dl[15],
-                                 const double Wr[5], const float dr[15], double dt,
-                                 double out[30], int *status) {
-    const double N = P.Nint;
-    const Prim L = to_prim(Wl, P.gamma), R = to_prim(Wr, P.gamma);
-    if (!(L.rho > 0.0 && L.p > 0.0 && R.rho > 0.0 && R.p > 0.0)) {
+__device__ void flux_point_mixed(const PhysParams &P, const double Ql[5], const float ol[5],
+                                 const float dl[15], const double Qr[5], const float orr[5],
+                                 const float dr[15], double dt, ff out[30], int *status) {
+    const ff gm1 = ff_from_double(P.gamma - 1.0);
+    const ff N = ff_from_double(P.Nint);
+    ff Wl[5], Wr[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        Wl[i] = ff_add_f(ff_from_double(Ql[i]), ol[i]);
+        Wr[i] = ff_add_f(ff_from_double(Qr[i]), orr[i]);
+    }
+    const PrimFF L = to_prim_ff(Wl, gm1), R = to_prim_ff(Wr, gm1);
+    if (!(L.rho.hi > 0.0f && L.p.hi > 0.0f && R.rho.hi > 0.0f && R.p.hi > 0.0f)) {
         flag_status(status, kStatusNonphysical);
 #pragma unroll
-        for (int i = 0; i < 30; ++i) out[i] = nan("");
+        for (int i = 0; i < 30; ++i) out[i] = ff_make(nanf(""), 0.0f);
         return;
     }
-    double W0[5], X4d[5], ul0, ul1, ur0, ur1;
-    interface_state<true>(L, R, N, W0, X4d, ul0, ul1, ur0, ur1);
-    const Prim Z = to_prim(W0, P.gamma);
-    if (!(Z.rho > 0.0 && Z.p > 0.0)) {
+    ff W0[5], X4[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) W0[i] = X4[i] = ff_make(0.0f, 0.0f);
+    float ul0, ul1, ur0, ur1;
+    half_side_ff<1>(L, N, W0, X4, ul0, ul1);
+    half_side_ff<-1>(R, N, W0, X4, ur0, ur1);
+    const PrimFF Z = to_prim_ff(W0, gm1);
+    if (!(Z.rho.hi > 0.0f && Z.p.hi > 0.0f)) {
         flag_status(status, kStatusNonphysical);
 #pragma unroll
-        for (int i = 0; i < 30; ++i) out[i] = nan("");
+        for (int i = 0; i < 30; ++i) out[i] = ff_make(nanf(""), 0.0f);
         return;
     }
-    // term 1: the Euler flux of W0, FP64
-    double X1[5];
+    // term 1: the Euler flux of W0; D = X1 - X4
+    ff X1[5];
     X1[0] = W0[1];
-    X1[1] = W0[1] * Z.U + Z.p;
-    X1[2] = W0[2] * Z.U;
-    X1[3] = W0[3] * Z.U;
-    X1[4] = (W0[4] + Z.p) * Z.U;
-    const float Nf = (float)N;
-    const PrimT<float> Lf = to_float(L), Rf = to_float(R), Zf = to_float(Z);
+    X1[1] = ff_add(ff_mul(W0[1], Z.U), Z.p);
+    X1[2] = ff_mul(W0[2], Z.U);
+    X1[3] = ff_mul(W0[3], Z.U);
+    X1[4] = ff_mul(ff_add(W0[4], Z.p), Z.U);
+    float D[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) D[i] = ff_sub(X1[i], X4[i]).hi;
+
+    // FP32 core: slopes and the moments of terms 2, 3, 5, 6 (and the heat
+    // fluxes for the Prandtl fix)
+    const float Nf = N.hi;
+    const PrimT<float> Lf = prim_f(L), Rf = prim_f(R), Zf = prim_f(Z);
     float dW0[3][5], X[6][5], q[6] = {0, 0, 0, 0, 0, 0}, dtWl[5], dtWr[5], dtW0[5];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
@@ -504,21 +651,56 @@ __device__ void flux_point_mixed(const PhysParams &P, const double Wl[5], const 
     for (int k = 0; k < 6; ++k)
 #pragma unroll
         for (int i = 0; i < 5; ++i) X[k][i] = 0.0f;
-    side_terms<1>(dl, Lf, Nf, (float)ul0, (float)ul1, Zf.U, Zf.V, Zf.W, dW0, X[3], X[4], X[5],
-                  q + 3, dtWl);
-    side_terms<-1>(dr, Rf, Nf, (float)ur0, (float)ur1, Zf.U, Zf.V, Zf.W, dW0, X[3], X[4], X[5],
-                   q + 3, dtWr);
+    side_terms<1>(dl, Lf, Nf, ul0, ul1, Zf.U, Zf.V, Zf.W, dW0, X[3], X[4], X[5], q + 3, dtWl);
+    side_terms<-1>(dr, Rf, Nf, ur0, ur1, Zf.U, Zf.V, Zf.W, dW0, X[3], X[4], X[5], q + 3, dtWr);
     equilibrium_terms<false>(Zf, Nf, dW0, X, q, dtW0);  // a Maxwellian carries no heat flux: q1 = 0
-    double dpr;
-    combine_terms<float>(P, L, R, Z, dt, X, q, X1, X4d, out, dpr);
+
+    // collision time (Sec. 4) and time coefficients, FP64; then FP32
+    const float dpr = fabsf(ff_sub(L.p, R.p).hi / ff_add(L.p, R.p).hi);
+    const double zp = ff_to_double(Z.p);
+    const double tau = P.inviscid
+                           ? (P.eps_tau * dt + P.C_tau * (double)dpr * dt)
+                           : (viscosity(P, ff_to_double(Z.rho), zp) / zp + P.C_tau * (double)dpr * dt);
+    double ald[6], bed[6];
+    time_coefficients(dt, tau, ald, bed);
+    float al[6], be[6];
+#pragma unroll
+    for (int k = 1; k < 6; ++k) {
+        al[k] = (float)ald[k];
+        be[k] = (float)bed[k];
+    }
+    const float prfix = (float)(1.0 / P.Pr - 1.0);
+    float qn = 0.0f, qt = 0.0f;
+#pragma unroll
+    for (int k = 1; k < 6; ++k) {
+        qn = fmaf(al[k], q[k], qn);
+        qt = fmaf(be[k], q[k], qt);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        float cf = -al[3] * D[i], ct = -be[3] * D[i];
+#pragma unroll
+        for (int k = 1; k < 6; ++k) {
+            if (k == 3) continue;
+            cf = fmaf(al[k], X[k][i], cf);
+            ct = fmaf(be[k], X[k][i], ct);
+        }
+        if (i == 4) {
+            cf = fmaf(prfix, qn, cf);
+            ct = fmaf(prfix, qt, ct);
+        }
+        out[i] = ff_add_f(X1[i], cf);
+        out[5 + i] = ff_make(ct, 0.0f);
+    }
     if (kInterface) {
-        const double e = (P.C_tau * dpr > 0.0) ? exp(-1.0 / (P.C_tau * dpr)) : 0.0;
+        const float cd = (float)P.C_tau * dpr;
+        const float e = cd > 0.0f ? expf(-1.0f / cd) : 0.0f;
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            out[10 + i] = (1.0 - e) * W0[i] + e * Wl[i];
-            out[15 + i] = (1.0 - e) * (double)dtW0[i] + e * (double)dtWl[i];
-            out[20 + i] = (1.0 - e) * W0[i] + e * Wr[i];
-            out[25 + i] = (1.0 - e) * (double)dtW0[i] + e * (double)dtWr[i];
+            out[10 + i] = ff_add_f(W0[i], e * ff_sub(Wl[i], W0[i]).hi);
+            out[15 + i] = ff_make((1.0f - e) * dtW0[i] + e * dtWl[i], 0.0f);
+            out[20 + i] = ff_add_f(W0[i], e * ff_sub(Wr[i], W0[i]).hi);
+            out[25 + i] = ff_make((1.0f - e) * dtW0[i] + e * dtWr[i], 0.0f);
         }
     }
 }
@@ -546,8 +728,9 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const PhysPar
     const long long left = cell_index(g, d == 0 ? wrap(i - 1, g.nx) : i,
                                       d == 1 ? wrap(j - 1, g.ny) : j,
                                       d == 2 ? wrap(kk - 1, g.nz) : kk);
-    double out[30];
+    constexpr int NV = kCGKS ? 30 : 10;
     if (!MIXED) {
+        double out[30];
         const double *fs = (const double *)fsv;
         double sl[20], sr[20];
         const double *pl = fs + ((long long)((2 * d + 1) * K + k) * 20) * n + left;
@@ -558,42 +741,74 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const PhysPar
             sr[q] = __ldg(pr + (long long)q * n);
         }
         flux_point<kCGKS>(P, sl, sr, dt, out, valid ? status : nullptr);
+        if (kCGKS) {
+            // Gauss-point average: butterfly over the four lanes of the face
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                double s = out[q] + __shfl_xor_sync(0xffffffffu, out[q], 1);
+                s = s + __shfl_xor_sync(0xffffffffu, s, 2);
+                out[q] = 0.25 * s;
+            }
+        }
+        if (!valid) return;
+        // face frame -> global frame; lane k writes the values with q % K == k
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            if (q % K != k) continue;
+            const int blk = q / 5, cmp = q % 5;
+            frec[((long long)d * 30 + blk * 5 + global_var(cmp, d)) * n + c] = out[q];
+        }
     } else {
+        ff out[30];
         const float *fs = (const float *)fsv;
-        double Wl[5], Wr[5];
-        float dl[15], dr[15];
+        double Ql[5], Qr[5];
+        float ol[5], orr[5], dl[15], dr[15];
         const float *pl = fs + ((long long)((2 * d + 1) * K + k) * 20) * n + left;
         const float *pr = fs + ((long long)((2 * d) * K + k) * 20) * n + c;
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             const int v = global_var(q, d);
-            Wl[q] = __ldg(Q + (long long)v * n + left) + (double)__ldg(pl + (long long)q * n);
-            Wr[q] = __ldg(Q + (long long)v * n + c) + (double)__ldg(pr + (long long)q * n);
+            Ql[q] = __ldg(Q + (long long)v * n + left);
+            Qr[q] = __ldg(Q + (long long)v * n + c);
+            ol[q] = __ldg(pl + (long long)q * n);
+            orr[q] = __ldg(pr + (long long)q * n);
         }
 #pragma unroll
         for (int q = 0; q < 15; ++q) {
             dl[q] = __ldg(pl + (long long)(5 + q) * n);
             dr[q] = __ldg(pr + (long long)(5 + q) * n);
         }
-        flux_point_mixed<kCGKS>(P, Wl, dl, Wr, dr, dt, out, valid ? status : nullptr);
-    }
-    constexpr int NV = kCGKS ? 30 : 10;
-    if (kCGKS) {
-        // Gauss-point average: butterfly over the four lanes of the face
+        flux_point_mixed<kCGKS>(P, Ql, ol, dl, Qr, orr, dr, dt, out, valid ? status : nullptr);
+        if (kCGKS) {
+            // Gauss-point average in float-float (the FP32 entries have lo = 0)
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            double s = out[q] + __shfl_xor_sync(0xffffffffu, out[q], 1);
-            s = s + __shfl_xor_sync(0xffffffffu, s, 2);
-            out[q] = 0.25 * s;
+            for (int q = 0; q < NV; ++q) {
+                ff s = ff_add(out[q], ff_make(__shfl_xor_sync(0xffffffffu, out[q].hi, 1),
+                                              __shfl_xor_sync(0xffffffffu, out[q].lo, 1)));
+                s = ff_add(s, ff_make(__shfl_xor_sync(0xffffffffu, s.hi, 2),
+                                      __shfl_xor_sync(0xffffffffu, s.lo, 2)));
+                out[q] = ff_make(0.25f * s.hi, 0.25f * s.lo);  // exact
+            }
         }
-    }
-    if (!valid) return;
-    // face frame -> global frame; lane k writes the values with q % K == k
+        if (!valid) return;
+        // lane k converts and writes the values q = 4j + k only (chosen with
+        // selects, so that the four lanes of a face do not diverge)
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        if (q % K != k) continue;
-        const int blk = q / 5, cmp = q % 5;
-        frec[((long long)d * 30 + blk * 5 + global_var(cmp, d)) * n + c] = out[q];
+        for (int jq = 0; jq < (NV + K - 1) / K; ++jq) {
+            ff x = out[K * jq];
+            int q = K * jq;
+#pragma unroll
+            for (int kq = 1; kq < K; ++kq) {
+                if (K * jq + kq < NV && k == kq) {
+                    x = out[K * jq + kq];
+                    q = K * jq + kq;
+                }
+            }
+            if (q < NV && (K == 1 || q % K == k)) {
+                const int blk = q / 5, cmp = q % 5;
+                frec[((long long)d * 30 + blk * 5 + global_var(cmp, d)) * n + c] = ff_to_double(x);
+            }
+        }
     }
 }
 

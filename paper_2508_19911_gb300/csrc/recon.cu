@@ -40,6 +40,7 @@ __device__ __forceinline__ void static_for(F &&f) {
 }
 
 __constant__ double cR[kNumBasis][kNumData];
+__constant__ double cRs[kNumData][kMaxClass];  // R in the symmetrised data basis
 __constant__ double cH[kNumBasis][kNumBasis];
 __constant__ double cMean[kNumBasis];
 __constant__ double cMval[3][kNumBasis];
@@ -50,8 +51,9 @@ __constant__ double cMder[3][3][kNumBasis];
 // floats, each section 16-byte aligned; kPad pads the 34 basis
 // coefficients to a multiple of four.
 constexpr int kPad = 36;
-constexpr int kTabR = 0;                                  // [63][kPad]: column c of R
-constexpr int kTabMval = kTabR + kNumData * kPad;         // [3][kPad]
+constexpr int kPadS = 12;                                 // kMaxClass padded to a float4 multiple
+constexpr int kTabRs = 0;                                 // [63][kPadS]: class block of R per combination
+constexpr int kTabMval = kTabRs + kNumData * kPadS;       // [3][kPad]
 constexpr int kTabMder = kTabMval + 3 * kPad;             // [3][3][kPad]
 constexpr int kTabH = kTabMder + 9 * kPad;                // [34][kPad]
 constexpr int kTabMean = kTabH + kNumBasis * kPad;        // [kPad]
@@ -60,6 +62,7 @@ constexpr int kTabB1 = kTabW1 + kNumData * kMlpHidden;    // [kMlpHidden]
 constexpr int kTabW2 = kTabB1 + kMlpHidden;               // [kMlpHidden]
 constexpr int kTabB2 = kTabW2 + kMlpHidden;               // b2, logit(theta), 2 unused
 constexpr int kTabFloats = kTabB2 + 4;
+static_assert(kMaxClass <= kPadS && kPadS % 4 == 0, "class block padding");
 static_assert(kTabMval % 4 == 0 && kTabMder % 4 == 0 && kTabH % 4 == 0 && kTabMean % 4 == 0 &&
                   kTabW1 % 4 == 0 && kMlpHidden % 4 == 0 && kTabFloats % 4 == 0,
               "sections of the FP32 table must be float4 aligned");
@@ -86,65 +89,63 @@ __device__ __forceinline__ void stage_tables(float *sT) {
 constexpr double kG = 0.28867513459481288225;     // 1/(2 sqrt 3)
 constexpr double kRs2 = 0.70710678118654752440;   // 1/sqrt 2
 
-template <int COL>
-__device__ __forceinline__ void add_column(double a[kNumBasis], double x) {
-#pragma unroll
-    for (int i = 0; i < kNumBasis; ++i) a[i] = fma(cR[i][COL], x, a[i]);
-}
-
 // face-frame component of conserved variable v on a face normal to axis d
 __device__ __forceinline__ int frame_comp(int v, int d) {
     return (v == 0 || v == 4) ? v : 1 + (v - 1 - d + 3) % 3;
 }
 
-template <int D, int SIDE, int KK>
-__device__ __forceinline__ void write_point(double *__restrict__ fs, long long n, long long c,
-                                            int v, const double S[8], const double Dq[3][8],
-                                            double base, double chi, const double bbar[3],
-                                            double q0, bool nonlinear, const double h[3]) {
-    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-    constexpr double sD = SIDE ? 1.0 : -1.0;
-    constexpr double s1 = (KK & 1) ? 1.0 : -1.0;
-    constexpr double s2 = (KK & 2) ? 1.0 : -1.0;
-    double sg[3];
-    sg[D] = sD;
-    sg[T1] = s1;
-    sg[T2] = s2;
-    double val = base, der[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int cls = 0; cls < 8; ++cls) {
-        const double sign = ((cls & 1) ? sg[0] : 1.0) * ((cls & 2) ? sg[1] : 1.0) *
-                            ((cls & 4) ? sg[2] : 1.0);
-        val += sign * S[cls];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) der[q] += sign * Dq[q][cls];
+// Value of data column K for one (cell, variable) (layout in basis.h)
+template <int K>
+__device__ __forceinline__ double data_col(const double *__restrict__ Qv,
+                                           const double *__restrict__ Gv, long long n, long long c,
+                                           const long long nbF[6], const long long nbE[12],
+                                           double q0, const double h[3]) {
+    if constexpr (K < kColEdge) {
+        return __ldg(Qv + nbF[K]) - q0;
+    } else if constexpr (K < kColFaceGrad) {
+        return __ldg(Qv + nbE[K - kColEdge]) - q0;
+    } else if constexpr (K < kColEdgeGrad) {
+        constexpr int m = (K - kColFaceGrad) / 3, j = (K - kColFaceGrad) % 3;
+        return h[j] * __ldg(Gv + j * n + nbF[m]);
+    } else if constexpr (K < kColCentreGrad) {
+        constexpr int e = (K - kColEdgeGrad) / 2;
+        constexpr int ea = edge_axis_a(e), eb = edge_axis_b(e), ee = edge_axis_e(e);
+        if constexpr ((K - kColEdgeGrad) % 2 == 0) {
+            constexpr double oa = edge_off(e, ea), ob = edge_off(e, eb);
+            const double da = h[ea] * __ldg(Gv + ea * n + nbE[e]);
+            const double db = h[eb] * __ldg(Gv + eb * n + nbE[e]);
+            return (oa * da - ob * db) * kRs2;
+        } else {
+            return h[ee] * __ldg(Gv + ee * n + nbE[e]);
+        }
+    } else {
+        constexpr int j = K - kColCentreGrad;
+        return h[j] * __ldg(Gv + j * n + c);
     }
-    if (nonlinear) {
-        double x[3];
-        x[D] = 0.5 * sD;
-        x[T1] = kG * s1;
-        x[T2] = kG * s2;
-        const double p1 = q0 + bbar[0] * x[0] + bbar[1] * x[1] + bbar[2] * x[2];
-        val = chi * val + (1.0 - chi) * p1;
+}
+
+// In-place Walsh-Hadamard transform over the three axis bits: from class
+// sums X[cls] to the values at the eight points (+-x, +-y, +-z); afterwards
+// X[p] is the value where axis j has sign + if bit j of p is set, else -.
+template <typename T>
+__device__ __forceinline__ void class_to_points(T X[8]) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) der[q] = chi * der[q] + (1.0 - chi) * bbar[q];
-    }
-    constexpr int f = 2 * D + SIDE;
-    const int cmp = frame_comp(v, D);
-    double *o = fs + ((long long)(f * 4 + KK) * 20) * n + c;
-    o[(long long)cmp * n] = val;
+    for (int b = 1; b < 8; b <<= 1)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int jf = (q - D + 3) % 3;
-        o[(long long)(5 + 5 * jf + cmp) * n] = der[q] / h[q];
-    }
+        for (int p = 0; p < 8; ++p)
+            if (!(p & b)) {
+                const T lo = X[p], hi = X[p | b];
+                X[p] = lo - hi;
+                X[p | b] = lo + hi;
+            }
 }
 
 template <int D>
 __device__ __forceinline__ void eval_faces(double *__restrict__ fs, long long n, long long c,
                                            int v, const double a[kNumBasis], double base,
                                            double chi, const double bbar[3], double q0,
-                                           bool nonlinear, const double h[3]) {
+                                           bool nonlinear, const double ih[3]) {
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     double S[8], Dq[3][8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -163,14 +164,35 @@ __device__ __forceinline__ void eval_faces(double *__restrict__ fs, long long n,
             }
         });
     });
-    write_point<D, 0, 0>(fs, n, c, v, S, Dq, base, chi, bbar, q0, nonlinear, h);
-    write_point<D, 0, 1>(fs, n, c, v, S, Dq, base, chi, bbar, q0, nonlinear, h);
-    write_point<D, 0, 2>(fs, n, c, v, S, Dq, base, chi, bbar, q0, nonlinear, h);
-    write_point<D, 0, 3>(fs, n, c, v, S, Dq, base, chi, bbar, q0, nonlinear, h);
-    write_point<D, 1, 0>(fs, n, c, v, S, Dq, base, chi, bbar, q0, nonlinear, h);
-    write_point<D, 1, 1>(fs, n, c, v, S, Dq, base, chi, bbar, q0, nonlinear, h);
-    write_point<D, 1, 2>(fs, n, c, v, S, Dq, base, chi, bbar, q0, nonlinear, h);
-    write_point<D, 1, 3>(fs, n, c, v, S, Dq, base, chi, bbar, q0, nonlinear, h);
+    class_to_points(S);
+    class_to_points(Dq[0]);
+    class_to_points(Dq[1]);
+    class_to_points(Dq[2]);
+    const int cmp = frame_comp(v, D);
+#pragma unroll
+    for (int side = 0; side < 2; ++side)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int p = (side << D) | ((kk & 1) << T1) | (((kk >> 1) & 1) << T2);
+            double val = base + S[p], der[3] = {Dq[0][p], Dq[1][p], Dq[2][p]};
+            if (nonlinear) {
+                double x[3];
+                x[D] = side ? 0.5 : -0.5;
+                x[T1] = (kk & 1) ? kG : -kG;
+                x[T2] = (kk & 2) ? kG : -kG;
+                const double p1 = q0 + bbar[0] * x[0] + bbar[1] * x[1] + bbar[2] * x[2];
+                val = chi * val + (1.0 - chi) * p1;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) der[q] = chi * der[q] + (1.0 - chi) * bbar[q];
+            }
+            double *o = fs + ((long long)((2 * D + side) * 4 + kk) * 20) * n + c;
+            o[(long long)cmp * n] = val;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int jf = (q - D + 3) % 3;
+                o[(long long)(5 + 5 * jf + cmp) * n] = der[q] * ih[q];
+            }
+        }
 }
 
 __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
@@ -191,109 +213,102 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
         nbE[e] = cell_index(g, wrap(i + edge_off(e, 0), g.nx), wrap(j + edge_off(e, 1), g.ny),
                             wrap(k + edge_off(e, 2), g.nz));
     const double h[3] = {g.h[0], g.h[1], g.h[2]};
+    const double ih[3] = {1.0 / h[0], 1.0 / h[1], 1.0 / h[2]};
 
-    {
-        const double *Qv = Q + (long long)v * n;
-        const double *Gv = G + (long long)v * 3 * n;
-        const double q0 = __ldg(Qv + c);
-        double a[kNumBasis];
+    const double *Qv = Q + (long long)v * n;
+    const double *Gv = G + (long long)v * 3 * n;
+    const double q0 = __ldg(Qv + c);
+    double a[kNumBasis];
 #pragma unroll
-        for (int ii = 0; ii < kNumBasis; ++ii) a[ii] = 0.0;
-        double dface[6], dctr[3];
-        // face neighbours
-#define FACE_COLS(M)                                                               \
-        {                                                                          \
-            const double dq = __ldg(Qv + nbF[M]) - q0;                             \
-            dface[M] = dq;                                                         \
-            add_column<kColFace + M>(a, dq);                                       \
-            add_column<kColFaceGrad + 3 * M + 0>(a, h[0] * __ldg(Gv + nbF[M]));     \
-            add_column<kColFaceGrad + 3 * M + 1>(a, h[1] * __ldg(Gv + n + nbF[M])); \
-            add_column<kColFaceGrad + 3 * M + 2>(a, h[2] * __ldg(Gv + 2 * n + nbF[M])); \
+    for (int ii = 0; ii < kNumBasis; ++ii) a[ii] = 0.0;
+    double dface[6], dctr[3];
+    // a = R d orbit by orbit: load the orbit's columns, form its symmetrised
+    // combinations, multiply each with its class block of R
+    double ov[8];
+    static_for<kNumData>([&](auto Rr) {
+        constexpr int r = decltype(Rr)::value;
+        constexpr int nm = kSym.nm[r];
+        if constexpr (kSym.orbit[r] == r) {
+            static_for<nm>([&](auto Qq) {
+                constexpr int q = decltype(Qq)::value;
+                constexpr int col = kSym.mem[r][q];
+                ov[q] = data_col<col>(Qv, Gv, n, c, nbF, nbE, q0, h);
+                if constexpr (col < kColEdge) dface[col] = ov[q];
+                if constexpr (col >= kColCentreGrad) dctr[col - kColCentreGrad] = ov[q];
+            });
         }
-        FACE_COLS(0) FACE_COLS(1) FACE_COLS(2) FACE_COLS(3) FACE_COLS(4) FACE_COLS(5)
-#undef FACE_COLS
-        // edge neighbours: in-plane direction orthogonal to the offset, and
-        // the edge direction
-#define EDGE_COLS(E)                                                                   \
-        {                                                                              \
-            constexpr int ea = edge_axis_a(E), eb = edge_axis_b(E), ee = edge_axis_e(E); \
-            constexpr double oa = edge_off(E, ea), ob = edge_off(E, eb);              \
-            add_column<kColEdge + E>(a, __ldg(Qv + nbE[E]) - q0);                      \
-            const double da = h[ea] * __ldg(Gv + ea * n + nbE[E]);                     \
-            const double db = h[eb] * __ldg(Gv + eb * n + nbE[E]);                     \
-            add_column<kColEdgeGrad + 2 * E>(a, (oa * da - ob * db) * kRs2);           \
-            add_column<kColEdgeGrad + 2 * E + 1>(a, h[ee] * __ldg(Gv + ee * n + nbE[E])); \
-        }
-        EDGE_COLS(0) EDGE_COLS(1) EDGE_COLS(2) EDGE_COLS(3) EDGE_COLS(4) EDGE_COLS(5)
-        EDGE_COLS(6) EDGE_COLS(7) EDGE_COLS(8) EDGE_COLS(9) EDGE_COLS(10) EDGE_COLS(11)
-#undef EDGE_COLS
-        // own gradient
-        dctr[0] = h[0] * __ldg(Gv + c);
-        dctr[1] = h[1] * __ldg(Gv + n + c);
-        dctr[2] = h[2] * __ldg(Gv + 2 * n + c);
-        add_column<kColCentreGrad + 0>(a, dctr[0]);
-        add_column<kColCentreGrad + 1>(a, dctr[1]);
-        add_column<kColCentreGrad + 2>(a, dctr[2]);
+        double ds = kSym.sgn[r][0] > 0 ? ov[0] : -ov[0];
+        static_for<nm - 1>([&](auto Qq) {
+            constexpr int q = decltype(Qq)::value + 1;
+            if constexpr (kSym.sgn[r][q] > 0) ds += ov[q];
+            else ds -= ov[q];
+        });
+        constexpr int cls = kSym.cls[r];
+        static_for<kClass.n[cls]>([&](auto J) {
+            constexpr int jj = decltype(J)::value;
+            constexpr int ib = kClass.member[cls][jj];
+            a[ib] = fma(cRs[r][jj], ds, a[ib]);
+        });
+    });
 
-        // P4(x) = Q0 - sum_i a_i mean_i + sum_i a_i x^{e_i}/e_i!
-        double K = 0.0;
+    // P4(x) = Q0 - sum_i a_i mean_i + sum_i a_i x^{e_i}/e_i!
+    double K = 0.0;
+    static_for<kNumBasis>([&](auto I) {
+        constexpr int ii = decltype(I)::value;
+        if constexpr (basis_class(ii) == 0) K = fma(a[ii], cMean[ii], K);
+    });
+    const double base = q0 - K;
+
+    double chi = 1.0, bbar[3] = {0.0, 0.0, 0.0};
+    if (nonlinear) {
+        const double eps = 1e-15;
+        double w[6], IS[6], wsum = 0.0;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            const int ax = m / 2;
+            const double bn = (m & 1) ? dface[m] : -dface[m];
+            double s = bn * bn;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (q != ax) s += dctr[q] * dctr[q];
+            IS[m] = s;
+            const double t = s + eps, t2 = t * t;
+            w[m] = (1.0 / 6.0) / (t2 * t2 * t);
+            wsum += w[m];
+        }
+        double ISL = 0.0;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            w[m] /= wsum;
+            ISL += w[m] * IS[m];
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            // sum_m w_m b^m_q: tangential slopes from the own gradient,
+            // the normal one from the neighbour difference
+            bbar[q] = (1.0 - w[2 * q] - w[2 * q + 1]) * dctr[q] - w[2 * q] * dface[2 * q] +
+                      w[2 * q + 1] * dface[2 * q + 1];
+        }
+        double ISH = 0.0;
         static_for<kNumBasis>([&](auto I) {
             constexpr int ii = decltype(I)::value;
-            if constexpr (basis_class(ii) == 0) K = fma(a[ii], cMean[ii], K);
-        });
-        const double base = q0 - K;
-
-        double chi = 1.0, bbar[3] = {0.0, 0.0, 0.0};
-        if (nonlinear) {
-            const double eps = 1e-15;
-            double w[6], IS[6], wsum = 0.0;
-#pragma unroll
-            for (int m = 0; m < 6; ++m) {
-                const int ax = m / 2;
-                const double bn = (m & 1) ? dface[m] : -dface[m];
-                double s = bn * bn;
-#pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    if (q != ax) s += dctr[q] * dctr[q];
-                IS[m] = s;
-                const double t = s + eps, t2 = t * t;
-                w[m] = (1.0 / 6.0) / (t2 * t2 * t);
-                wsum += w[m];
-            }
-            double ISL = 0.0;
-#pragma unroll
-            for (int m = 0; m < 6; ++m) {
-                w[m] /= wsum;
-                ISL += w[m] * IS[m];
-            }
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                // sum_m w_m b^m_q: tangential slopes from the own gradient,
-                // the normal one from the neighbour difference
-                bbar[q] = (1.0 - w[2 * q] - w[2 * q + 1]) * dctr[q] - w[2 * q] * dface[2 * q] +
-                          w[2 * q + 1] * dface[2 * q + 1];
-            }
-            double ISH = 0.0;
-            static_for<kNumBasis>([&](auto I) {
-                constexpr int ii = decltype(I)::value;
-                double t = 0.0;
-                static_for<kNumBasis>([&](auto J) {
-                    constexpr int jj = decltype(J)::value;
-                    if constexpr (basis_class(ii) == basis_class(jj)) t = fma(cH[ii][jj], a[jj], t);
-                });
-                ISH = fma(a[ii], t, ISH);
+            double t = 0.0;
+            static_for<kNumBasis>([&](auto J) {
+                constexpr int jj = decltype(J)::value;
+                if constexpr (basis_class(ii) == basis_class(jj)) t = fma(cH[ii][jj], a[jj], t);
             });
-            const double r = fabs(ISH - ISL) / (ISH + ISL + eps);
-            const double rr = r * 10.0;
-            chi = 1.0 / (1.0 + rr * rr * rr);
-        }
-        eval_faces<0>(fs, n, c, v, a, base, chi, bbar, q0, nonlinear, h);
-        eval_faces<1>(fs, n, c, v, a, base, chi, bbar, q0, nonlinear, h);
-        eval_faces<2>(fs, n, c, v, a, base, chi, bbar, q0, nonlinear, h);
+            ISH = fma(a[ii], t, ISH);
+        });
+        const double r = fabs(ISH - ISL) / (ISH + ISL + eps);
+        const double rr = r * 10.0;
+        chi = 1.0 / (1.0 + rr * rr * rr);
     }
+    eval_faces<0>(fs, n, c, v, a, base, chi, bbar, q0, nonlinear, ih);
+    eval_faces<1>(fs, n, c, v, a, base, chi, bbar, q0, nonlinear, ih);
+    eval_faces<2>(fs, n, c, v, a, base, chi, bbar, q0, nonlinear, ih);
 }
 
-__global__ void __launch_bounds__(128, 3) recon5_kernel(GridDesc g, int nonlinear,
+__global__ void __launch_bounds__(128) recon5_kernel(GridDesc g, int nonlinear,
                                                      const double *__restrict__ Q,
                                                      const double *__restrict__ G,
                                                      double *__restrict__ fs) {
@@ -373,70 +388,53 @@ constexpr int kModePlain = 0;      // full GENO
 constexpr int kModeIndicator = 1;  // GENO skipped where the network is confident
 constexpr int kModeDump = 2;       // write the data vector and chi, no face states
 
-template <int COL, int MODE>
-__device__ __forceinline__ void add_column_f(const float *T, float a[kNumBasis],
-                                             float hid[kMlpHidden], float &amax, float x) {
-    static_for<kPad / 4>([&](auto I4) {
-        constexpr int i4 = decltype(I4)::value;
-        const float4 w = ld4(T, kTabR + COL * kPad + 4 * i4);
-        static_for<4>([&](auto K) {
-            constexpr int i = 4 * i4 + decltype(K)::value;
-            if constexpr (i < kNumBasis) a[i] = fmaf(f4(w, decltype(K)::value), x, a[i]);
-        });
+// learned indicator: hidden pre-activations from data column COL
+template <int COL>
+__device__ __forceinline__ void add_hidden_f(const float *T, float hid[kMlpHidden], float &amax,
+                                             float x) {
+    static_for<kMlpHidden / 4>([&](auto J4) {
+        constexpr int j4 = decltype(J4)::value;
+        const float4 w = ld4(T, kTabW1 + COL * kMlpHidden + 4 * j4);
+        hid[4 * j4 + 0] = fmaf(w.x, x, hid[4 * j4 + 0]);
+        hid[4 * j4 + 1] = fmaf(w.y, x, hid[4 * j4 + 1]);
+        hid[4 * j4 + 2] = fmaf(w.z, x, hid[4 * j4 + 2]);
+        hid[4 * j4 + 3] = fmaf(w.w, x, hid[4 * j4 + 3]);
     });
-    if (MODE == kModeIndicator) {
-        static_for<kMlpHidden / 4>([&](auto J4) {
-            constexpr int j4 = decltype(J4)::value;
-            const float4 w = ld4(T, kTabW1 + COL * kMlpHidden + 4 * j4);
-            hid[4 * j4 + 0] = fmaf(w.x, x, hid[4 * j4 + 0]);
-            hid[4 * j4 + 1] = fmaf(w.y, x, hid[4 * j4 + 1]);
-            hid[4 * j4 + 2] = fmaf(w.z, x, hid[4 * j4 + 2]);
-            hid[4 * j4 + 3] = fmaf(w.w, x, hid[4 * j4 + 3]);
-        });
-        amax = fmaxf(amax, fabsf(x));
-    }
+    amax = fmaxf(amax, fabsf(x));
 }
 
-template <int D, int SIDE, int KK>
-__device__ __forceinline__ void write_point_f(float *__restrict__ fs, long long n, long long c,
-                                              int v, const float S[8], const float Dq[3][8],
-                                              float base, float chi, const float bbar[3],
-                                              bool nonlinear, const float ih[3]) {
-    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-    constexpr float sD = SIDE ? 1.0f : -1.0f;
-    constexpr float s1 = (KK & 1) ? 1.0f : -1.0f;
-    constexpr float s2 = (KK & 2) ? 1.0f : -1.0f;
-    float sg[3];
-    sg[D] = sD;
-    sg[T1] = s1;
-    sg[T2] = s2;
-    float val = base, der[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int cls = 0; cls < 8; ++cls) {
-        const float sign = ((cls & 1) ? sg[0] : 1.0f) * ((cls & 2) ? sg[1] : 1.0f) *
-                           ((cls & 4) ? sg[2] : 1.0f);
-        val += sign * S[cls];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) der[q] += sign * Dq[q][cls];
-    }
-    if (nonlinear) {
-        float x[3];
-        x[D] = 0.5f * sD;
-        x[T1] = (float)kG * s1;
-        x[T2] = (float)kG * s2;
-        const float p1 = bbar[0] * x[0] + bbar[1] * x[1] + bbar[2] * x[2];
-        val = chi * val + (1.0f - chi) * p1;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) der[q] = chi * der[q] + (1.0f - chi) * bbar[q];
-    }
-    constexpr int f = 2 * D + SIDE;
-    const int cmp = frame_comp(v, D);
-    float *o = fs + ((long long)(f * 4 + KK) * 20) * n + c;
-    o[(long long)cmp * n] = val;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int jf = (q - D + 3) % 3;
-        o[(long long)(5 + 5 * jf + cmp) * n] = der[q] * ih[q];
+// FP32 data column K: differences of averages in FP64, rounded once; the
+// gradient entries h G in FP32. The products are __fmul_rn (never fused
+// into a later sum), so that every kernel that inlines this rounds them the
+// same way, whatever else uses the value (network, dump).
+template <int K>
+__device__ __forceinline__ float data_col_f(const double *__restrict__ Qv,
+                                            const double *__restrict__ Gv, long long n,
+                                            long long c, const long long nbF[6],
+                                            const long long nbE[12], double q0, const float hf[3]) {
+    if constexpr (K < kColEdge) {
+        return (float)(__ldg(Qv + nbF[K]) - q0);
+    } else if constexpr (K < kColFaceGrad) {
+        return (float)(__ldg(Qv + nbE[K - kColEdge]) - q0);
+    } else if constexpr (K < kColEdgeGrad) {
+        constexpr int m = (K - kColFaceGrad) / 3, j = (K - kColFaceGrad) % 3;
+        return __fmul_rn(hf[j], (float)__ldg(Gv + j * n + nbF[m]));
+    } else if constexpr (K < kColCentreGrad) {
+        constexpr int e = (K - kColEdgeGrad) / 2;
+        constexpr int ea = edge_axis_a(e), eb = edge_axis_b(e), ee = edge_axis_e(e);
+        if constexpr ((K - kColEdgeGrad) % 2 == 0) {
+            const float da = __fmul_rn(hf[ea], (float)__ldg(Gv + ea * n + nbE[e]));
+            const float db = __fmul_rn(hf[eb], (float)__ldg(Gv + eb * n + nbE[e]));
+            // o_a d_a - o_b d_b with o = +-1
+            constexpr bool same = edge_off(e, ea) == edge_off(e, eb);
+            const float t = same ? __fsub_rn(da, db) : __fadd_rn(da, db);
+            return __fmul_rn(edge_off(e, ea) > 0 ? t : -t, (float)kRs2);
+        } else {
+            return __fmul_rn(hf[ee], (float)__ldg(Gv + ee * n + nbE[e]));
+        }
+    } else {
+        constexpr int j = K - kColCentreGrad;
+        return __fmul_rn(hf[j], (float)__ldg(Gv + j * n + c));
     }
 }
 
@@ -446,6 +444,7 @@ __device__ __forceinline__ void eval_faces_f(const float *T, float *__restrict__
                                              const float a[kNumBasis], float base, float chi,
                                              const float bbar[3], bool nonlinear,
                                              const float ih[3]) {
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     float S[8], Dq[3][8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -479,14 +478,35 @@ __device__ __forceinline__ void eval_faces_f(const float *T, float *__restrict__
             }
         });
     });
-    write_point_f<D, 0, 0>(fs, n, c, v, S, Dq, base, chi, bbar, nonlinear, ih);
-    write_point_f<D, 0, 1>(fs, n, c, v, S, Dq, base, chi, bbar, nonlinear, ih);
-    write_point_f<D, 0, 2>(fs, n, c, v, S, Dq, base, chi, bbar, nonlinear, ih);
-    write_point_f<D, 0, 3>(fs, n, c, v, S, Dq, base, chi, bbar, nonlinear, ih);
-    write_point_f<D, 1, 0>(fs, n, c, v, S, Dq, base, chi, bbar, nonlinear, ih);
-    write_point_f<D, 1, 1>(fs, n, c, v, S, Dq, base, chi, bbar, nonlinear, ih);
-    write_point_f<D, 1, 2>(fs, n, c, v, S, Dq, base, chi, bbar, nonlinear, ih);
-    write_point_f<D, 1, 3>(fs, n, c, v, S, Dq, base, chi, bbar, nonlinear, ih);
+    class_to_points(S);
+    class_to_points(Dq[0]);
+    class_to_points(Dq[1]);
+    class_to_points(Dq[2]);
+    const int cmp = frame_comp(v, D);
+#pragma unroll
+    for (int side = 0; side < 2; ++side)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int p = (side << D) | ((kk & 1) << T1) | (((kk >> 1) & 1) << T2);
+            float val = base + S[p], der[3] = {Dq[0][p], Dq[1][p], Dq[2][p]};
+            if (nonlinear) {
+                float x[3];
+                x[D] = side ? 0.5f : -0.5f;
+                x[T1] = (kk & 1) ? (float)kG : -(float)kG;
+                x[T2] = (kk & 2) ? (float)kG : -(float)kG;
+                const float p1 = bbar[0] * x[0] + bbar[1] * x[1] + bbar[2] * x[2];
+                val = chi * val + (1.0f - chi) * p1;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) der[q] = chi * der[q] + (1.0f - chi) * bbar[q];
+            }
+            float *o = fs + ((long long)((2 * D + side) * 4 + kk) * 20) * n + c;
+            o[(long long)cmp * n] = val;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int jf = (q - D + 3) % 3;
+                o[(long long)(5 + 5 * jf + cmp) * n] = der[q] * ih[q];
+            }
+        }
 }
 
 template <int MODE>
@@ -527,53 +547,44 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
 #pragma unroll
         for (int jj = 0; jj < kMlpHidden; ++jj) hid[jj] = 0.0f;
         float dface[6], dctr[3];
-        // dump mode: data entry COL of (cell, variable) ->
-        // dump_x[COL * dump_ld + dump_base + 5 c + v]
-#define DUMP(COL, X)                                                                         \
-        if (MODE == kModeDump) dump_x[(long long)(COL) * dump_ld + dump_base + 5 * c + v] = (X);
-#define FACE_COLS_F(M)                                                                       \
-        {                                                                                    \
-            const float dq = (float)(__ldg(Qv + nbF[M]) - q0);                               \
-            const float g0 = hf[0] * (float)__ldg(Gv + nbF[M]);                              \
-            const float g1 = hf[1] * (float)__ldg(Gv + n + nbF[M]);                          \
-            const float g2 = hf[2] * (float)__ldg(Gv + 2 * n + nbF[M]);                      \
-            dface[M] = dq;                                                                   \
-            add_column_f<kColFace + M, MODE>(T, a, hid, amax, dq);                              \
-            add_column_f<kColFaceGrad + 3 * M + 0, MODE>(T, a, hid, amax, g0);                  \
-            add_column_f<kColFaceGrad + 3 * M + 1, MODE>(T, a, hid, amax, g1);                  \
-            add_column_f<kColFaceGrad + 3 * M + 2, MODE>(T, a, hid, amax, g2);                  \
-            DUMP(kColFace + M, dq) DUMP(kColFaceGrad + 3 * M, g0)                            \
-            DUMP(kColFaceGrad + 3 * M + 1, g1) DUMP(kColFaceGrad + 3 * M + 2, g2)            \
-        }
-        FACE_COLS_F(0) FACE_COLS_F(1) FACE_COLS_F(2) FACE_COLS_F(3) FACE_COLS_F(4) FACE_COLS_F(5)
-#undef FACE_COLS_F
-#define EDGE_COLS_F(E)                                                                       \
-        {                                                                                    \
-            constexpr int ea = edge_axis_a(E), eb = edge_axis_b(E), ee = edge_axis_e(E);     \
-            constexpr float oa = edge_off(E, ea), ob = edge_off(E, eb);                      \
-            const float dq = (float)(__ldg(Qv + nbE[E]) - q0);                               \
-            const float da = hf[ea] * (float)__ldg(Gv + ea * n + nbE[E]);                    \
-            const float db = hf[eb] * (float)__ldg(Gv + eb * n + nbE[E]);                    \
-            const float t0 = (oa * da - ob * db) * (float)kRs2;                              \
-            const float t1 = hf[ee] * (float)__ldg(Gv + ee * n + nbE[E]);                    \
-            add_column_f<kColEdge + E, MODE>(T, a, hid, amax, dq);                              \
-            add_column_f<kColEdgeGrad + 2 * E, MODE>(T, a, hid, amax, t0);                      \
-            add_column_f<kColEdgeGrad + 2 * E + 1, MODE>(T, a, hid, amax, t1);                  \
-            DUMP(kColEdge + E, dq) DUMP(kColEdgeGrad + 2 * E, t0)                            \
-            DUMP(kColEdgeGrad + 2 * E + 1, t1)                                               \
-        }
-        EDGE_COLS_F(0) EDGE_COLS_F(1) EDGE_COLS_F(2) EDGE_COLS_F(3) EDGE_COLS_F(4) EDGE_COLS_F(5)
-        EDGE_COLS_F(6) EDGE_COLS_F(7) EDGE_COLS_F(8) EDGE_COLS_F(9) EDGE_COLS_F(10) EDGE_COLS_F(11)
-#undef EDGE_COLS_F
-        dctr[0] = hf[0] * (float)__ldg(Gv + c);
-        dctr[1] = hf[1] * (float)__ldg(Gv + n + c);
-        dctr[2] = hf[2] * (float)__ldg(Gv + 2 * n + c);
-        add_column_f<kColCentreGrad + 0, MODE>(T, a, hid, amax, dctr[0]);
-        add_column_f<kColCentreGrad + 1, MODE>(T, a, hid, amax, dctr[1]);
-        add_column_f<kColCentreGrad + 2, MODE>(T, a, hid, amax, dctr[2]);
-        DUMP(kColCentreGrad, dctr[0]) DUMP(kColCentreGrad + 1, dctr[1])
-        DUMP(kColCentreGrad + 2, dctr[2])
-#undef DUMP
+        // a = R d orbit by orbit (see recon5_cell); the network and the dump
+        // see the raw columns as they are loaded. Dump mode: data entry COL
+        // of (cell, variable) -> dump_x[COL * dump_ld + dump_base + 5 c + v]
+        float ov[8];
+        static_for<kNumData>([&](auto Rr) {
+            constexpr int r = decltype(Rr)::value;
+            constexpr int nm = kSym.nm[r];
+            if constexpr (kSym.orbit[r] == r) {
+                static_for<nm>([&](auto Qq) {
+                    constexpr int q = decltype(Qq)::value;
+                    constexpr int col = kSym.mem[r][q];
+                    ov[q] = data_col_f<col>(Qv, Gv, n, c, nbF, nbE, q0, hf);
+                    if constexpr (col < kColEdge) dface[col] = ov[q];
+                    if constexpr (col >= kColCentreGrad) dctr[col - kColCentreGrad] = ov[q];
+                    if constexpr (MODE == kModeIndicator) add_hidden_f<col>(T, hid, amax, ov[q]);
+                    if constexpr (MODE == kModeDump)
+                        dump_x[(long long)col * dump_ld + dump_base + 5 * c + v] = ov[q];
+                });
+            }
+            float ds = kSym.sgn[r][0] > 0 ? ov[0] : -ov[0];
+            static_for<nm - 1>([&](auto Qq) {
+                constexpr int q = decltype(Qq)::value + 1;
+                if constexpr (kSym.sgn[r][q] > 0) ds += ov[q];
+                else ds -= ov[q];
+            });
+            constexpr int cls = kSym.cls[r];
+            static_for<(kClass.n[cls] + 3) / 4>([&](auto J4) {
+                constexpr int j4 = decltype(J4)::value;
+                const float4 w = ld4(T, kTabRs + r * kPadS + 4 * j4);
+                static_for<4>([&](auto K) {
+                    constexpr int jj = 4 * j4 + decltype(K)::value;
+                    if constexpr (jj < kClass.n[cls]) {
+                        constexpr int ib = kClass.member[cls][jj];
+                        a[ib] = fmaf(f4(w, decltype(K)::value), ds, a[ib]);
+                    }
+                });
+            });
+        });
         // learned indicator: the network sees d / (max|d| + delta); by
         // linearity the hidden pre-activations were accumulated on the raw d
         bool geno = nonlinear != 0;
@@ -788,6 +799,7 @@ int upload_recon_tables(void) {
         built = 1;
     }
     if (cudaMemcpyToSymbol(cR, t.R, sizeof(t.R)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(cRs, t.Rs, sizeof(t.Rs)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cH, t.H, sizeof(t.H)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cMean, t.mean, sizeof(t.mean)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cMval, t.mval, sizeof(t.mval)) != cudaSuccess) return -2;
@@ -796,8 +808,9 @@ int upload_recon_tables(void) {
     // as they are)
     static float tab[kTabW1];
     for (int i = 0; i < kTabW1; ++i) tab[i] = 0.0f;
+    for (int r = 0; r < kNumData; ++r)
+        for (int j = 0; j < kMaxClass; ++j) tab[kTabRs + r * kPadS + j] = (float)t.Rs[r][j];
     for (int i = 0; i < kNumBasis; ++i) {
-        for (int c = 0; c < kNumData; ++c) tab[kTabR + c * kPad + i] = (float)t.R[i][c];
         for (int j = 0; j < kNumBasis; ++j) tab[kTabH + i * kPad + j] = (float)t.H[i][j];
         tab[kTabMean + i] = (float)t.mean[i];
         for (int d = 0; d < 3; ++d) {

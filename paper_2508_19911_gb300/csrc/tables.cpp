@@ -188,6 +188,26 @@ int build_recon_tables(ReconTables *t) {
         }
     }
 
+    // R in the symmetrised data basis: column r of R T^{-1}, T^{-1} = T^T
+    // diag(1/nm) (the rows of T are orthogonal); by the reflection symmetry
+    // it maps a class-c combination to class-c monomials only, which is
+    // checked here
+    double rmax = 0.0;
+    for (int i = 0; i < nb; ++i)
+        for (int col = 0; col < kNumData; ++col) rmax = std::fmax(rmax, std::fabs(t->R[i][col]));
+    for (int r = 0; r < kNumData; ++r) {
+        const int c = kSym.cls[r];
+        for (int i = 0; i < nb; ++i) {
+            double s = 0.0;
+            for (int q = 0; q < kSym.nm[r]; ++q) s += kSym.sgn[r][q] * t->R[i][kSym.mem[r][q]];
+            s /= kSym.nm[r];
+            if (parity_class(kExp[i][0], kExp[i][1], kExp[i][2]) == c)
+                t->Rs[r][kClass.pos[i]] = s;
+            else if (std::fabs(s) > 1e-12 * rmax)
+                return -1;
+        }
+    }
+
     // smoothness form and means on the unit cell [-1/2, 1/2]^3
     auto mono_int = [](int n) { return (n % 2) ? 0.0 : std::pow(0.5, n) / (n + 1); };
     for (int i = 0; i < nb; ++i) {

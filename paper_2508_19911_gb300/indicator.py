@@ -24,7 +24,7 @@ from . import workloads as wl
 # below 1e-5)
 LABEL_EPS = 1e-3
 NEG_WEIGHT = 1.0
-THETA = 0.7
+THETA = 0.9
 
 
 D = 63

@@ -76,8 +76,8 @@ def grouped_err(a, b):
     return max(errs)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
-def test_instances_match_their_solo_runs(env, precision, tol):
+@pytest.mark.parametrize("precision,tol,tol_t", [("fp64", 1e-12, 1e-12), ("mixed", 1e-6, 1e-9)])
+def test_instances_match_their_solo_runs(env, precision, tol, tol_t):
     torch, dev, gks = env
     insts = small_instances()
     e = build(env, insts, precision)
@@ -89,7 +89,7 @@ def test_instances_match_their_solo_runs(env, precision, tol):
         Qs, Gs, dts = solo_steps(env, Q, G, grid, ph, precision, 3)
         q, gg = e.views(i)
         assert t1[i] == dts[0], i                      # first dt: same state, same reduction
-        assert t[i] == pytest.approx(sum(dts), rel=1e-12), i
+        assert t[i] == pytest.approx(sum(dts), rel=tol_t), i
         eq = grouped_err(q, Qs)
         eg = float((gg - Gs).abs().max() / Gs.abs().max().clamp_min(1e-300))
         print(f"instance {i} {precision}: state err {eq:.2e}, gradient err {eg:.2e}")
