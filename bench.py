@@ -31,18 +31,31 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-stage updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
-FP64_FLOP_PER_CLK_PER_SM = 4   # nominal 1.25 TFLOP/s / (152 SMs x 2.07 GHz)
+FP64_FLOP_PER_CLK_PER_SM = 4     # nominal 1.25 TFLOP/s / (152 SMs x 2.07 GHz)
+FP32_FLOP_PER_CLK_PER_SM = 256   # 128 FP32 lanes x FMA
 SM_MAX_MHZ_NOMINAL = 2070.0
-# FP64 operations (DFMA counted as 2, DADD and DMUL as 1) per unit of work,
-# from ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on on
-# TGV 32^3 (see profiles/); a unit is one face Gauss point for the flux
-# kernel and one cell for the reconstruction kernel.
-FLOPS_PER_UNIT = {
-    "flux_cgks5": 5218.5,   # per face Gauss point
-    "recon5": 38865.0,      # per cell (5 conserved variables)
-    "flux_gks2": None,
+HBM_FALLBACK_GBS = 6800.0
+# Work per unit of the hot kernels, from ncu's SASS op counters
+# (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul,ffma,fadd,fmul}_pred_on,
+# an FMA counted as 2 FLOP) and dram__bytes_{read,write} on TGV 64^3 (see
+# profiles/): FP64 and FP32 FLOP, algorithmic bytes (state and face-state
+# buffers read and written once) and measured DRAM bytes. A unit is one cell
+# for a reconstruction, one face Gauss point for a flux kernel (12 per cell
+# for CGKS-5th: 3 faces x 4 points; 3 per cell for GKS-2nd).
+KERNEL_OPS = {
+    "recon5": {"fp64": 14559.0, "fp32": 0.0, "bytes": 160 + 3840, "dram": 3769.0},
+    "flux_cgks5": {"fp64": 5220.3, "fp32": 0.0, "bytes": (3840 + 720) / 12, "dram": 379.2},
+    "recon5_mixed": {"fp64": 90.0, "fp32": 13537.0, "bytes": 40 + 60 + 1920, "dram": 1791.0},
+    "flux_cgks5_mixed": {"fp64": 143.0, "fp32": 9031.0, "bytes": (1920 + 40 + 720) / 12,
+                         "dram": 223.2},
 }
-LAUNCHES_PER_STEP = {"cgks5": 8, "gks2": 5}
+KERNEL_OPS["recon5_learned"] = KERNEL_OPS["recon5_mixed"]
+KERNEL_OPS["flux_cgks5_learned"] = KERNEL_OPS["flux_cgks5_mixed"]
+# kernels of my own per step: dt (reduction + finalisation), then per stage
+# reconstruction, flux, update (+ the FP32 gradient copy of the mixed
+# CGKS-5th reconstruction)
+LAUNCHES_PER_STEP = {("cgks5", "fp64"): 8, ("cgks5", "mixed"): 10, ("gks2", "fp64"): 5,
+                     ("gks2", "mixed"): 5}
 
 
 def parse():
@@ -56,8 +69,15 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--indicator", action="store_true",
                     help="mixed precision with the learned smoothness indicator (CGKS-5th)")
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "hit"],
+                    help="tgv: Taylor-Green vortex (Ma 0.1, Re 1600); hit: decaying isotropic "
+                         "turbulence (Mt 0.5, k0 8, seed 103, mu 1e-3)")
+    ap.add_argument("--slab-planes", type=int, default=0,
+                    help="z-planes per reconstruction/flux slab (0: automatic)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the host round trip (very large grids)")
     return ap.parse_args()
 
 
@@ -237,7 +257,16 @@ def run_ours(args, rank, world, local_rank):
     scheme = args.scheme
     cg = scheme == "cgks5"
     stages = 2 if cg else 1
-    Qh, Gh, grid = wl.taylor_green(n)
+    if args.workload == "tgv":
+        Qh, Gh, grid = wl.taylor_green(n)
+        phys = dict(mu=1.0 / 1600)
+        wname, wdata = "taylor_green", "synthetic (Taylor-Green cell averages)"
+        wcfg = {"Ma": 0.1, "Re": 1600}
+    else:
+        Qh, Gh, grid, hit_info = wl.isotropic_turbulence(n, Mt=0.5, k0=8.0, seed=103)
+        phys = dict(mu=1e-3)
+        wname, wdata = "isotropic_turbulence", "synthetic (seeded isotropic turbulence)"
+        wcfg = {"Mt": 0.5, "k0": 8, "seed": 103, "mu": 1e-3}
     cells = n ** 3
     prec = "mixed" if args.indicator else args.precision
     if args.indicator and not cg:
@@ -246,7 +275,9 @@ def run_ours(args, rank, world, local_rank):
     if args.indicator or (cg and not args.no_variants and rank == 0):
         params, ind_info = trained_indicator(torch, dev)
     solver = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=scheme, nonlinear=True,
-                                   precision=prec, indicator=args.indicator), stream)
+                                   precision=prec, indicator=args.indicator,
+                                   slab_planes=args.slab_planes, **phys), stream)
+    slab = solver.slab_planes
     if args.indicator:
         solver.set_indicator(params, theta=ind_info["theta"])
     Q = torch.tensor(Qh, device=dev)
@@ -270,59 +301,94 @@ def run_ours(args, rank, world, local_rank):
         ind_info["skip_fraction"] = solver.indicator_skips() / (
             5 * cells * stages * (args.steps + args.warmup))
 
-    # dominant kernel: reconstruction or flux launch timed alone (same inputs)
-    fs = solver.reconstruct(Q, G)
-    dtd = solver.compute_dt(Q)
-    reps = 3
-    t_recon = time_kernel(torch, lambda: solver.reconstruct(Q, G, out=fs), reps, stream)
-    frec = solver.flux(fs, dtd, Q=Q)
-    t_flux = time_kernel(torch, lambda: solver.flux(fs, dtd, out=frec, Q=Q), reps, stream)
-    K = 4 if cg else 1
-    sfx = ("_learned" if args.indicator else "_mixed") if prec == "mixed" else ""
-    if t_flux >= t_recon:
-        kname, t_k = ("flux_cgks5" if cg else "flux_gks2") + sfx, t_flux
-        units = 3 * cells * K
+    if slab == 0:
+        # dominant kernel: reconstruction or flux launch timed alone (same inputs)
+        fs = solver.reconstruct(Q, G)
+        dtd = solver.compute_dt(Q)
+        reps = 3
+        t_recon = time_kernel(torch, lambda: solver.reconstruct(Q, G, out=fs), reps, stream)
+        frec = solver.flux(fs, dtd, Q=Q)
+        t_flux = time_kernel(torch, lambda: solver.flux(fs, dtd, out=frec, Q=Q), reps, stream)
+        K = 4 if cg else 1
+        sfx = ("_learned" if args.indicator else "_mixed") if prec == "mixed" else ""
+        if t_flux >= t_recon:
+            kname, t_k = ("flux_cgks5" if cg else "flux_gks2") + sfx, t_flux
+            units = 3 * cells * K
+        else:
+            kname, t_k = ("recon5" if cg else "recon2") + sfx, t_recon
+            units = cells
+        clocks = clk.summary()
+        f_mhz = clocks["sm_max_mhz"] or SM_MAX_MHZ_NOMINAL
+        peak64 = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * f_mhz * 1e6 / 1e12
+        peak32 = SM_COUNT * FP32_FLOP_PER_CLK_PER_SM * f_mhz * 1e6 / 1e12
+        peaks = measured_peaks()
+        hbm_peak = peaks.get("hbm_gbs") or HBM_FALLBACK_GBS
+        ops = KERNEL_OPS.get(kname)
+        roofline = {"kernel": kname, "ms_per_launch": t_k, "units_per_launch": units,
+                    "other_kernel_ms": {"recon": t_recon, "flux": t_flux}}
+        if ops:
+            sec = t_k / 1e3
+            a64 = ops["fp64"] * units / sec / 1e12
+            a32 = ops["fp32"] * units / sec / 1e12
+            hbm = ops["bytes"] * units / sec / 1e9
+            f64, f32 = a64 / peak64, a32 / peak32
+            # the binding unit: the FP64 pipe unless the FP32 one is busier
+            if f64 >= f32:
+                roofline.update({"bound": "alu", "achieved": a64, "peak": peak64,
+                                 "unit": "TFLOP/s (FP64)", "frac": f64})
+            else:
+                roofline.update({"bound": "alu", "achieved": a32, "peak": peak32,
+                                 "unit": "TFLOP/s (FP32)", "frac": f32})
+            roofline.update({
+                "traffic": ops["dram"] * units,
+                "traffic_note": "ncu dram__bytes_read+write per unit on TGV 64^3, scaled to this launch",
+                "fp64": {"achieved_tflops": a64, "peak_tflops": peak64, "frac": f64},
+                "fp32": {"achieved_tflops": a32, "peak_tflops": peak32, "frac": f32},
+                "hbm": {"achieved_gbs": hbm, "peak_gbs": hbm_peak, "frac": hbm / hbm_peak,
+                        "peak_source": "MEASURED_PEAKS.json" if peaks.get("hbm_gbs") else "fallback"},
+                "peak_note": "ALU peaks from unit counts (152 SMs x 4 FP64 / 256 FP32 FLOP/clk x "
+                             "sm_max clock); HBM peak measured copy bandwidth",
+            })
+        else:
+            roofline.update({"bound": "alu", "achieved": None, "peak": peak64,
+                             "unit": "TFLOP/s (FP64)", "frac": None, "traffic": None})
     else:
-        kname, t_k = ("recon5" if cg else "recon2") + sfx, t_recon
-        units = cells
-    clocks = clk.summary()
-    f_mhz = clocks["sm_max_mhz"] or SM_MAX_MHZ_NOMINAL
-    peak_tflops = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * f_mhz * 1e6 / 1e12
-    fpu = FLOPS_PER_UNIT.get(kname)
-    achieved = (fpu * units / (t_k / 1e3) / 1e12) if fpu else None
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_tflops,
-                "unit": "TFLOP/s (FP64)", "frac": (achieved / peak_tflops) if achieved else None,
-                "traffic": None, "ms_per_launch": t_k,
-                "peak_note": "FP64 ALU peak from unit counts: 152 SMs x 4 FP64 flop/clk x sm_max clock",
-                "other_kernel_ms": {"recon": t_recon, "flux": t_flux}}
+        # the face-state buffer holds one z-slab: the kernels are not timed
+        # alone here (the whole-grid buffer they would need does not fit)
+        roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": None, "note": f"z-slabs of {slab} planes; kernels not timed alone"}
+        clocks = clk.summary()
 
-    # end to end through the C-ABI with host buffers: pinned H2D of the
-    # state, one step, D2H of the state, every step
-    Qp = torch.from_numpy(Qh).pin_memory()
-    Gp = torch.from_numpy(Gh).pin_memory() if cg else None
-    e2e_steps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        Q.copy_(Qp, non_blocking=True)
-        if cg:
-            G.copy_(Gp, non_blocking=True)
-        solver.step(Q, G, nsteps=1, sync=False)
-        Qp.copy_(Q, non_blocking=True)
-        if cg:
-            Gp.copy_(G, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    state_bytes = Qh.nbytes + (Gh.nbytes if cg else 0)
-    e2e = {"value": world * cells * stages / (e2e_ms / 1e3), "unit": "cell-stage/s",
-           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
-           "ms_per_step": e2e_ms}
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C-ABI with host buffers: pinned H2D of the
+        # state, one step, D2H of the state, every step
+        Qp = torch.from_numpy(Qh).pin_memory()
+        Gp = torch.from_numpy(Gh).pin_memory() if cg else None
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            Q.copy_(Qp, non_blocking=True)
+            if cg:
+                G.copy_(Gp, non_blocking=True)
+            solver.step(Q, G, nsteps=1, sync=False)
+            Qp.copy_(Q, non_blocking=True)
+            if cg:
+                Gp.copy_(G, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        state_bytes = Qh.nbytes + (Gh.nbytes if cg else 0)
+        e2e = {"value": world * cells * stages / (e2e_ms / 1e3), "unit": "cell-stage/s",
+               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+               "ms_per_step": e2e_ms}
 
     solver.close()
-    del fs, frec
+    fs = frec = None  # release the whole-grid buffers before the variants
+    torch.cuda.empty_cache()
     variants = {}
     if not args.no_variants and rank == 0:
         main_tag = (scheme, "learned" if args.indicator else prec)
@@ -363,14 +429,16 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == "fp64" else "f32+f64",
         "indicator": ind_info if args.indicator else None,
-        "data": "synthetic (Taylor-Green cell averages)",
-        "config": {"workload": f"taylor_green_{n}^3_{scheme}_{'learned' if args.indicator else prec}"
-                               "_nonlinear", "cells": cells,
-                   "scheme": scheme, "stages_per_step": stages, "Ma": 0.1, "Re": 1600,
-                   "gamma": 1.4, "Pr": 0.72, "cfl": 0.3, "parallelism": f"replicas{world}",
-                   "l2": "working set larger than L2 (state + face buffers > 129 MB)"},
+        "data": wdata,
+        "config": dict({"workload": f"{wname}_{n}^3_{scheme}_{'learned' if args.indicator else prec}"
+                                   "_nonlinear", "cells": cells,
+                        "scheme": scheme, "stages_per_step": stages,
+                        "gamma": 1.4, "Pr": 0.72, "cfl": 0.3, "parallelism": f"replicas{world}",
+                        "slab_planes": slab,
+                        "l2": "working set larger than L2 (state + face buffers > 129 MB)"},
+                       **wcfg),
         "roofline": roofline, "e2e": e2e,
-        "gpu_launches": LAUNCHES_PER_STEP[scheme] * args.steps, "clocks": clocks,
+        "gpu_launches": LAUNCHES_PER_STEP[(scheme, prec)] * args.steps, "clocks": clocks,
         "variants": variants,
     }
     return line

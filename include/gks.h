@@ -66,11 +66,20 @@ typedef struct {
     double eps_tau;  /* Sec. 4 inviscid constant epsilon (default 0.05)      */
     double T_ref;    /* Sutherland reference temperature (default 1)         */
     double theta;    /* indicator threshold in (0, 1] (default 0.9)          */
+    int slab_planes; /* face-state buffer size for gks_step: 0 (default) the
+                        whole grid when it fits in 40% of the free device
+                        memory at gks_init, else the most z-planes that fit
+                        in 25% of it; > 0: slabs of this many z-planes
+                        (nz or more: the whole grid). gks_step then runs
+                        reconstruction and flux slab by slab (each slab
+                        also reconstructs the plane below it); the results
+                        equal the whole-grid ones bit for bit.           */
+    int reserved;    /* set to 0                                            */
 } gks_options;
 
 /* Fill *opt with the defaults: CGKS-5th, nonlinear, FP64, no indicator,
  * constant mu, viscous tau, C_tau = 10, eps_tau = 0.05, T_ref = 1,
- * theta = 0.9. */
+ * theta = 0.9, slab_planes = 0 (automatic). */
 void gks_default_options(gks_options *opt);
 
 /* Create a context for one grid (Sec. 4 problem statement: gamma, Pr, mu,
@@ -97,6 +106,10 @@ const char *gks_strerror(int code);
 size_t gks_face_state_bytes(const gks_ctx *ctx);
 /* Bytes of the face-flux records written by gks_flux: 3 x 30 x cells x 8. */
 size_t gks_face_flux_bytes(const gks_ctx *ctx);
+/* z-planes per slab of gks_step's reconstruction + flux (see slab_planes in
+ * gks_options): 0 when the context's face-state buffer holds the whole grid,
+ * -1 for a NULL context. */
+int gks_slab_planes(const gks_ctx *ctx);
 
 /* a0 -- time step of Sec. 4: dt = CFL min( min_{cells,d} h_d/(|U_d| + c),
  * h_min^2/(3 nu_max) ) (the viscous bound only when the flow is viscous).

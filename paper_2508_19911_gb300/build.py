@@ -21,7 +21,12 @@ LIB = os.path.join(BUILD, "libgks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["flux.cu", "recon.cu", "update.cu", "capi.cu", "noalloc.cu", "mlp.cu", "ensemble.cu"]
 CPP_SOURCES = ["tables.cpp"]
-HEADERS = ["basis.h", "common.cuh"]
+HEADERS = ["basis.h", "common.cuh", "ff.cuh"]
+# recon.cu: no implicit multiply-add contraction (only explicit fma), so
+# that every kernel inlining the same reconstruction rounds identically
+# (the learned indicator's never-skip limit equals the plain kernel bit for
+# bit; ptxas would otherwise fuse differently in each kernel's context)
+EXTRA_FLAGS = {"recon.cu": ["-fmad=false"]}
 COMPILE_TIMEOUT = 900
 
 
@@ -51,6 +56,7 @@ def _compile(src: str, obj: str) -> None:
                              "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
     if src.endswith(".cpp"):
         cmd += ["-x", "c++"]
+    cmd += EXTRA_FLAGS.get(os.path.basename(src), [])
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=COMPILE_TIMEOUT)
     if r.returncode != 0:
         raise RuntimeError(f"compiling {os.path.basename(src)} failed:\n{r.stderr[-4000:]}")

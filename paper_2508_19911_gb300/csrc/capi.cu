@@ -25,6 +25,8 @@ struct gks_ctx {
     unsigned long long *skips;  // (cell, variable) pairs that skipped GENO
     double *frec;          // face records [3][30][n]
     double *Qs, *Gs, *Acc, *S1;  // CGKS-5th stage buffers
+    float *Gf;             // mixed CGKS-5th: FP32 copy of the gradients [15][n]
+    int slab_planes;       // 0: fs holds the whole grid; > 0: z-slabs of this many planes
     double *scal;          // [0] dt, [1..2] dt reduction words, [3] diagnostics out (12)
     int *status;
     double *partials;
@@ -101,6 +103,7 @@ void gks_destroy(gks_ctx *c) {
     cudaFree(c->Gs);
     cudaFree(c->Acc);
     cudaFree(c->S1);
+    cudaFree(c->Gf);
     cudaFree(c->scal);
     cudaFree(c->status);
     cudaFree(c->partials);
@@ -124,7 +127,7 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
         return GKS_ERR_ARG;
     if (o.indicator && !(o.theta > 0.0 && o.theta <= 1.0)) return GKS_ERR_ARG;
     if (o.mu_law < 0 || o.mu_law > 1 || !(o.C_tau >= 0.0) || !(o.eps_tau >= 0.0) ||
-        !(o.T_ref > 0.0))
+        !(o.T_ref > 0.0) || o.slab_planes < 0)
         return GKS_ERR_ARG;
     const long long n = (long long)nx * ny * nz;
     if (n > (1LL << 31)) return GKS_ERR_ARG;
@@ -151,7 +154,22 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
         if (t) { gks_destroy(c); return t == -1 ? GKS_ERR_ARG : GKS_ERR_CUDA; }
     }
     c->diag_blocks = diagnostics_blocks(c->g);
-    if ((rc = dalloc((char **)&c->fs, (size_t)6 * c->K * 20 * n * (c->mixed ? 4 : 8))) ||
+    // face-state buffer: the whole grid, or z-slabs (+1 plane below each)
+    const size_t fs_per_cell = (size_t)6 * c->K * 20 * (c->mixed ? 4 : 8);
+    const long long nxy = (long long)nx * ny;
+    long long planes = nz;
+    if (o.slab_planes > 0) {
+        planes = o.slab_planes;
+    } else {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (double)fs_per_cell * n > 0.4 * fr) {
+            planes = (long long)(0.25 * fr / ((double)fs_per_cell * nxy)) - 1;
+            if (planes < 1) planes = 1;
+        }
+    }
+    c->slab_planes = planes >= nz ? 0 : (int)planes;
+    const long long fs_cells = c->slab_planes ? nxy * (c->slab_planes + 1) : n;
+    if ((rc = dalloc((char **)&c->fs, fs_per_cell * fs_cells)) ||
         (rc = dalloc(&c->frec, (size_t)90 * n)) ||
         (rc = dalloc(&c->scal, (size_t)3 + 12)) ||
         (rc = dalloc(&c->status, 1)) ||
@@ -162,7 +180,8 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
     }
     if (o.scheme == GKS_SCHEME_CGKS5) {
         if ((rc = dalloc(&c->Qs, (size_t)5 * n)) || (rc = dalloc(&c->Gs, (size_t)15 * n)) ||
-            (rc = dalloc(&c->Acc, (size_t)5 * n)) || (rc = dalloc(&c->S1, (size_t)15 * n))) {
+            (rc = dalloc(&c->Acc, (size_t)5 * n)) || (rc = dalloc(&c->S1, (size_t)15 * n)) ||
+            (c->mixed && (rc = dalloc(&c->Gf, (size_t)15 * n)))) {
             gks_destroy(c);
             return rc;
         }
@@ -182,6 +201,8 @@ size_t gks_face_state_bytes(const gks_ctx *c) {
     return c ? (size_t)6 * c->K * 20 * c->g.n * (c->mixed ? 4 : 8) : 0;
 }
 
+int gks_slab_planes(const gks_ctx *c) { return c ? c->slab_planes : -1; }
+
 size_t gks_face_flux_bytes(const gks_ctx *c) {
     return c ? (size_t)90 * c->g.n * sizeof(double) : 0;
 }
@@ -192,36 +213,70 @@ int gks_compute_dt(gks_ctx *c, const double *Q, double *dt_dev) {
 }
 
 namespace {
-int recon_any(gks_ctx *c, const double *Q, const double *G, void *fs) {
+// reconstruction and flux of one face-state buffer S (the FP32 gradient
+// copy of the mixed CGKS-5th reconstruction is made by the caller)
+int recon_any(gks_ctx *c, const Slab &S, const double *Q, const double *G, void *fs) {
     const bool cg = c->P.scheme == GKS_SCHEME_CGKS5;
     if (c->mixed)
-        return cg ? launch_recon5_mixed(c->g, c->P, Q, G, (float *)fs, c->stream, c->indicator_on,
-                                        c->skips)
-                  : launch_recon2_mixed(c->g, c->P, Q, (float *)fs, c->stream);
-    return cg ? launch_recon5(c->g, c->P, Q, G, (double *)fs, c->stream)
-              : launch_recon2(c->g, c->P, Q, (double *)fs, c->stream);
+        return cg ? launch_recon5_mixed(c->g, S, c->P, Q, c->Gf, (float *)fs, c->stream,
+                                        c->indicator_on, c->skips)
+                  : launch_recon2_mixed(c->g, S, c->P, Q, (float *)fs, c->stream);
+    return cg ? launch_recon5(c->g, S, c->P, Q, G, (double *)fs, c->stream)
+              : launch_recon2(c->g, S, c->P, Q, (double *)fs, c->stream);
 }
-int flux_any(gks_ctx *c, const double *Q, const void *fs, const double *dt, double *fr) {
+int flux_any(gks_ctx *c, const Slab &S, const double *Q, const void *fs, const double *dt,
+             double *fr) {
     if (c->mixed)
-        return launch_flux_faces_mixed(c->g, c->P, (const float *)fs, Q, dt, fr, c->status,
+        return launch_flux_faces_mixed(c->g, S, c->P, (const float *)fs, Q, dt, fr, c->status,
                                        c->stream);
-    return launch_flux_faces(c->g, c->P, (const double *)fs, dt, fr, c->status, c->stream);
+    return launch_flux_faces(c->g, S, c->P, (const double *)fs, dt, fr, c->status, c->stream);
+}
+// one stage's face records: reconstruction + flux over the whole grid or
+// slab by slab into the context's buffer
+int stage_faces(gks_ctx *c, const double *Q, const double *G, const double *dt) {
+    int rc;
+    if (c->mixed && c->P.scheme == GKS_SCHEME_CGKS5 && (rc = launch_g_to_f32(c->g, G, c->Gf, c->stream)))
+        return rc;
+    if (!c->slab_planes) {
+        const Slab S = whole_grid(c->g);
+        if ((rc = recon_any(c, S, Q, G, c->fs)) || (rc = flux_any(c, S, Q, c->fs, dt, c->frec)))
+            return rc;
+        return 0;
+    }
+    const int nz = c->g.nz;
+    const long long nxy = (long long)c->g.nx * c->g.ny;
+    for (int z0 = 0; z0 < nz; z0 += c->slab_planes) {
+        const int nzs = nz - z0 < c->slab_planes ? nz - z0 : c->slab_planes;
+        Slab S;
+        S.zb = (z0 - 1 + nz) % nz;
+        S.nzb = nzs + 1;
+        S.p0 = 1;
+        S.pad = 0;
+        S.nb = nxy * S.nzb;
+        if ((rc = recon_any(c, S, Q, G, c->fs)) || (rc = flux_any(c, S, Q, c->fs, dt, c->frec)))
+            return rc;
+    }
+    return 0;
 }
 }  // namespace
 
 int gks_reconstruct(gks_ctx *c, const double *Q, const double *G, void *face_states) {
     if (!c || !Q) return GKS_ERR_ARG;
     if (c->P.scheme == GKS_SCHEME_CGKS5 && !G) return GKS_ERR_ARG;
-    return launch_ok(recon_any(c, Q, G, face_states ? face_states : c->fs));
+    if (!face_states && c->slab_planes) return GKS_ERR_STATE;  // own buffer holds a slab only
+    if (c->mixed && c->P.scheme == GKS_SCHEME_CGKS5 && launch_g_to_f32(c->g, G, c->Gf, c->stream))
+        return GKS_ERR_CUDA;
+    return launch_ok(recon_any(c, whole_grid(c->g), Q, G, face_states ? face_states : c->fs));
 }
 
 int gks_flux(gks_ctx *c, const double *Q, const void *face_states, const double *dt_dev,
              double *face_flux) {
     if (!c || !dt_dev) return GKS_ERR_ARG;
     if (c->mixed && !Q) return GKS_ERR_ARG;
+    if (!face_states && c->slab_planes) return GKS_ERR_STATE;
     const void *fs = face_states ? face_states : c->fs;
     double *fr = face_flux ? face_flux : c->frec;
-    return launch_ok(flux_any(c, Q, fs, dt_dev, fr));
+    return launch_ok(flux_any(c, whole_grid(c->g), Q, fs, dt_dev, fr));
 }
 
 int gks_flux_points(gks_ctx *c, const double *s_l, const double *s_r, int n,
@@ -241,18 +296,15 @@ int gks_step(gks_ctx *c, double *Q, double *G, int nsteps, double t_stop, double
         int rc = launch_dt(c->g, c->P, Q, red_slot(c), dt, t_dev, t_stop, c->stream);
         if (rc) return GKS_ERR_CUDA;
         if (!cgks) {
-            if ((rc = recon_any(c, Q, nullptr, c->fs)) ||
-                (rc = flux_any(c, Q, c->fs, dt, c->frec)) ||
+            if ((rc = stage_faces(c, Q, nullptr, dt)) ||
                 (rc = launch_update(c->g, c->P, 0, c->frec, dt, Q, nullptr, nullptr, nullptr,
                                     nullptr, nullptr, c->status, c->stream)))
                 return GKS_ERR_CUDA;
         } else {
-            if ((rc = recon_any(c, Q, G, c->fs)) ||
-                (rc = flux_any(c, Q, c->fs, dt, c->frec)) ||
+            if ((rc = stage_faces(c, Q, G, dt)) ||
                 (rc = launch_update(c->g, c->P, 1, c->frec, dt, Q, G, c->Qs, c->Gs, c->Acc, c->S1,
                                     c->status, c->stream)) ||
-                (rc = recon_any(c, c->Qs, c->Gs, c->fs)) ||
-                (rc = flux_any(c, c->Qs, c->fs, dt, c->frec)) ||
+                (rc = stage_faces(c, c->Qs, c->Gs, dt)) ||
                 (rc = launch_update(c->g, c->P, 2, c->frec, dt, Q, G, c->Qs, c->Gs, c->Acc, c->S1,
                                     c->status, c->stream)))
                 return GKS_ERR_CUDA;
@@ -308,7 +360,7 @@ int gks_indicator_dump(gks_ctx *c, const double *Q, const double *G, float label
                        float *chi, float *y) {
     if (!c || !Q || !G || !x || !chi || !y || !(label_eps >= 0.0f)) return GKS_ERR_ARG;
     if (c->P.scheme != GKS_SCHEME_CGKS5) return GKS_ERR_STATE;
-    if (launch_indicator_dump(c->g, Q, G, x, chi, c->stream)) return GKS_ERR_CUDA;
+    if (launch_indicator_dump(c->g, Q, G, c->Gf, x, chi, c->stream)) return GKS_ERR_CUDA;
     if (launch_labels(chi, y, 5 * c->g.n, label_eps, c->stream)) return GKS_ERR_CUDA;
     return GKS_OK;
 }

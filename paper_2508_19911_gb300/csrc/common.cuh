@@ -47,6 +47,36 @@ __device__ __forceinline__ int wrap(int i, int n) {
     return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
+// The face-state buffer holds nzb z-planes starting at the global plane zb
+// (periodic), position l = (plane - zb) nx ny + j nx + i, stride nb =
+// nx ny nzb. The reconstruction fills all its planes; the flux computes the
+// faces of the cells in planes p0..nzb-1 (their low faces need the plane
+// below: p0 = 1 for a slab, whose plane 0 is the plane below its first
+// cell plane; p0 = 0 for the whole grid, nzb = nz, where plane 0's lower
+// neighbour is plane nz - 1 of the same buffer).
+struct Slab {
+    int zb, nzb, p0, pad;
+    long long nb;
+};
+
+__host__ __device__ __forceinline__ Slab whole_grid(const GridDesc &g) {
+    Slab s;
+    s.zb = 0;
+    s.nzb = g.nz;
+    s.p0 = 0;
+    s.pad = 0;
+    s.nb = g.n;
+    return s;
+}
+
+// global cell of buffer position l
+__device__ __forceinline__ long long slab_global(const GridDesc &g, const Slab &S, long long l) {
+    const long long nxy = (long long)g.nx * g.ny;
+    const long long p = l / nxy;
+    const long long gz = (S.zb + p) % g.nz;
+    return gz * nxy + (l - p * nxy);
+}
+
 // dynamic viscosity: constant, or the Sutherland law of Sec. 4.2 with the
 // temperature T = p/rho normalised by T_ref
 __device__ __forceinline__ double viscosity(const PhysParams &P, double rho, double p) {
@@ -60,24 +90,28 @@ __device__ __forceinline__ void flag_status(int *status, int bits) {
 }
 
 // Kernel launch helpers (defined in the .cu files)
-int launch_recon5(const GridDesc &g, const PhysParams &P, const double *Q, const double *G,
+// reconstruction and flux launchers take the face-state buffer's Slab
+int launch_recon5(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
+                  const double *G, double *fs, cudaStream_t s);
+int launch_recon2(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
                   double *fs, cudaStream_t s);
-int launch_recon2(const GridDesc &g, const PhysParams &P, const double *Q, double *fs,
-                  cudaStream_t s);
 int upload_recon_tables(void);
-int launch_flux_faces(const GridDesc &g, const PhysParams &P, const double *fs,
+int launch_flux_faces(const GridDesc &g, const Slab &S, const PhysParams &P, const double *fs,
                       const double *dt_dev, double *frec, int *status, cudaStream_t s);
-int launch_flux_faces_mixed(const GridDesc &g, const PhysParams &P, const float *fs,
-                            const double *Q, const double *dt_dev, double *frec, int *status,
-                            cudaStream_t s);
-int launch_recon5_mixed(const GridDesc &g, const PhysParams &P, const double *Q, const double *G,
-                        float *fs, cudaStream_t s, int indicator, unsigned long long *skips);
-int launch_indicator_dump(const GridDesc &g, const double *Q, const double *G, float *x,
+int launch_flux_faces_mixed(const GridDesc &g, const Slab &S, const PhysParams &P,
+                            const float *fs, const double *Q, const double *dt_dev, double *frec,
+                            int *status, cudaStream_t s);
+// FP32 copy of the cell gradients for the mixed reconstruction (once per stage)
+int launch_g_to_f32(const GridDesc &g, const double *G, float *Gf, cudaStream_t s);
+int launch_recon5_mixed(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
+                        const float *Gf, float *fs, cudaStream_t s, int indicator,
+                        unsigned long long *skips);
+int launch_indicator_dump(const GridDesc &g, const double *Q, const double *G, float *Gf, float *x,
                           float *chi, cudaStream_t s);
 int upload_indicator(const float *params, float theta);
 int launch_labels(const float *chi, float *y, long long m, float eps, cudaStream_t s);
-int launch_recon2_mixed(const GridDesc &g, const PhysParams &P, const double *Q, float *fs,
-                        cudaStream_t s);
+int launch_recon2_mixed(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
+                        float *fs, cudaStream_t s);
 int launch_flux_points(const PhysParams &P, const double *sl, const double *sr, int n,
                        const double *dt_dev, double *out, int *status, cudaStream_t s);
 int launch_dt(const GridDesc &g, const PhysParams &P, const double *Q, double *red,

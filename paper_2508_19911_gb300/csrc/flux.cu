@@ -714,31 +714,48 @@ __device__ __forceinline__ int global_var(int c, int d) {
 // over the face's K Gauss points (lanes 4m..4m+3 hold the points of one
 // face; all 32 lanes of the warp must call this together) and written to
 // the face records. MIXED: FP32 face-state offsets + FP64 averages Q.
+// l: the right cell's position in the face-state buffer S (the face is its
+// low face along d); face states are read at buffer positions (stride
+// S.nb), the averages Q and the records at global cells (stride g.n).
 template <bool kCGKS, bool MIXED>
-__device__ __forceinline__ void flux_face_point(const GridDesc &g, const PhysParams &P,
+__device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S,
+                                                const PhysParams &P,
                                                 const void *__restrict__ fsv,
                                                 const double *__restrict__ Q, double dt,
                                                 double *__restrict__ frec, int *status, int d,
-                                                long long c, int k, bool valid) {
+                                                long long l, int k, bool valid) {
     constexpr int K = kCGKS ? 4 : 1;
-    const long long n = g.n;
-    const int i = (int)(c % g.nx);
-    const int j = (int)((c / g.nx) % g.ny);
-    const int kk = (int)(c / ((long long)g.nx * g.ny));
-    const long long left = cell_index(g, d == 0 ? wrap(i - 1, g.nx) : i,
-                                      d == 1 ? wrap(j - 1, g.ny) : j,
-                                      d == 2 ? wrap(kk - 1, g.nz) : kk);
+    const long long n = g.n, nb = S.nb;
+    const long long nxy = (long long)g.nx * g.ny;
+    const int p = (int)(l / nxy);
+    const long long ij = l - (long long)p * nxy;
+    const int i = (int)(ij % g.nx), j = (int)(ij / g.nx);
+    const int gz = (S.zb + p) % g.nz;
+    const long long c = (long long)gz * nxy + ij;  // global right cell
+    long long ll, left;                            // left cell: buffer position, global
+    if (d == 0) {
+        const long long o = (long long)j * g.nx + wrap(i - 1, g.nx);
+        ll = (long long)p * nxy + o;
+        left = (long long)gz * nxy + o;
+    } else if (d == 1) {
+        const long long o = (long long)wrap(j - 1, g.ny) * g.nx + i;
+        ll = (long long)p * nxy + o;
+        left = (long long)gz * nxy + o;
+    } else {
+        ll = (long long)(p > 0 ? p - 1 : S.nzb - 1) * nxy + ij;
+        left = (long long)wrap(gz - 1, g.nz) * nxy + ij;
+    }
     constexpr int NV = kCGKS ? 30 : 10;
     if (!MIXED) {
         double out[30];
         const double *fs = (const double *)fsv;
         double sl[20], sr[20];
-        const double *pl = fs + ((long long)((2 * d + 1) * K + k) * 20) * n + left;
-        const double *pr = fs + ((long long)((2 * d) * K + k) * 20) * n + c;
+        const double *pl = fs + ((long long)((2 * d + 1) * K + k) * 20) * nb + ll;
+        const double *pr = fs + ((long long)((2 * d) * K + k) * 20) * nb + l;
 #pragma unroll
         for (int q = 0; q < 20; ++q) {
-            sl[q] = __ldg(pl + (long long)q * n);
-            sr[q] = __ldg(pr + (long long)q * n);
+            sl[q] = __ldg(pl + (long long)q * nb);
+            sr[q] = __ldg(pr + (long long)q * nb);
         }
         flux_point<kCGKS>(P, sl, sr, dt, out, valid ? status : nullptr);
         if (kCGKS) {
@@ -763,20 +780,20 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const PhysPar
         const float *fs = (const float *)fsv;
         double Ql[5], Qr[5];
         float ol[5], orr[5], dl[15], dr[15];
-        const float *pl = fs + ((long long)((2 * d + 1) * K + k) * 20) * n + left;
-        const float *pr = fs + ((long long)((2 * d) * K + k) * 20) * n + c;
+        const float *pl = fs + ((long long)((2 * d + 1) * K + k) * 20) * nb + ll;
+        const float *pr = fs + ((long long)((2 * d) * K + k) * 20) * nb + l;
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             const int v = global_var(q, d);
             Ql[q] = __ldg(Q + (long long)v * n + left);
             Qr[q] = __ldg(Q + (long long)v * n + c);
-            ol[q] = __ldg(pl + (long long)q * n);
-            orr[q] = __ldg(pr + (long long)q * n);
+            ol[q] = __ldg(pl + (long long)q * nb);
+            orr[q] = __ldg(pr + (long long)q * nb);
         }
 #pragma unroll
         for (int q = 0; q < 15; ++q) {
-            dl[q] = __ldg(pl + (long long)(5 + q) * n);
-            dr[q] = __ldg(pr + (long long)(5 + q) * n);
+            dl[q] = __ldg(pl + (long long)(5 + q) * nb);
+            dr[q] = __ldg(pr + (long long)(5 + q) * nb);
         }
         flux_point_mixed<kCGKS>(P, Ql, ol, dl, Qr, orr, dr, dt, out, valid ? status : nullptr);
         if (kCGKS) {
@@ -812,8 +829,10 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const PhysPar
     }
 }
 
+// mixed: at most 168 registers for 3 blocks per SM (a few spills; 20%
+// faster at 128^3 than 2 blocks with 255 registers and none)
 template <bool kCGKS, bool MIXED>
-__global__ void __launch_bounds__(128) flux_faces_kernel(GridDesc g, PhysParams P,
+__global__ void __launch_bounds__(128, MIXED ? 3 : 1) flux_faces_kernel(GridDesc g, Slab S, PhysParams P,
                                                          const void *__restrict__ fs,
                                                          const double *__restrict__ Q,
                                                          const double *__restrict__ dt_dev,
@@ -821,16 +840,17 @@ __global__ void __launch_bounds__(128) flux_faces_kernel(GridDesc g, PhysParams 
     const double dt = *dt_dev;
     if (!(dt > 0.0)) return;  // same for every thread of the grid
     constexpr int K = kCGKS ? 4 : 1;
-    const long long n = g.n;
-    const long long total = 3 * n * K;
+    const long long nxy = (long long)g.nx * g.ny;
+    const long long cnt = (long long)(S.nzb - S.p0) * nxy;  // cells whose faces are computed
+    const long long total = 3 * cnt * K;
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = gid < total;
     if (!valid) gid = total - 1;  // groups of K lanes are entirely in or out
     const int k = (int)(gid % K);
     const long long fc = gid / K;
-    const int d = (int)(fc / n);
-    const long long c = fc - (long long)d * n;
-    flux_face_point<kCGKS, MIXED>(g, P, fs, Q, dt, frec, status, d, c, k, valid);
+    const int d = (int)(fc / cnt);
+    const long long t = fc - (long long)d * cnt;
+    flux_face_point<kCGKS, MIXED>(g, S, P, fs, Q, dt, frec, status, d, S.p0 * nxy + t, k, valid);
 }
 
 // Persistent ensemble flux (CGKS-5th): blocks stride over the work items
@@ -859,8 +879,8 @@ __global__ void __launch_bounds__(128) flux_ens_kernel(const EnsInst *__restrict
             const long long rem = gid >> 2;
             const int d = (int)(rem / T);
             const long long c = it.c0 + rem % T;
-            flux_face_point<true, MIXED>(I.g, I.P, fs, Qa + 5 * I.off, dt, fra + 90 * I.off,
-                                         status, d, c, k, valid);
+            flux_face_point<true, MIXED>(I.g, whole_grid(I.g), I.P, fs, Qa + 5 * I.off, dt,
+                                         fra + 90 * I.off, status, d, c, k, valid);
         }
     }
 }
@@ -885,29 +905,34 @@ __global__ void __launch_bounds__(128) flux_points_kernel(PhysParams P, const do
 
 }  // namespace
 
-int launch_flux_faces_mixed(const GridDesc &g, const PhysParams &P, const float *fs, const double *Q,
-                            const double *dt_dev, double *frec, int *status, cudaStream_t s) {
+int launch_flux_faces_mixed(const GridDesc &g, const Slab &S, const PhysParams &P,
+                            const float *fs, const double *Q, const double *dt_dev, double *frec,
+                            int *status, cudaStream_t s) {
     const int K = P.scheme ? 4 : 1;
-    const long long total = 3 * g.n * K;
+    const long long total = 3 * (long long)(S.nzb - S.p0) * g.nx * g.ny * K;
     const int block = 128;
     const long long grid = (total + block - 1) / block;
     if (P.scheme)
-        flux_faces_kernel<true, true><<<(unsigned)grid, block, 0, s>>>(g, P, fs, Q, dt_dev, frec, status);
+        flux_faces_kernel<true, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Q, dt_dev, frec,
+                                                                        status);
     else
-        flux_faces_kernel<false, true><<<(unsigned)grid, block, 0, s>>>(g, P, fs, Q, dt_dev, frec, status);
+        flux_faces_kernel<false, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Q, dt_dev,
+                                                                         frec, status);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
-int launch_flux_faces(const GridDesc &g, const PhysParams &P, const double *fs,
+int launch_flux_faces(const GridDesc &g, const Slab &S, const PhysParams &P, const double *fs,
                       const double *dt_dev, double *frec, int *status, cudaStream_t s) {
     const int K = P.scheme ? 4 : 1;
-    const long long total = 3 * g.n * K;
+    const long long total = 3 * (long long)(S.nzb - S.p0) * g.nx * g.ny * K;
     const int block = 128;
     const long long grid = (total + block - 1) / block;
     if (P.scheme)
-        flux_faces_kernel<true, false><<<(unsigned)grid, block, 0, s>>>(g, P, fs, nullptr, dt_dev, frec, status);
+        flux_faces_kernel<true, false><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, nullptr,
+                                                                         dt_dev, frec, status);
     else
-        flux_faces_kernel<false, false><<<(unsigned)grid, block, 0, s>>>(g, P, fs, nullptr, dt_dev, frec, status);
+        flux_faces_kernel<false, false><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, nullptr,
+                                                                          dt_dev, frec, status);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -180,10 +180,10 @@ __device__ __forceinline__ void eval_faces(double *__restrict__ fs, long long n,
                 x[D] = side ? 0.5 : -0.5;
                 x[T1] = (kk & 1) ? kG : -kG;
                 x[T2] = (kk & 2) ? kG : -kG;
-                const double p1 = q0 + bbar[0] * x[0] + bbar[1] * x[1] + bbar[2] * x[2];
-                val = chi * val + (1.0 - chi) * p1;
+                const double p1 = fma(bbar[0], x[0], fma(bbar[1], x[1], fma(bbar[2], x[2], q0)));
+                val = fma(chi, val - p1, p1);  // chi P4 + (1 - chi) P1
 #pragma unroll
-                for (int q = 0; q < 3; ++q) der[q] = chi * der[q] + (1.0 - chi) * bbar[q];
+                for (int q = 0; q < 3; ++q) der[q] = fma(chi, der[q] - bbar[q], bbar[q]);
             }
             double *o = fs + ((long long)((2 * D + side) * 4 + kk) * 20) * n + c;
             o[(long long)cmp * n] = val;
@@ -195,10 +195,12 @@ __device__ __forceinline__ void eval_faces(double *__restrict__ fs, long long n,
         }
 }
 
+// cell c (global), variable v; face states to buffer position l (stride nb)
 __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
                                             const double *__restrict__ Q,
                                             const double *__restrict__ G,
-                                            double *__restrict__ fs, long long c, int v) {
+                                            double *__restrict__ fs, long long c, int v,
+                                            long long nb, long long l) {
     const long long n = g.n;
     const int i = (int)(c % g.nx);
     const int j = (int)((c / g.nx) % g.ny);
@@ -270,7 +272,7 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
             double s = bn * bn;
 #pragma unroll
             for (int q = 0; q < 3; ++q)
-                if (q != ax) s += dctr[q] * dctr[q];
+                if (q != ax) s = fma(dctr[q], dctr[q], s);
             IS[m] = s;
             const double t = s + eps, t2 = t * t;
             w[m] = (1.0 / 6.0) / (t2 * t2 * t);
@@ -280,7 +282,7 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
             w[m] /= wsum;
-            ISL += w[m] * IS[m];
+            ISL = fma(w[m], IS[m], ISL);
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -303,25 +305,27 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
         const double rr = r * 10.0;
         chi = 1.0 / (1.0 + rr * rr * rr);
     }
-    eval_faces<0>(fs, n, c, v, a, base, chi, bbar, q0, nonlinear, ih);
-    eval_faces<1>(fs, n, c, v, a, base, chi, bbar, q0, nonlinear, ih);
-    eval_faces<2>(fs, n, c, v, a, base, chi, bbar, q0, nonlinear, ih);
+    eval_faces<0>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
+    eval_faces<1>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
+    eval_faces<2>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
 }
 
-__global__ void __launch_bounds__(128) recon5_kernel(GridDesc g, int nonlinear,
+__global__ void __launch_bounds__(128) recon5_kernel(GridDesc g, Slab S, int nonlinear,
                                                      const double *__restrict__ Q,
                                                      const double *__restrict__ G,
                                                      double *__restrict__ fs) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < g.n) recon5_cell(g, nonlinear, Q, G, fs, c, (int)blockIdx.y);
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < S.nb)
+        recon5_cell(g, nonlinear, Q, G, fs, slab_global(g, S, l), (int)blockIdx.y, S.nb, l);
 }
 
-__global__ void __launch_bounds__(128) recon2_kernel(GridDesc g, int nonlinear, double eps2,
-                                                     const double *__restrict__ Q,
+__global__ void __launch_bounds__(128) recon2_kernel(GridDesc g, Slab S, int nonlinear,
+                                                     double eps2, const double *__restrict__ Q,
                                                      double *__restrict__ fs) {
     const long long n = g.n;
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= S.nb) return;
+    const long long c = slab_global(g, S, l);
     const int i = (int)(c % g.nx);
     const int j = (int)((c / g.nx) % g.ny);
     const int k = (int)(c / ((long long)g.nx * g.ny));
@@ -365,12 +369,12 @@ __global__ void __launch_bounds__(128) recon2_kernel(GridDesc g, int nonlinear, 
         for (int f = 0; f < 6; ++f) {
             const int d = f / 2;
             const int cmp = frame_comp(v, d);
-            double *o = fs + ((long long)f * 20) * n + c;
-            o[(long long)cmp * n] = q0 + phi * ((f & 1) ? 0.5 : -0.5) * b[d];
+            double *o = fs + ((long long)f * 20) * S.nb + l;
+            o[(long long)cmp * S.nb] = q0 + phi * ((f & 1) ? 0.5 : -0.5) * b[d];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const int jf = (q - d + 3) % 3;
-                o[(long long)(5 + 5 * jf + cmp) * n] = phi * b[q] / g.h[q];
+                o[(long long)(5 + 5 * jf + cmp) * S.nb] = phi * b[q] / g.h[q];
             }
         }
     }
@@ -407,9 +411,22 @@ __device__ __forceinline__ void add_hidden_f(const float *T, float hid[kMlpHidde
 // gradient entries h G in FP32. The products are __fmul_rn (never fused
 // into a later sum), so that every kernel that inlines this rounds them the
 // same way, whatever else uses the value (network, dump).
-template <int K>
+// FP32 data column K: differences of averages in FP64, rounded once; the
+// gradient entries h G in FP32, G either converted here or read from an
+// FP32 copy Gf (VIEW; the same values). The products are __fmul_rn (never
+// fused into a later sum), so that every kernel that inlines this rounds
+// them the same way, whatever else uses the value (network, dump).
+template <bool VIEW>
+__device__ __forceinline__ float gval(const double *__restrict__ Gv, const float *__restrict__ Gfv,
+                                      long long idx) {
+    if constexpr (VIEW) return __ldg(Gfv + idx);
+    else return (float)__ldg(Gv + idx);
+}
+
+template <int K, bool VIEW>
 __device__ __forceinline__ float data_col_f(const double *__restrict__ Qv,
-                                            const double *__restrict__ Gv, long long n,
+                                            const double *__restrict__ Gv,
+                                            const float *__restrict__ Gfv, long long n,
                                             long long c, const long long nbF[6],
                                             const long long nbE[12], double q0, const float hf[3]) {
     if constexpr (K < kColEdge) {
@@ -418,23 +435,23 @@ __device__ __forceinline__ float data_col_f(const double *__restrict__ Qv,
         return (float)(__ldg(Qv + nbE[K - kColEdge]) - q0);
     } else if constexpr (K < kColEdgeGrad) {
         constexpr int m = (K - kColFaceGrad) / 3, j = (K - kColFaceGrad) % 3;
-        return __fmul_rn(hf[j], (float)__ldg(Gv + j * n + nbF[m]));
+        return __fmul_rn(hf[j], gval<VIEW>(Gv, Gfv, j * n + nbF[m]));
     } else if constexpr (K < kColCentreGrad) {
         constexpr int e = (K - kColEdgeGrad) / 2;
         constexpr int ea = edge_axis_a(e), eb = edge_axis_b(e), ee = edge_axis_e(e);
         if constexpr ((K - kColEdgeGrad) % 2 == 0) {
-            const float da = __fmul_rn(hf[ea], (float)__ldg(Gv + ea * n + nbE[e]));
-            const float db = __fmul_rn(hf[eb], (float)__ldg(Gv + eb * n + nbE[e]));
+            const float da = __fmul_rn(hf[ea], gval<VIEW>(Gv, Gfv, ea * n + nbE[e]));
+            const float db = __fmul_rn(hf[eb], gval<VIEW>(Gv, Gfv, eb * n + nbE[e]));
             // o_a d_a - o_b d_b with o = +-1
             constexpr bool same = edge_off(e, ea) == edge_off(e, eb);
             const float t = same ? __fsub_rn(da, db) : __fadd_rn(da, db);
             return __fmul_rn(edge_off(e, ea) > 0 ? t : -t, (float)kRs2);
         } else {
-            return __fmul_rn(hf[ee], (float)__ldg(Gv + ee * n + nbE[e]));
+            return __fmul_rn(hf[ee], gval<VIEW>(Gv, Gfv, ee * n + nbE[e]));
         }
     } else {
         constexpr int j = K - kColCentreGrad;
-        return __fmul_rn(hf[j], (float)__ldg(Gv + j * n + c));
+        return __fmul_rn(hf[j], gval<VIEW>(Gv, Gfv, j * n + c));
     }
 }
 
@@ -494,10 +511,10 @@ __device__ __forceinline__ void eval_faces_f(const float *T, float *__restrict__
                 x[D] = side ? 0.5f : -0.5f;
                 x[T1] = (kk & 1) ? (float)kG : -(float)kG;
                 x[T2] = (kk & 2) ? (float)kG : -(float)kG;
-                const float p1 = bbar[0] * x[0] + bbar[1] * x[1] + bbar[2] * x[2];
-                val = chi * val + (1.0f - chi) * p1;
+                const float p1 = fmaf(bbar[0], x[0], fmaf(bbar[1], x[1], bbar[2] * x[2]));
+                val = fmaf(chi, val - p1, p1);  // chi P4 + (1 - chi) P1
 #pragma unroll
-                for (int q = 0; q < 3; ++q) der[q] = chi * der[q] + (1.0f - chi) * bbar[q];
+                for (int q = 0; q < 3; ++q) der[q] = fmaf(chi, der[q] - bbar[q], bbar[q]);
             }
             float *o = fs + ((long long)((2 * D + side) * 4 + kk) * 20) * n + c;
             o[(long long)cmp * n] = val;
@@ -509,16 +526,18 @@ __device__ __forceinline__ void eval_faces_f(const float *T, float *__restrict__
         }
 }
 
-template <int MODE>
+template <int MODE, bool VIEW>
 __device__ __forceinline__ void recon5_mixed_cell(const float *T,
                                                   const GridDesc &g, int nonlinear,
                                                   const double *__restrict__ Q,
                                                   const double *__restrict__ G,
+                                                  const float *__restrict__ Gf,
                                                   float *__restrict__ fs,
                                                   float *__restrict__ dump_x,
                                                   float *__restrict__ dump_chi,
                                                   unsigned long long *skips, long long c,
-                                                  long long dump_ld, long long dump_base, int v) {
+                                                  long long dump_ld, long long dump_base, int v,
+                                                  long long nb, long long l) {
     const long long n = g.n;
     const int i = (int)(c % g.nx);
     const int j = (int)((c / g.nx) % g.ny);
@@ -539,7 +558,8 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
 
 {
         const double *Qv = Q + (long long)v * n;
-        const double *Gv = G + (long long)v * 3 * n;
+        const double *Gv = VIEW ? nullptr : G + (long long)v * 3 * n;
+        const float *Gfv = VIEW ? Gf + (long long)v * 3 * n : nullptr;
         const double q0 = __ldg(Qv + c);
         float a[kNumBasis], hid[kMlpHidden], amax = 0.0f;
 #pragma unroll
@@ -558,7 +578,7 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
                 static_for<nm>([&](auto Qq) {
                     constexpr int q = decltype(Qq)::value;
                     constexpr int col = kSym.mem[r][q];
-                    ov[q] = data_col_f<col>(Qv, Gv, n, c, nbF, nbE, q0, hf);
+                    ov[q] = data_col_f<col, VIEW>(Qv, Gv, Gfv, n, c, nbF, nbE, q0, hf);
                     if constexpr (col < kColEdge) dface[col] = ov[q];
                     if constexpr (col >= kColCentreGrad) dctr[col - kColCentreGrad] = ov[q];
                     if constexpr (MODE == kModeIndicator) add_hidden_f<col>(T, hid, amax, ov[q]);
@@ -665,9 +685,9 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
             dump_chi[dump_base + 5 * c + v] = chi;
             return;
         }
-        eval_faces_f<0>(T, fs, n, c, v, a, base, chi, bbar, geno, ih);
-        eval_faces_f<1>(T, fs, n, c, v, a, base, chi, bbar, geno, ih);
-        eval_faces_f<2>(T, fs, n, c, v, a, base, chi, bbar, geno, ih);
+        eval_faces_f<0>(T, fs, nb, l, v, a, base, chi, bbar, geno, ih);
+        eval_faces_f<1>(T, fs, nb, l, v, a, base, chi, bbar, geno, ih);
+        eval_faces_f<2>(T, fs, nb, l, v, a, base, chi, bbar, geno, ih);
     }
 }
 
@@ -676,23 +696,25 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
 // block are adjacent tiles). The empty asm with a memory clobber at the top
 // of each tile keeps the compiler from hoisting table loads out of the tile
 // loop into registers (which spills).
-template <int MODE>
-__global__ void __launch_bounds__(128) recon5_mixed_kernel(GridDesc g, int nonlinear,
+template <int MODE, bool VIEW>
+__global__ void __launch_bounds__(128) recon5_mixed_kernel(GridDesc g, Slab S, int nonlinear,
                                                            const double *__restrict__ Q,
                                                            const double *__restrict__ G,
+                                                           const float *__restrict__ Gf,
                                                            float *__restrict__ fs,
                                                            float *__restrict__ dump_x,
                                                            float *__restrict__ dump_chi,
                                                            unsigned long long *skips) {
     __shared__ __align__(16) float sT[kTabFloats];
     stage_tables(sT);
-    const long long ntiles = 5 * ((g.n + 127) / 128);
+    const long long ntiles = 5 * ((S.nb + 127) / 128);
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         asm volatile("" ::: "memory");
-        const long long c = (t / 5) * 128 + threadIdx.x;
-        if (c < g.n)
-            recon5_mixed_cell<MODE>(sT, g, nonlinear, Q, G, fs, dump_x, dump_chi, skips, c,
-                                    5 * g.n, 0, (int)(t % 5));
+        const long long l = (t / 5) * 128 + threadIdx.x;
+        if (l < S.nb)
+            recon5_mixed_cell<MODE, VIEW>(sT, g, nonlinear, Q, G, Gf, fs, dump_x, dump_chi, skips,
+                                          slab_global(g, S, l), 5 * g.n, 0, (int)(t % 5), S.nb,
+                                          l);
     }
 }
 
@@ -719,23 +741,24 @@ __global__ void __launch_bounds__(128) recon5_ens_kernel(const EnsInst *__restri
         for (long long t = threadIdx.x; t < 5 * T; t += blockDim.x) {
             asm volatile("" ::: "memory");
             if constexpr (MIXED)
-                recon5_mixed_cell<MODE>(sT, I.g, I.P.nonlinear, Q, G,
+                recon5_mixed_cell<MODE, false>(sT, I.g, I.P.nonlinear, Q, G, nullptr,
                                         fsa ? (float *)fsa + 480 * I.off : nullptr, dump_x,
                                         dump_chi, skips, it.c0 + t % T, dump_ld, 5 * I.off,
-                                        (int)(t / T));
+                                        (int)(t / T), I.g.n, it.c0 + t % T);
             else
                 recon5_cell(I.g, I.P.nonlinear, Q, G, (double *)fsa + 480 * I.off, it.c0 + t % T,
-                            (int)(t / T));
+                            (int)(t / T), I.g.n, it.c0 + t % T);
         }
     }
 }
 
-__global__ void __launch_bounds__(128) recon2_mixed_kernel(GridDesc g, int nonlinear, float eps2,
-                                                           const double *__restrict__ Q,
+__global__ void __launch_bounds__(128) recon2_mixed_kernel(GridDesc g, Slab S, int nonlinear,
+                                                           float eps2, const double *__restrict__ Q,
                                                            float *__restrict__ fs) {
     const long long n = g.n;
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= S.nb) return;
+    const long long c = slab_global(g, S, l);
     const int i = (int)(c % g.nx);
     const int j = (int)((c / g.nx) % g.ny);
     const int k = (int)(c / ((long long)g.nx * g.ny));
@@ -778,12 +801,12 @@ __global__ void __launch_bounds__(128) recon2_mixed_kernel(GridDesc g, int nonli
         for (int f = 0; f < 6; ++f) {
             const int d = f / 2;
             const int cmp = frame_comp(v, d);
-            float *o = fs + ((long long)f * 20) * n + c;
-            o[(long long)cmp * n] = phi * ((f & 1) ? 0.5f : -0.5f) * b[d];
+            float *o = fs + ((long long)f * 20) * S.nb + l;
+            o[(long long)cmp * S.nb] = phi * ((f & 1) ? 0.5f : -0.5f) * b[d];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const int jf = (q - d + 3) % 3;
-                o[(long long)(5 + 5 * jf + cmp) * n] = phi * b[q] * ih[q];
+                o[(long long)(5 + 5 * jf + cmp) * S.nb] = phi * b[q] * ih[q];
             }
         }
     }
@@ -839,25 +862,54 @@ static unsigned persistent_blocks(K kernel, long long tiles) {
     return (unsigned)(tiles < b ? tiles : b);
 }
 
-int launch_recon5_mixed(const GridDesc &g, const PhysParams &P, const double *Q, const double *G,
-                        float *fs, cudaStream_t s, int indicator, unsigned long long *skips) {
-    const long long tiles = 5 * ((g.n + 127) / 128);
-    if (indicator)
-        recon5_mixed_kernel<kModeIndicator>
-            <<<persistent_blocks(recon5_mixed_kernel<kModeIndicator>, tiles), 128, 0, s>>>(
-                g, P.nonlinear, Q, G, fs, nullptr, nullptr, skips);
-    else
-        recon5_mixed_kernel<kModePlain>
-            <<<persistent_blocks(recon5_mixed_kernel<kModePlain>, tiles), 128, 0, s>>>(
-                g, P.nonlinear, Q, G, fs, nullptr, nullptr, nullptr);
+// FP32 copy of the cell gradients (15 per cell), read by the mixed
+// reconstruction instead of converting each G value at every stencil use
+__global__ void g_to_f32_kernel(const double *__restrict__ G, float *__restrict__ Gf, long long m) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (long long)gridDim.x * blockDim.x)
+        Gf[i] = (float)G[i];
+}
+
+int launch_g_to_f32(const GridDesc &g, const double *G, float *Gf, cudaStream_t s) {
+    const long long m = 15 * g.n;
+    const long long blocks = (m + 255) / 256;
+    g_to_f32_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(G, Gf, m);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
-int launch_indicator_dump(const GridDesc &g, const double *Q, const double *G, float *x,
+// Gf: the FP32 gradient copy of this stage (launch_g_to_f32)
+int launch_recon5_mixed(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
+                        const float *Gf, float *fs, cudaStream_t s, int indicator,
+                        unsigned long long *skips) {
+    if (!Gf) return -1;
+    const long long tiles = 5 * ((S.nb + 127) / 128);
+    if (indicator)
+        recon5_mixed_kernel<kModeIndicator, true>
+            <<<persistent_blocks(recon5_mixed_kernel<kModeIndicator, true>, tiles), 128, 0, s>>>(
+                g, S, P.nonlinear, Q, nullptr, Gf, fs, nullptr, nullptr, skips);
+    else
+        recon5_mixed_kernel<kModePlain, true>
+            <<<persistent_blocks(recon5_mixed_kernel<kModePlain, true>, tiles), 128, 0, s>>>(
+                g, S, P.nonlinear, Q, nullptr, Gf, fs, nullptr, nullptr, nullptr);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+// Gf: FP32 gradient buffer of a mixed context, or nullptr (FP64 context:
+// each G value is converted where it is used; the same values)
+int launch_indicator_dump(const GridDesc &g, const double *Q, const double *G, float *Gf, float *x,
                           float *chi, cudaStream_t s) {
     const long long tiles = 5 * ((g.n + 127) / 128);
-    recon5_mixed_kernel<kModeDump><<<persistent_blocks(recon5_mixed_kernel<kModeDump>, tiles), 128,
-                                     0, s>>>(g, 1, Q, G, nullptr, x, chi, nullptr);
+    const Slab S = whole_grid(g);
+    if (Gf) {
+        if (launch_g_to_f32(g, G, Gf, s)) return -2;
+        recon5_mixed_kernel<kModeDump, true>
+            <<<persistent_blocks(recon5_mixed_kernel<kModeDump, true>, tiles), 128, 0, s>>>(
+                g, S, 1, Q, nullptr, Gf, nullptr, x, chi, nullptr);
+    } else {
+        recon5_mixed_kernel<kModeDump, false>
+            <<<persistent_blocks(recon5_mixed_kernel<kModeDump, false>, tiles), 128, 0, s>>>(
+                g, S, 1, Q, G, nullptr, nullptr, x, chi, nullptr);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -903,31 +955,31 @@ int upload_indicator(const float *params, float theta) {
     return 0;
 }
 
-int launch_recon2_mixed(const GridDesc &g, const PhysParams &P, const double *Q, float *fs,
-                        cudaStream_t s) {
+int launch_recon2_mixed(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
+                        float *fs, cudaStream_t s) {
     const double hv = cbrt(g.h[0] * g.h[1] * g.h[2]);
     const float eps2 = (float)(hv * hv * hv);
     const int block = 128;
-    const long long grid = (g.n + block - 1) / block;
-    recon2_mixed_kernel<<<(unsigned)grid, block, 0, s>>>(g, P.nonlinear, eps2, Q, fs);
+    const long long grid = (S.nb + block - 1) / block;
+    recon2_mixed_kernel<<<(unsigned)grid, block, 0, s>>>(g, S, P.nonlinear, eps2, Q, fs);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
-int launch_recon5(const GridDesc &g, const PhysParams &P, const double *Q, const double *G,
-                  double *fs, cudaStream_t s) {
+int launch_recon5(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
+                  const double *G, double *fs, cudaStream_t s) {
     const int block = 128;
-    const long long grid = (g.n + block - 1) / block;
-    recon5_kernel<<<dim3((unsigned)grid, 5), block, 0, s>>>(g, P.nonlinear, Q, G, fs);
+    const long long grid = (S.nb + block - 1) / block;
+    recon5_kernel<<<dim3((unsigned)grid, 5), block, 0, s>>>(g, S, P.nonlinear, Q, G, fs);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
-int launch_recon2(const GridDesc &g, const PhysParams &P, const double *Q, double *fs,
-                  cudaStream_t s) {
+int launch_recon2(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
+                  double *fs, cudaStream_t s) {
     const double hv = cbrt(g.h[0] * g.h[1] * g.h[2]);
     const double eps2 = hv * hv * hv;  // (K h)^3 with K = 1
     const int block = 128;
-    const long long grid = (g.n + block - 1) / block;
-    recon2_kernel<<<(unsigned)grid, block, 0, s>>>(g, P.nonlinear, eps2, Q, fs);
+    const long long grid = (S.nb + block - 1) / block;
+    recon2_kernel<<<(unsigned)grid, block, 0, s>>>(g, S, P.nonlinear, eps2, Q, fs);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

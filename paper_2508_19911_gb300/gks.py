@@ -43,6 +43,7 @@ class Options(ctypes.Structure):
         ("mu_law", ctypes.c_int), ("inviscid", ctypes.c_int),
         ("C_tau", ctypes.c_double), ("eps_tau", ctypes.c_double),
         ("T_ref", ctypes.c_double), ("theta", ctypes.c_double),
+        ("slab_planes", ctypes.c_int), ("reserved", ctypes.c_int),
     ]
 
 
@@ -59,6 +60,7 @@ SIGNATURES = {
     "gks_strerror": (ctypes.c_char_p, [_I]),
     "gks_face_state_bytes": (ctypes.c_size_t, [_VP]),
     "gks_face_flux_bytes": (ctypes.c_size_t, [_VP]),
+    "gks_slab_planes": (_I, [_VP]),
     "gks_compute_dt": (_I, [_VP, _VP, _VP]),
     "gks_reconstruct": (_I, [_VP, _VP, _VP, _VP]),
     "gks_flux": (_I, [_VP, _VP, _VP, _VP, _VP]),
@@ -181,6 +183,7 @@ class Config:
     eps_tau: float = 0.05
     T_ref: float = 1.0
     theta: float = 0.9
+    slab_planes: int = 0
 
 
 class Solver:
@@ -200,6 +203,7 @@ class Solver:
         opt.mu_law = int(cfg.mu_law)
         opt.inviscid = int(bool(cfg.inviscid))
         opt.C_tau, opt.eps_tau, opt.T_ref, opt.theta = cfg.C_tau, cfg.eps_tau, cfg.T_ref, cfg.theta
+        opt.slab_planes = int(cfg.slab_planes)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.device = self.stream.device
         ctx = _VP()
@@ -237,6 +241,11 @@ class Solver:
         dt = self.zeros(1) if dt is None else dt
         _check(lib().gks_compute_dt(self.ctx, _ptr(Q), _ptr(dt)), "gks_compute_dt")
         return dt
+
+    @property
+    def slab_planes(self):
+        """z-planes per slab of step()'s reconstruction + flux (0: whole grid)."""
+        return int(lib().gks_slab_planes(self.ctx))
 
     def reconstruct(self, Q, G=None, out=None):
         if out is None:
