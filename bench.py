@@ -78,6 +78,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the host round trip (very large grids)")
+    ap.add_argument("--c5", action="store_true",
+                    help="FP64 vs mixed vs mixed + learned indicator on one isotropic-turbulence "
+                         "state (default 512^3, z-slabs), with the KE error against FP64")
+    ap.add_argument("--c4", action="store_true",
+                    help="batched ensemble of 64 uneven 2D instances (double shear layers, "
+                         "four-quadrant Riemann problems), autotuned tiles, graph-replayed steps")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="--c5: FP64 steps (an FP64 step at 512^3 takes ~23 s)")
     return ap.parse_args()
 
 
@@ -444,8 +452,156 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
+def run_c5(args):
+    """FP64 and mixed(+learned) CGKS-5th on one seeded isotropic-turbulence
+    state (Mt 0.5, k0 8, seed 103; 512^3 by default, z-slabs chosen by the
+    library): throughput of each path, its slab size and peak device memory,
+    and the relative L2 error of the per-cell kinetic energy of the mixed
+    paths against FP64 after the same steps."""
+    import torch
+
+    from paper_2508_19911_gb300 import gks
+    from paper_2508_19911_gb300 import workloads as wl
+
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    n = args.n
+    t0 = time.time()
+    Qh, Gh, grid, info = wl.isotropic_turbulence(n, Mt=0.5, k0=8.0, seed=103)
+    gen_s = time.time() - t0
+    cells = n ** 3
+    params, ind_info = trained_indicator(torch, dev)
+
+    def ke(Q):
+        return 0.5 * (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0]
+
+    paths, ke_ref, results = [("fp64", False), ("mixed", False), ("mixed", True)], None, {}
+    for prec, learned in paths:
+        tag = "learned" if learned else prec
+        steps = args.fp64_steps if prec == "fp64" else args.steps
+        warm = 1 if prec == "fp64" else args.warmup
+        s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision=prec,
+                                  indicator=learned, mu=1e-3, slab_planes=args.slab_planes),
+                       stream)
+        if learned:
+            s.set_indicator(params, theta=ind_info["theta"])
+        Q = torch.tensor(Qh, device=dev)
+        G = torch.tensor(Gh, device=dev)
+        torch.cuda.reset_peak_memory_stats(dev)
+        free0, total = torch.cuda.mem_get_info(dev)
+        for _ in range(warm):
+            s.step(Q, G, nsteps=1, sync=False)
+        torch.cuda.synchronize()
+        with ClockSampler(0) as clk:
+            ms = time_steps(torch, s, Q, G, steps, stream)
+        if s.status():
+            raise RuntimeError(f"non-physical state in the {tag} run")
+        free1, _ = torch.cuda.mem_get_info(dev)
+        # KE after the first min(warm + steps) steps of each path: rerun from
+        # the initial state for the comparison step count
+        results[tag] = {"value": cells * 2 * steps / (ms / 1e3), "unit": "cell-stage/s",
+                        "ms_per_step": ms / steps, "steps": steps, "warmup": warm,
+                        "slab_planes": s.slab_planes,
+                        "device_bytes_in_use": int(total - free1), "clocks": clk.summary()}
+        s.close()
+        del Q, G
+        torch.cuda.empty_cache()
+    # accuracy: the same number of steps (the FP64 count) on every path
+    k = args.fp64_steps + 1
+    kes = {}
+    for prec, learned in paths:
+        tag = "learned" if learned else prec
+        s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision=prec,
+                                  indicator=learned, mu=1e-3, slab_planes=args.slab_planes),
+                       stream)
+        if learned:
+            s.set_indicator(params, theta=ind_info["theta"])
+        Q = torch.tensor(Qh, device=dev)
+        G = torch.tensor(Gh, device=dev)
+        s.step(Q, G, nsteps=k)
+        if learned:
+            results[tag]["skip_fraction"] = s.indicator_skips() / (5 * cells * 2 * k)
+        kes[tag] = ke(Q)
+        s.close()
+        del Q, G
+        torch.cuda.empty_cache()
+    for tag in ("mixed", "learned"):
+        d = kes[tag] - kes["fp64"]
+        results[tag]["ke_rel_l2_vs_fp64"] = float(torch.linalg.vector_norm(d) /
+                                                  torch.linalg.vector_norm(kes["fp64"]))
+        results[tag]["ke_steps"] = k
+    line = {
+        "metric": METRIC, "value": results["learned"]["value"], "unit": "cell-stage/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": results["learned"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded isotropic turbulence)",
+        "config": {"workload": f"isotropic_turbulence_{n}^3_cgks5_fp64_vs_mixed_learned",
+                   "cells": cells, "Mt": 0.5, "k0": 8, "seed": 103, "mu": 1e-3,
+                   "taylor_lambda": float(info["taylor_lambda"]), "generation_s": gen_s,
+                   "indicator": ind_info},
+        "paths": results,
+    }
+    return line
+
+
+def run_c4(args):
+    """The batched ensemble (row a9): 64 seeded 2D instances of 64^2..512^2
+    cells advanced together by persistent launches over one work list,
+    captured in a CUDA graph, tile size from the autotuner; cell-stage
+    updates per second over all instances."""
+    import torch
+
+    from paper_2508_19911_gb300 import gks
+    from paper_2508_19911_gb300 import workloads as wl
+
+    dev = torch.device("cuda:0")
+    insts = wl.ensemble_instances(64, seed0=2000)
+    spec = [dict(n=g.n, L=g.L, **ph) for _, _, g, ph in insts]
+    cells = sum(g.n[0] * g.n[1] * g.n[2] for _, _, g, _ in insts)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        e = gks.Ensemble(spec, precision=prec)
+        for i, (Q, G, _, _) in enumerate(insts):
+            q, gg = e.views(i)
+            q.copy_(torch.tensor(Q, device=dev))
+            gg.copy_(torch.tensor(G, device=dev))
+        tile, tune_ms = e.autotune()
+        e.step(args.warmup, graph=True)
+        torch.cuda.synchronize()
+        with ClockSampler(0) as clk:
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(torch.cuda.current_stream(dev))
+            e.step(args.steps, graph=True)
+            t1.record(torch.cuda.current_stream(dev))
+            torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        e.times()  # raises if an instance became non-physical
+        out[prec] = {"value": cells * 2 * args.steps / (ms / 1e3), "unit": "cell-stage/s",
+                     "ms_per_step": ms / args.steps, "tile": tile, "autotune_ms_per_step": tune_ms,
+                     "clocks": clk.summary()}
+        e.close()
+        torch.cuda.empty_cache()
+    return {
+        "metric": METRIC, "value": out["fp64"]["value"], "unit": "cell-stage/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["fp64"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded 2D double shear layers and four-quadrant Riemann problems)",
+        "config": {"workload": "ensemble_64x2d_64..512", "instances": 64, "cells": cells,
+                   "launches_per_step": 7},
+        "paths": out,
+    }
+
+
 def main():
     args = parse()
+    if args.c4:
+        print(json.dumps(run_c4(args)))
+        return
+    if args.c5:
+        print(json.dumps(run_c5(args)))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -193,13 +193,16 @@ __device__ __forceinline__ void time_integrals_pair(double dt, double tau, doubl
 
 // Coefficients of terms 2..6 (k = 1..5) in F^n = sum_k al_k X_k and
 // F_t = sum_k be_k X_k, al_k = (4 C_k(dt/2) - C_k(dt))/dt, be_k =
-// 4 (C_k(dt) - 2 C_k(dt/2))/dt^2. For dt >= 2 tau they are written out in
-// b = exp(-dt/(2 tau)) and a = 1 - b (>= 1 - 1/e: no cancellation),
-// e.g. al_4 = tau a (3 - b)/dt, be_4 = -4 tau a^2/dt^2; otherwise they
-// come from the time integrals (Taylor series for small dt/tau).
-__device__ __forceinline__ void time_coefficients(double dt, double tau, double al[6], double be[6]) {
-    if (tau > 0.0 && dt >= 2.0 * tau) {
-        const double b = exp(-0.5 * dt / tau), a = 1.0 - b;
+// 4 (C_k(dt) - 2 C_k(dt/2))/dt^2, written out in b = exp(-dt/(2 tau)) and
+// a = 1 - b, e.g. al_4 = tau a (3 - b)/dt, be_4 = -4 tau a^2/dt^2, for
+// dt >= x_min tau; below, from the time integrals (Taylor series). For small
+// x = dt/tau the closed forms of al_1, al_2 cancel to O(x^2) of their terms
+// (relative error ~ 1e-16/x^2): x_min = 2 keeps FP64 accuracy, x_min = 0.01
+// (1e-12) suffices where the coefficients are rounded to FP32.
+__device__ __forceinline__ void time_coefficients(double dt, double tau, double al[6], double be[6],
+                                                  double x_min) {
+    if (tau > 0.0 && dt >= x_min * tau) {
+        const double a = -expm1(-0.5 * dt / tau), b = 1.0 - a;
         const double idt = 1.0 / dt;
         const double t2 = tau * tau;
         const double g = a * (3.0 - b) * idt;          // (4 E_h - E)/dt
@@ -505,27 +508,37 @@ __device__ __forceinline__ PrimFF to_prim_ff(const ff s[5], ff gm1) {
 
 // Half-line starting moments of one side (SGN = +1: u > 0; -1: u < 0):
 // with y = sqrt(lam) U, m0 = (1 + SGN erf(y))/2 and m1 = U m0 + SGN
-// e^{-y^2}/(2 sqrt(pi lam)). For |y| <= 1 (subsonic states) erf and the
-// exponential come from one series in t_n = (-y^2)^n/n!:
-// e^{-y^2} = sum t_n, erf(y) = 2y/sqrt(pi) sum t_n/(2n+1), in float-float
-// (|t_n| <= 1/n!: 18 terms reach 2^-50); otherwise the FP64 erfc and exp.
-constexpr int kSeriesTerms = 18;
-__device__ __forceinline__ ffc series_inv(int n) {  // 1/n, n = 1..18
+// e^{-y^2}/(2 sqrt(pi lam)). For |y| <= 2 (every state below a component
+// Mach number of ~2.4) erf and the exponential come from one series in
+// t_n = (-y^2)^n/n!: e^{-y^2} = sum t_n, erf(y) = 2y/sqrt(pi) sum t_n/(2n+1),
+// in float-float (|t_n| <= 4^n/n!: 32 terms reach 2^-53; the largest term,
+// 10.7 at n = 4, costs one digit to cancellation); otherwise the FP64 erfc
+// and exp.
+constexpr int kSeriesTerms = 32;
+__device__ __forceinline__ ffc series_inv(int n) {  // 1/n, n = 1..32
     constexpr ffc t[kSeriesTerms + 1] = {
-        ff_const(0.0), ff_const(1.0), ff_const(1.0 / 2), ff_const(1.0 / 3), ff_const(1.0 / 4),
-        ff_const(1.0 / 5), ff_const(1.0 / 6), ff_const(1.0 / 7), ff_const(1.0 / 8),
-        ff_const(1.0 / 9), ff_const(1.0 / 10), ff_const(1.0 / 11), ff_const(1.0 / 12),
-        ff_const(1.0 / 13), ff_const(1.0 / 14), ff_const(1.0 / 15), ff_const(1.0 / 16),
-        ff_const(1.0 / 17), ff_const(1.0 / 18)};
+        ff_const(0.0), ff_const(1.0 / 1), ff_const(1.0 / 2), ff_const(1.0 / 3),
+        ff_const(1.0 / 4), ff_const(1.0 / 5), ff_const(1.0 / 6), ff_const(1.0 / 7),
+        ff_const(1.0 / 8), ff_const(1.0 / 9), ff_const(1.0 / 10), ff_const(1.0 / 11),
+        ff_const(1.0 / 12), ff_const(1.0 / 13), ff_const(1.0 / 14), ff_const(1.0 / 15),
+        ff_const(1.0 / 16), ff_const(1.0 / 17), ff_const(1.0 / 18), ff_const(1.0 / 19),
+        ff_const(1.0 / 20), ff_const(1.0 / 21), ff_const(1.0 / 22), ff_const(1.0 / 23),
+        ff_const(1.0 / 24), ff_const(1.0 / 25), ff_const(1.0 / 26), ff_const(1.0 / 27),
+        ff_const(1.0 / 28), ff_const(1.0 / 29), ff_const(1.0 / 30), ff_const(1.0 / 31),
+        ff_const(1.0 / 32)};
     return t[n];
 }
-__device__ __forceinline__ ffc series_inv_odd(int n) {  // 1/(2n+1), n = 1..18
+__device__ __forceinline__ ffc series_inv_odd(int n) {  // 1/(2n+1), n = 0..32
     constexpr ffc t[kSeriesTerms + 1] = {
-        ff_const(1.0), ff_const(1.0 / 3), ff_const(1.0 / 5), ff_const(1.0 / 7), ff_const(1.0 / 9),
-        ff_const(1.0 / 11), ff_const(1.0 / 13), ff_const(1.0 / 15), ff_const(1.0 / 17),
-        ff_const(1.0 / 19), ff_const(1.0 / 21), ff_const(1.0 / 23), ff_const(1.0 / 25),
-        ff_const(1.0 / 27), ff_const(1.0 / 29), ff_const(1.0 / 31), ff_const(1.0 / 33),
-        ff_const(1.0 / 35), ff_const(1.0 / 37)};
+        ff_const(1.0 / 1), ff_const(1.0 / 3), ff_const(1.0 / 5), ff_const(1.0 / 7),
+        ff_const(1.0 / 9), ff_const(1.0 / 11), ff_const(1.0 / 13), ff_const(1.0 / 15),
+        ff_const(1.0 / 17), ff_const(1.0 / 19), ff_const(1.0 / 21), ff_const(1.0 / 23),
+        ff_const(1.0 / 25), ff_const(1.0 / 27), ff_const(1.0 / 29), ff_const(1.0 / 31),
+        ff_const(1.0 / 33), ff_const(1.0 / 35), ff_const(1.0 / 37), ff_const(1.0 / 39),
+        ff_const(1.0 / 41), ff_const(1.0 / 43), ff_const(1.0 / 45), ff_const(1.0 / 47),
+        ff_const(1.0 / 49), ff_const(1.0 / 51), ff_const(1.0 / 53), ff_const(1.0 / 55),
+        ff_const(1.0 / 57), ff_const(1.0 / 59), ff_const(1.0 / 61), ff_const(1.0 / 63),
+        ff_const(1.0 / 65)};
     return t[n];
 }
 
@@ -533,7 +546,7 @@ template <int SGN>
 __device__ __forceinline__ void half_start_ff(const PrimFF &S, ff &m0, ff &m1) {
     const ff sl = ff_sqrt(S.lam);
     const ff y = ff_mul(sl, S.U);
-    if (fabsf(y.hi) <= 1.0f) {
+    if (fabsf(y.hi) <= 2.0f) {
         const ff w = ff_neg(ff_mul(y, y));
         ff t = ff_make(1.0f, 0.0f), se = t, sf = t;
 #pragma unroll
@@ -662,7 +675,7 @@ __device__ void flux_point_mixed(const PhysParams &P, const double Ql[5], const 
                            ? (P.eps_tau * dt + P.C_tau * (double)dpr * dt)
                            : (viscosity(P, ff_to_double(Z.rho), zp) / zp + P.C_tau * (double)dpr * dt);
     double ald[6], bed[6];
-    time_coefficients(dt, tau, ald, bed);
+    time_coefficients(dt, tau, ald, bed, 0.01);
     float al[6], be[6];
 #pragma unroll
     for (int k = 1; k < 6; ++k) {

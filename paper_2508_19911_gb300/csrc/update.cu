@@ -123,6 +123,9 @@ __device__ __forceinline__ void update_cell(const GridDesc &g, const PhysParams 
                              cell_index(g, i, wrap(j + 1, g.ny), k),
                              cell_index(g, i, j, wrap(k + 1, g.nz))};
     const double dt2 = dt * dt;
+    // 1/h once per thread (FP64 division is a multi-instruction sequence)
+    const double ih[3] = {1.0 / g.h[0], 1.0 / g.h[1], 1.0 / g.h[2]};
+    constexpr double kSixth = 1.0 / 6.0, kThird = 1.0 / 3.0;
     double out[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -130,8 +133,8 @@ __device__ __forceinline__ void update_cell(const GridDesc &g, const PhysParams 
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double *F = fr + (long long)d * 30 * n;
-            L += (F[(long long)v * n + hi[d]] - F[(long long)v * n + c]) / g.h[d];
-            Lt += (F[(long long)(5 + v) * n + hi[d]] - F[(long long)(5 + v) * n + c]) / g.h[d];
+            L += (F[(long long)v * n + hi[d]] - F[(long long)v * n + c]) * ih[d];
+            Lt += (F[(long long)(5 + v) * n + hi[d]] - F[(long long)(5 + v) * n + c]) * ih[d];
         }
         L = -L;
         Lt = -Lt;
@@ -143,7 +146,7 @@ __device__ __forceinline__ void update_cell(const GridDesc &g, const PhysParams 
             const double q = Q[qi];
             out[v] = q + 0.5 * dt * L + 0.125 * dt2 * Lt;
             Qs[qi] = out[v];
-            Acc[qi] = q + dt * L + dt2 / 6.0 * Lt;
+            Acc[qi] = q + dt * L + dt2 * kSixth * Lt;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const double *F = fr + (long long)d * 30 * n;
@@ -152,11 +155,11 @@ __device__ __forceinline__ void update_cell(const GridDesc &g, const PhysParams 
                 const double qr = F[(long long)(20 + v) * n + c];
                 const double qrt = F[(long long)(25 + v) * n + c];
                 const long long gi = ((long long)v * 3 + d) * n + c;
-                Gs[gi] = ((ql + 0.5 * dt * qlt) - (qr + 0.5 * dt * qrt)) / g.h[d];
-                S1[gi] = (ql - qr) / g.h[d];
+                Gs[gi] = ((ql + 0.5 * dt * qlt) - (qr + 0.5 * dt * qrt)) * ih[d];
+                S1[gi] = (ql - qr) * ih[d];
             }
         } else {
-            out[v] = Acc[qi] + dt2 / 3.0 * Lt;
+            out[v] = Acc[qi] + dt2 * kThird * Lt;
             Q[qi] = out[v];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -164,7 +167,7 @@ __device__ __forceinline__ void update_cell(const GridDesc &g, const PhysParams 
                 const double qlt = F[(long long)(15 + v) * n + hi[d]];
                 const double qrt = F[(long long)(25 + v) * n + c];
                 const long long gi = ((long long)v * 3 + d) * n + c;
-                G[gi] = S1[gi] + dt * (qlt - qrt) / g.h[d];
+                G[gi] = S1[gi] + dt * (qlt - qrt) * ih[d];
             }
         }
     }

@@ -315,13 +315,16 @@ def riemann_quadrants(nx=64, ny=64, *, states, amp=0.01, seed=0, gamma=1.4):
     return Q, G, grid
 
 
-def ensemble_instances(count=64, seed0=2000, sizes=(64, 128, 256, 512)):
+def ensemble_instances(count=64, seed0=2000, sizes=(64, 128, 256, 512), max_rho_ratio=5.0):
     """Seeded ensemble of 2D instances: the first half periodic double shear
     layers (Ma 0.3, Re 1e4), the second half four-quadrant Riemann problems
     (inviscid collision time) with quadrant states drawn per seed
-    (rho in [0.1, 1.5], p in [0.05, 1.5], u, v in [-1, 1]); nx, ny drawn from
-    ``sizes``, perturbation amplitude log-uniform in [1e-3, 1e-1].
-    Returns a list of (Q, G, grid, physics dict)."""
+    (rho in [0.1, 1.5], p in [0.05, 1.5], u, v in [-1, 1]), drawn again from
+    the same generator until the density ratio between the quadrants is at
+    most ``max_rho_ratio`` (the scheme has no positivity limiter: unconstrained
+    draws with ratios of 5.7 to 11 became non-physical within 20 steps); nx,
+    ny drawn from ``sizes``, perturbation amplitude log-uniform in
+    [1e-3, 1e-1]. Returns a list of (Q, G, grid, physics dict)."""
     out = []
     for i in range(count):
         rng = np.random.default_rng(seed0 + i)
@@ -331,8 +334,11 @@ def ensemble_instances(count=64, seed0=2000, sizes=(64, 128, 256, 512)):
             Q, G, grid = double_shear_layer(nx, ny, amp=amp)
             phys = dict(mu=1.0 / 1e4, inviscid=False)
         else:
-            st = np.stack([rng.uniform(0.1, 1.5, 4), rng.uniform(-1, 1, 4),
-                           rng.uniform(-1, 1, 4), rng.uniform(0.05, 1.5, 4)], axis=1)
+            while True:
+                st = np.stack([rng.uniform(0.1, 1.5, 4), rng.uniform(-1, 1, 4),
+                               rng.uniform(-1, 1, 4), rng.uniform(0.05, 1.5, 4)], axis=1)
+                if st[:, 0].max() <= max_rho_ratio * st[:, 0].min():
+                    break
             Q, G, grid = riemann_quadrants(nx, ny, states=st, amp=amp, seed=seed0 + i)
             phys = dict(mu=0.0, inviscid=True)
         out.append((Q, G, grid, phys))

@@ -147,3 +147,57 @@ def test_mixed_uniform_flow_and_conservation(torch_dev):
         s.step(Qd, Gd if scheme == "cgks5" else None, nsteps=3)
         assert np.array_equal(Qd.cpu().numpy(), Qu)
         assert np.array_equal(Gd.cpu().numpy(), Gu)
+
+
+def restore_offsets(torch, fs_mixed, Qd):
+    """W = Q0 + FP32 offset for the value entries of mixed face states."""
+    out = fs_mixed.double().clone()
+    n = Qd[0].numel()
+    Qf = Qd.reshape(5, n)
+    for f in range(6):
+        d = f // 2
+        for c in range(5):
+            v = c if c in (0, 4) else 1 + (d + c - 1) % 3
+            out[f, :, c, :] += Qf[v][None, :]
+    return out
+
+
+@pytest.mark.parametrize("case", ["tgv48", "hit64", "tgv_ma2_32", "sod256"])
+def test_mixed_flux_shell_accuracy(torch_dev, case):
+    """The mixed flux (float-float W0, X1, D = X1 - X4; FP32 core) against
+    the FP64 flux kernel on identical face states, per record block and
+    group (density, momentum, energy), relative to the FP64 group scale:
+    F^n (float-float parts) within 1e-7; F_t and dQ/dt (FP32 core, tau-sized
+    coefficients) within 2e-5; the interface values Q = W0 + e (W - W0)
+    within 1e-7 (W0 float-float; the blend weight e and the difference are
+    FP32, so where the jump W - W0 is large the error is FP32-level: 1.5e-8
+    on the double Sod, 1e-14 on smooth flow)."""
+    import math
+    torch, dev = torch_dev
+    if case == "tgv48":
+        Q, G, grid = wl.taylor_green(48)
+        kw = dict(mu=1.0 / 1600)
+    elif case == "hit64":
+        Q, G, grid, _ = wl.isotropic_turbulence(64, Mt=0.5, k0=2.0, seed=303)
+        kw = dict(mu=1e-3)
+    elif case == "tgv_ma2_32":
+        Q, G, grid = wl.taylor_green_supersonic(32)
+        kw = dict(mu=math.sqrt(1.4) * 2 / 1600, mu_law=1, Pr=0.7)
+    else:
+        Q, G, grid = wl.double_sod(256)
+        kw = dict(inviscid=True, Pr=1.0)
+    mix = make(torch_dev, grid, scheme="cgks5", precision="mixed", **kw)
+    f64 = make(torch_dev, grid, scheme="cgks5", precision="fp64", **kw)
+    Qd, Gd = torch.tensor(Q, device=dev), torch.tensor(G, device=dev)
+    f64.step(Qd, Gd, nsteps=3)
+    fsm = mix.reconstruct(Qd, Gd)
+    dtd = f64.compute_dt(Qd)
+    got = mix.flux(fsm, dtd, Q=Qd).cpu().numpy().reshape(3, 6, 5, -1)
+    want = f64.flux(restore_offsets(torch, fsm, Qd).contiguous(), dtd).cpu().numpy()
+    want = want.reshape(3, 6, 5, -1)
+    bounds = {0: 1e-7, 1: 2e-5, 2: 1e-7, 3: 2e-5, 4: 1e-7, 5: 2e-5}
+    for blk, bound in bounds.items():
+        for gi in ([0], [1, 2, 3], [4]):
+            scale = np.abs(want[:, blk, gi]).max()
+            err = np.abs(got[:, blk, gi] - want[:, blk, gi]).max() / max(scale, 1e-300)
+            assert err < bound, (case, blk, gi, err)

@@ -23,3 +23,17 @@ def test_advection_exact_solution_is_a_translation():
     Q0, _, grid = wl.advection(12, dims=2)
     Q1, _, _ = wl.advection(12, dims=2, t=2 * np.pi / 2.0)  # (U + V) t = 2 pi: one period
     np.testing.assert_allclose(Q1, Q0, atol=1e-13)
+
+
+def test_ensemble_instances_are_seeded_and_bounded():
+    a = wl.ensemble_instances(6, seed0=2000, sizes=(8, 16))
+    b = wl.ensemble_instances(6, seed0=2000, sizes=(8, 16))
+    for (Qa, Ga, ga, pa), (Qb, Gb, gb, pb) in zip(a, b):
+        assert ga.n == gb.n and pa == pb
+        assert np.array_equal(Qa, Qb) and np.array_equal(Ga, Gb)
+        assert ga.n[2] == 1 and ga.n[0] in (8, 16) and ga.n[1] in (8, 16)
+        assert np.all(Qa[0] > 0)
+    # Riemann half: quadrant density ratio within the bound (noise aside)
+    for Q, G, g, ph in a[3:]:
+        assert ph["inviscid"]
+        assert Q[0].max() <= 5.0 * Q[0].min() * 1.25
