@@ -26,6 +26,7 @@ struct gks_ctx {
     double *frec;          // face records [3][30][n]
     double *Qs, *Gs, *Acc, *S1;  // CGKS-5th stage buffers
     float *Gf;             // mixed CGKS-5th: FP32 copy of the gradients [15][n]
+    float *Qv;             // mixed: float-float split of the averages [10][n]
     int slab_planes;       // 0: fs holds the whole grid; > 0: z-slabs of this many planes
     double *scal;          // [0] dt, [1..2] dt reduction words, [3] diagnostics out (12)
     int *status;
@@ -104,6 +105,7 @@ void gks_destroy(gks_ctx *c) {
     cudaFree(c->Acc);
     cudaFree(c->S1);
     cudaFree(c->Gf);
+    cudaFree(c->Qv);
     cudaFree(c->scal);
     cudaFree(c->status);
     cudaFree(c->partials);
@@ -174,7 +176,8 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
         (rc = dalloc(&c->scal, (size_t)3 + 12)) ||
         (rc = dalloc(&c->status, 1)) ||
         (rc = dalloc(&c->skips, 1)) ||
-        (rc = dalloc(&c->partials, (size_t)12 * c->diag_blocks))) {
+        (rc = dalloc(&c->partials, (size_t)12 * c->diag_blocks)) ||
+        (c->mixed && (rc = dalloc(&c->Qv, (size_t)10 * n)))) {
         gks_destroy(c);
         return rc;
     }
@@ -224,11 +227,13 @@ int recon_any(gks_ctx *c, const Slab &S, const double *Q, const double *G, void 
     return cg ? launch_recon5(c->g, S, c->P, Q, G, (double *)fs, c->stream)
               : launch_recon2(c->g, S, c->P, Q, (double *)fs, c->stream);
 }
+// mixed: c->Qv must hold the split of the averages the face states came from
 int flux_any(gks_ctx *c, const Slab &S, const double *Q, const void *fs, const double *dt,
              double *fr) {
+    (void)Q;
     if (c->mixed)
-        return launch_flux_faces_mixed(c->g, S, c->P, (const float *)fs, Q, dt, fr, c->status,
-                                       c->stream);
+        return launch_flux_faces_mixed(c->g, S, c->P, (const float *)fs, c->Qv, dt, fr,
+                                       c->status, c->stream);
     return launch_flux_faces(c->g, S, c->P, (const double *)fs, dt, fr, c->status, c->stream);
 }
 // one stage's face records: reconstruction + flux over the whole grid or
@@ -237,6 +242,7 @@ int stage_faces(gks_ctx *c, const double *Q, const double *G, const double *dt) 
     int rc;
     if (c->mixed && c->P.scheme == GKS_SCHEME_CGKS5 && (rc = launch_g_to_f32(c->g, G, c->Gf, c->stream)))
         return rc;
+    if (c->mixed && (rc = launch_q_to_ff(c->g, Q, c->Qv, c->stream))) return rc;
     if (!c->slab_planes) {
         const Slab S = whole_grid(c->g);
         if ((rc = recon_any(c, S, Q, G, c->fs)) || (rc = flux_any(c, S, Q, c->fs, dt, c->frec)))
@@ -276,6 +282,7 @@ int gks_flux(gks_ctx *c, const double *Q, const void *face_states, const double 
     if (!face_states && c->slab_planes) return GKS_ERR_STATE;
     const void *fs = face_states ? face_states : c->fs;
     double *fr = face_flux ? face_flux : c->frec;
+    if (c->mixed && launch_q_to_ff(c->g, Q, c->Qv, c->stream)) return GKS_ERR_CUDA;
     return launch_ok(flux_any(c, whole_grid(c->g), Q, fs, dt_dev, fr));
 }
 

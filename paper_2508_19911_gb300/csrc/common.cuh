@@ -98,8 +98,11 @@ int launch_recon2(const GridDesc &g, const Slab &S, const PhysParams &P, const d
 int upload_recon_tables(void);
 int launch_flux_faces(const GridDesc &g, const Slab &S, const PhysParams &P, const double *fs,
                       const double *dt_dev, double *frec, int *status, cudaStream_t s);
+// float-float split of the averages for the mixed flux (once per stage):
+// Qv hi [5][n] then lo [5][n]
+int launch_q_to_ff(const GridDesc &g, const double *Q, float *Qv, cudaStream_t s);
 int launch_flux_faces_mixed(const GridDesc &g, const Slab &S, const PhysParams &P,
-                            const float *fs, const double *Q, const double *dt_dev, double *frec,
+                            const float *fs, const float *Qv, const double *dt_dev, double *frec,
                             int *status, cudaStream_t s);
 // FP32 copy of the cell gradients for the mixed reconstruction (once per stage)
 int launch_g_to_f32(const GridDesc &g, const double *G, float *Gf, cudaStream_t s);

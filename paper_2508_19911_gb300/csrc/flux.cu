@@ -230,6 +230,28 @@ __device__ __forceinline__ void time_coefficients(double dt, double tau, double 
     }
 }
 
+// The closed forms above in FP32 (for the mixed flux, whose coefficients
+// meet FP32 moments): for x = dt/tau >= 4 their relative error is below
+// 1e-6 (1e-7 for x >= 30), checked against a 50-digit reference; it grows
+// to 1e-5 at x = 1/2 through the cancellation in al_1, al_2.
+__device__ __forceinline__ void time_coefficients_f(float dt, float tau, float al[6], float be[6]) {
+    const float a = -expm1f(-0.5f * dt / tau), b = 1.0f - a;
+    const float idt = 1.0f / dt;
+    const float t2 = tau * tau;
+    const float g = a * (3.0f - b) * idt;
+    const float h = 4.0f * a * a * idt * idt;
+    al[1] = 2.0f * t2 * g - tau * (1.0f + 2.0f * b - b * b);
+    be[1] = 4.0f * tau * a * (b * dt - 2.0f * tau * a) * idt * idt;
+    al[2] = t2 * g - tau;
+    be[2] = 1.0f - t2 * h;
+    al[3] = tau * g;
+    be[3] = -tau * h;
+    al[4] = tau * b * (2.0f - b) - 2.0f * t2 * g;
+    be[4] = -be[1];
+    al[5] = -t2 * g;
+    be[5] = t2 * h;
+}
+
 template <typename T>
 struct PrimT {
     T rho, U, V, W, p, lam;
@@ -608,17 +630,18 @@ __device__ __forceinline__ PrimT<float> prim_f(const PrimFF &P) {
 // One Gauss point's record in float-float: F^n, F_t^n and, with
 // kInterface, Q^l, dQ^l/dt, Q^r, dQ^r/dt (out[0..29], face frame); the
 // FP32 entries have lo = 0.
+// Ql, Qr: the two cells' FP64 averages as float-float pairs (exact splits)
 template <bool kInterface>
-__device__ void flux_point_mixed(const PhysParams &P, const double Ql[5], const float ol[5],
-                                 const float dl[15], const double Qr[5], const float orr[5],
+__device__ void flux_point_mixed(const PhysParams &P, const ff Ql[5], const float ol[5],
+                                 const float dl[15], const ff Qr[5], const float orr[5],
                                  const float dr[15], double dt, ff out[30], int *status) {
     const ff gm1 = ff_from_double(P.gamma - 1.0);
     const ff N = ff_from_double(P.Nint);
     ff Wl[5], Wr[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        Wl[i] = ff_add_f(ff_from_double(Ql[i]), ol[i]);
-        Wr[i] = ff_add_f(ff_from_double(Qr[i]), orr[i]);
+        Wl[i] = ff_add_f(Ql[i], ol[i]);
+        Wr[i] = ff_add_f(Qr[i], orr[i]);
     }
     const PrimFF L = to_prim_ff(Wl, gm1), R = to_prim_ff(Wr, gm1);
     if (!(L.rho.hi > 0.0f && L.p.hi > 0.0f && R.rho.hi > 0.0f && R.p.hi > 0.0f)) {
@@ -668,19 +691,32 @@ __device__ void flux_point_mixed(const PhysParams &P, const double Ql[5], const 
     side_terms<-1>(dr, Rf, Nf, ur0, ur1, Zf.U, Zf.V, Zf.W, dW0, X[3], X[4], X[5], q + 3, dtWr);
     equilibrium_terms<false>(Zf, Nf, dW0, X, q, dtW0);  // a Maxwellian carries no heat flux: q1 = 0
 
-    // collision time (Sec. 4) and time coefficients, FP64; then FP32
+    // collision time (Sec. 4) in FP32; time coefficients in FP32 for
+    // dt >= 4 tau, else from the FP64 closed forms (dt >= tau/100) or series
     const float dpr = fabsf(ff_sub(L.p, R.p).hi / ff_add(L.p, R.p).hi);
-    const double zp = ff_to_double(Z.p);
-    const double tau = P.inviscid
-                           ? (P.eps_tau * dt + P.C_tau * (double)dpr * dt)
-                           : (viscosity(P, ff_to_double(Z.rho), zp) / zp + P.C_tau * (double)dpr * dt);
-    double ald[6], bed[6];
-    time_coefficients(dt, tau, ald, bed, 0.01);
+    const float dtf = (float)dt;
+    float tau;
+    if (P.inviscid) {
+        tau = ((float)P.eps_tau + (float)P.C_tau * dpr) * dtf;
+    } else {
+        float mu = (float)P.mu0;
+        if (P.mu_law) {
+            const float th = (Zf.p / Zf.rho) / (float)P.T_ref;
+            mu *= 1.4042f * th * sqrtf(th) / (th + 0.4042f);
+        }
+        tau = mu / Zf.p + (float)P.C_tau * dpr * dtf;
+    }
     float al[6], be[6];
+    if (tau > 0.0f && dtf >= 4.0f * tau) {
+        time_coefficients_f(dtf, tau, al, be);
+    } else {
+        double ald[6], bed[6];
+        time_coefficients(dt, (double)tau, ald, bed, 0.01);
 #pragma unroll
-    for (int k = 1; k < 6; ++k) {
-        al[k] = (float)ald[k];
-        be[k] = (float)bed[k];
+        for (int k = 1; k < 6; ++k) {
+            al[k] = (float)ald[k];
+            be[k] = (float)bed[k];
+        }
     }
     const float prfix = (float)(1.0 / P.Pr - 1.0);
     float qn = 0.0f, qt = 0.0f;
@@ -730,11 +766,14 @@ __device__ __forceinline__ int global_var(int c, int d) {
 // l: the right cell's position in the face-state buffer S (the face is its
 // low face along d); face states are read at buffer positions (stride
 // S.nb), the averages Q and the records at global cells (stride g.n).
-template <bool kCGKS, bool MIXED>
+// mixed: the averages from Qv (VIEWQ: float-float pairs hi [5][n], lo
+// [5][n], written once per stage) or split here from the FP64 Q
+template <bool kCGKS, bool MIXED, bool VIEWQ = false>
 __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S,
                                                 const PhysParams &P,
                                                 const void *__restrict__ fsv,
-                                                const double *__restrict__ Q, double dt,
+                                                const double *__restrict__ Q,
+                                                const float *__restrict__ Qv, double dt,
                                                 double *__restrict__ frec, int *status, int d,
                                                 long long l, int k, bool valid) {
     constexpr int K = kCGKS ? 4 : 1;
@@ -791,15 +830,20 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S
     } else {
         ff out[30];
         const float *fs = (const float *)fsv;
-        double Ql[5], Qr[5];
+        ff Ql[5], Qr[5];
         float ol[5], orr[5], dl[15], dr[15];
         const float *pl = fs + ((long long)((2 * d + 1) * K + k) * 20) * nb + ll;
         const float *pr = fs + ((long long)((2 * d) * K + k) * 20) * nb + l;
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             const int v = global_var(q, d);
-            Ql[q] = __ldg(Q + (long long)v * n + left);
-            Qr[q] = __ldg(Q + (long long)v * n + c);
+            if constexpr (VIEWQ) {
+                Ql[q] = ff_make(__ldg(Qv + (long long)v * n + left), __ldg(Qv + (long long)(5 + v) * n + left));
+                Qr[q] = ff_make(__ldg(Qv + (long long)v * n + c), __ldg(Qv + (long long)(5 + v) * n + c));
+            } else {
+                Ql[q] = ff_from_double(__ldg(Q + (long long)v * n + left));
+                Qr[q] = ff_from_double(__ldg(Q + (long long)v * n + c));
+            }
             ol[q] = __ldg(pl + (long long)q * nb);
             orr[q] = __ldg(pr + (long long)q * nb);
         }
@@ -847,7 +891,7 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S
 template <bool kCGKS, bool MIXED>
 __global__ void __launch_bounds__(128, MIXED ? 3 : 1) flux_faces_kernel(GridDesc g, Slab S, PhysParams P,
                                                          const void *__restrict__ fs,
-                                                         const double *__restrict__ Q,
+                                                         const float *__restrict__ Qv,
                                                          const double *__restrict__ dt_dev,
                                                          double *__restrict__ frec, int *status) {
     const double dt = *dt_dev;
@@ -863,7 +907,8 @@ __global__ void __launch_bounds__(128, MIXED ? 3 : 1) flux_faces_kernel(GridDesc
     const long long fc = gid / K;
     const int d = (int)(fc / cnt);
     const long long t = fc - (long long)d * cnt;
-    flux_face_point<kCGKS, MIXED>(g, S, P, fs, Q, dt, frec, status, d, S.p0 * nxy + t, k, valid);
+    flux_face_point<kCGKS, MIXED, MIXED>(g, S, P, fs, nullptr, Qv, dt, frec, status, d,
+                                         S.p0 * nxy + t, k, valid);
 }
 
 // Persistent ensemble flux (CGKS-5th): blocks stride over the work items
@@ -892,8 +937,9 @@ __global__ void __launch_bounds__(128) flux_ens_kernel(const EnsInst *__restrict
             const long long rem = gid >> 2;
             const int d = (int)(rem / T);
             const long long c = it.c0 + rem % T;
-            flux_face_point<true, MIXED>(I.g, whole_grid(I.g), I.P, fs, Qa + 5 * I.off, dt,
-                                         fra + 90 * I.off, status, d, c, k, valid);
+            flux_face_point<true, MIXED, false>(I.g, whole_grid(I.g), I.P, fs, Qa + 5 * I.off,
+                                                nullptr, dt, fra + 90 * I.off, status, d, c, k,
+                                                valid);
         }
     }
 }
@@ -918,18 +964,36 @@ __global__ void __launch_bounds__(128) flux_points_kernel(PhysParams P, const do
 
 }  // namespace
 
+// float-float split of the averages: Qv hi [5][n] then lo [5][n]
+__global__ void q_to_ff_kernel(const double *__restrict__ Q, float *__restrict__ Qv, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 5 * n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const ff x = ff_from_double(Q[i]);
+        const long long v = i / n, c = i - v * n;
+        Qv[v * n + c] = x.hi;
+        Qv[(5 + v) * n + c] = x.lo;
+    }
+}
+
+int launch_q_to_ff(const GridDesc &g, const double *Q, float *Qv, cudaStream_t s) {
+    const long long m = 5 * g.n;
+    const long long blocks = (m + 255) / 256;
+    q_to_ff_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(Q, Qv, g.n);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
 int launch_flux_faces_mixed(const GridDesc &g, const Slab &S, const PhysParams &P,
-                            const float *fs, const double *Q, const double *dt_dev, double *frec,
+                            const float *fs, const float *Qv, const double *dt_dev, double *frec,
                             int *status, cudaStream_t s) {
     const int K = P.scheme ? 4 : 1;
     const long long total = 3 * (long long)(S.nzb - S.p0) * g.nx * g.ny * K;
     const int block = 128;
     const long long grid = (total + block - 1) / block;
     if (P.scheme)
-        flux_faces_kernel<true, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Q, dt_dev, frec,
-                                                                        status);
+        flux_faces_kernel<true, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Qv, dt_dev,
+                                                                        frec, status);
     else
-        flux_faces_kernel<false, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Q, dt_dev,
+        flux_faces_kernel<false, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Qv, dt_dev,
                                                                          frec, status);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
