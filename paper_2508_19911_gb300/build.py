@@ -19,13 +19,14 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["flux.cu", "recon.cu", "update.cu", "capi.cu", "noalloc.cu", "mlp.cu", "ensemble.cu"]
+CU_SOURCES = ["flux.cu", "recon.cu", "recon_fp64.cu", "update.cu", "capi.cu", "noalloc.cu", "mlp.cu", "ensemble.cu"]
 CPP_SOURCES = ["tables.cpp"]
-HEADERS = ["basis.h", "common.cuh", "ff.cuh"]
-# recon.cu: no implicit multiply-add contraction (only explicit fma), so
-# that every kernel inlining the same reconstruction rounds identically
-# (the learned indicator's never-skip limit equals the plain kernel bit for
-# bit; ptxas would otherwise fuse differently in each kernel's context)
+HEADERS = ["basis.h", "common.cuh", "ff.cuh", "recon_common.cuh"]
+# recon.cu (the mixed-precision reconstruction): no implicit multiply-add
+# contraction (only explicit fmaf), so that every kernel inlining the same
+# reconstruction rounds identically (the learned indicator's never-skip
+# limit equals the plain kernel bit for bit; ptxas would otherwise fuse
+# differently in each kernel's context). recon_fp64.cu keeps contraction.
 EXTRA_FLAGS = {"recon.cu": ["-fmad=false"]}
 COMPILE_TIMEOUT = 900
 

@@ -26,7 +26,7 @@ struct gks_ctx {
     double *frec;          // face records [3][30][n]
     double *Qs, *Gs, *Acc, *S1;  // CGKS-5th stage buffers
     float *Gf;             // mixed CGKS-5th: FP32 copy of the gradients [15][n]
-    float *Qv;             // mixed: float-float split of the averages [10][n]
+    float *Qv;             // mixed: float-float split of the averages, hi [5][n] then lo [5][n]
     int slab_planes;       // 0: fs holds the whole grid; > 0: z-slabs of this many planes
     double *scal;          // [0] dt, [1..2] dt reduction words, [3] diagnostics out (12)
     int *status;
@@ -218,11 +218,21 @@ int gks_compute_dt(gks_ctx *c, const double *Q, double *dt_dev) {
 namespace {
 // reconstruction and flux of one face-state buffer S (the FP32 gradient
 // copy of the mixed CGKS-5th reconstruction is made by the caller)
+// mixed: the views of Q, G (make_views) must be current
+int make_views(gks_ctx *c, const double *Q, const double *G) {
+    int rc;
+    if (c->mixed && c->P.scheme == GKS_SCHEME_CGKS5 && G &&
+        (rc = launch_g_to_f32(15 * c->g.n, G, c->Gf, c->stream)))
+        return rc;
+    if (c->mixed && (rc = launch_q_to_ff(5 * c->g.n, Q, c->Qv, c->Qv + 5 * c->g.n, c->stream)))
+        return rc;
+    return 0;
+}
 int recon_any(gks_ctx *c, const Slab &S, const double *Q, const double *G, void *fs) {
     const bool cg = c->P.scheme == GKS_SCHEME_CGKS5;
     if (c->mixed)
-        return cg ? launch_recon5_mixed(c->g, S, c->P, Q, c->Gf, (float *)fs, c->stream,
-                                        c->indicator_on, c->skips)
+        return cg ? launch_recon5_mixed(c->g, S, c->P, c->Gf, c->Qv, c->Qv + 5 * c->g.n,
+                                        (float *)fs, c->stream, c->indicator_on, c->skips)
                   : launch_recon2_mixed(c->g, S, c->P, Q, (float *)fs, c->stream);
     return cg ? launch_recon5(c->g, S, c->P, Q, G, (double *)fs, c->stream)
               : launch_recon2(c->g, S, c->P, Q, (double *)fs, c->stream);
@@ -232,17 +242,15 @@ int flux_any(gks_ctx *c, const Slab &S, const double *Q, const void *fs, const d
              double *fr) {
     (void)Q;
     if (c->mixed)
-        return launch_flux_faces_mixed(c->g, S, c->P, (const float *)fs, c->Qv, dt, fr,
-                                       c->status, c->stream);
+        return launch_flux_faces_mixed(c->g, S, c->P, (const float *)fs, c->Qv,
+                                       c->Qv + 5 * c->g.n, dt, fr, c->status, c->stream);
     return launch_flux_faces(c->g, S, c->P, (const double *)fs, dt, fr, c->status, c->stream);
 }
 // one stage's face records: reconstruction + flux over the whole grid or
 // slab by slab into the context's buffer
 int stage_faces(gks_ctx *c, const double *Q, const double *G, const double *dt) {
     int rc;
-    if (c->mixed && c->P.scheme == GKS_SCHEME_CGKS5 && (rc = launch_g_to_f32(c->g, G, c->Gf, c->stream)))
-        return rc;
-    if (c->mixed && (rc = launch_q_to_ff(c->g, Q, c->Qv, c->stream))) return rc;
+    if ((rc = make_views(c, Q, G))) return rc;
     if (!c->slab_planes) {
         const Slab S = whole_grid(c->g);
         if ((rc = recon_any(c, S, Q, G, c->fs)) || (rc = flux_any(c, S, Q, c->fs, dt, c->frec)))
@@ -270,8 +278,7 @@ int gks_reconstruct(gks_ctx *c, const double *Q, const double *G, void *face_sta
     if (!c || !Q) return GKS_ERR_ARG;
     if (c->P.scheme == GKS_SCHEME_CGKS5 && !G) return GKS_ERR_ARG;
     if (!face_states && c->slab_planes) return GKS_ERR_STATE;  // own buffer holds a slab only
-    if (c->mixed && c->P.scheme == GKS_SCHEME_CGKS5 && launch_g_to_f32(c->g, G, c->Gf, c->stream))
-        return GKS_ERR_CUDA;
+    if (make_views(c, Q, G)) return GKS_ERR_CUDA;
     return launch_ok(recon_any(c, whole_grid(c->g), Q, G, face_states ? face_states : c->fs));
 }
 
@@ -282,7 +289,8 @@ int gks_flux(gks_ctx *c, const double *Q, const void *face_states, const double 
     if (!face_states && c->slab_planes) return GKS_ERR_STATE;
     const void *fs = face_states ? face_states : c->fs;
     double *fr = face_flux ? face_flux : c->frec;
-    if (c->mixed && launch_q_to_ff(c->g, Q, c->Qv, c->stream)) return GKS_ERR_CUDA;
+    if (c->mixed && launch_q_to_ff(5 * c->g.n, Q, c->Qv, c->Qv + 5 * c->g.n, c->stream))
+        return GKS_ERR_CUDA;
     return launch_ok(flux_any(c, whole_grid(c->g), Q, fs, dt_dev, fr));
 }
 
@@ -367,7 +375,13 @@ int gks_indicator_dump(gks_ctx *c, const double *Q, const double *G, float label
                        float *chi, float *y) {
     if (!c || !Q || !G || !x || !chi || !y || !(label_eps >= 0.0f)) return GKS_ERR_ARG;
     if (c->P.scheme != GKS_SCHEME_CGKS5) return GKS_ERR_STATE;
-    if (launch_indicator_dump(c->g, Q, G, c->Gf, x, chi, c->stream)) return GKS_ERR_CUDA;
+    if (c->mixed) {
+        if (make_views(c, Q, G) ||
+            launch_indicator_dump(c->g, Q, G, c->Gf, c->Qv, c->Qv + 5 * c->g.n, x, chi, c->stream))
+            return GKS_ERR_CUDA;
+    } else if (launch_indicator_dump(c->g, Q, G, nullptr, nullptr, nullptr, x, chi, c->stream)) {
+        return GKS_ERR_CUDA;
+    }
     if (launch_labels(chi, y, 5 * c->g.n, label_eps, c->stream)) return GKS_ERR_CUDA;
     return GKS_OK;
 }

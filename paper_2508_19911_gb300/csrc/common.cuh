@@ -96,21 +96,31 @@ int launch_recon5(const GridDesc &g, const Slab &S, const PhysParams &P, const d
 int launch_recon2(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
                   double *fs, cudaStream_t s);
 int upload_recon_tables(void);
+// the FP64 tables (recon_fp64.cu), called by upload_recon_tables
+struct ReconTables;
+int upload_recon_tables_fp64(const ReconTables &t);
+int launch_recon5_ens_fp64(const EnsInst *inst, const EnsItem *items, int nitems, int blocks,
+                           const double *Qa, const double *Ga, double *fsa, cudaStream_t s);
 int launch_flux_faces(const GridDesc &g, const Slab &S, const PhysParams &P, const double *fs,
                       const double *dt_dev, double *frec, int *status, cudaStream_t s);
-// float-float split of the averages for the mixed flux (once per stage):
-// Qv hi [5][n] then lo [5][n]
-int launch_q_to_ff(const GridDesc &g, const double *Q, float *Qv, cudaStream_t s);
+// float-float split of m FP64 values (the averages, once per stage, for
+// the mixed reconstruction and flux): hi[i] + lo[i] = x[i]
+int launch_q_to_ff(long long m, const double *x, float *hi, float *lo, cudaStream_t s);
 int launch_flux_faces_mixed(const GridDesc &g, const Slab &S, const PhysParams &P,
-                            const float *fs, const float *Qv, const double *dt_dev, double *frec,
-                            int *status, cudaStream_t s);
-// FP32 copy of the cell gradients for the mixed reconstruction (once per stage)
-int launch_g_to_f32(const GridDesc &g, const double *G, float *Gf, cudaStream_t s);
-int launch_recon5_mixed(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
-                        const float *Gf, float *fs, cudaStream_t s, int indicator,
-                        unsigned long long *skips);
-int launch_indicator_dump(const GridDesc &g, const double *Q, const double *G, float *Gf, float *x,
-                          float *chi, cudaStream_t s);
+                            const float *fs, const float *Qhi, const float *Qlo,
+                            const double *dt_dev, double *frec, int *status, cudaStream_t s);
+// FP32 copy of m FP64 values (the cell gradients, once per stage, for the
+// mixed reconstruction)
+int launch_g_to_f32(long long m, const double *G, float *Gf, cudaStream_t s);
+// views of one stage: Gf = FP32 gradients, Qhi/Qlo = float-float averages
+int launch_recon5_mixed(const GridDesc &g, const Slab &S, const PhysParams &P, const float *Gf,
+                        const float *Qhi, const float *Qlo, float *fs, cudaStream_t s,
+                        int indicator, unsigned long long *skips);
+// Gf/Qhi/Qlo: the views (mixed context, the caller converts first) or
+// nullptr (FP64 context: the FP64 Q, G directly)
+int launch_indicator_dump(const GridDesc &g, const double *Q, const double *G, const float *Gf,
+                          const float *Qhi, const float *Qlo, float *x, float *chi,
+                          cudaStream_t s);
 int upload_indicator(const float *params, float theta);
 int launch_labels(const float *chi, float *y, long long m, float eps, cudaStream_t s);
 int launch_recon2_mixed(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
@@ -129,15 +139,17 @@ int launch_diagnostics(const GridDesc &g, const PhysParams &P, const double *Q,
 int diagnostics_blocks(const GridDesc &g);
 
 // persistent ensemble kernels (see ensemble.cu)
+// mixed ensemble kernels read the arenas' views (Gfa, Qhia, Qloa)
 int launch_recon5_ens(const EnsInst *inst, const EnsItem *items, int nitems, int blocks,
-                      int mixed, int indicator, const double *Qa, const double *Ga, void *fsa,
+                      int mixed, int indicator, const double *Qa, const double *Ga,
+                      const float *Gfa, const float *Qhia, const float *Qloa, void *fsa,
                       unsigned long long *skips, cudaStream_t s);
 int launch_indicator_dump_ens(const EnsInst *inst, const EnsItem *items, int nitems, int blocks,
-                              const double *Qa, const double *Ga, float *x, float *chi,
-                              long long total_cells, cudaStream_t s);
+                              const float *Gfa, const float *Qhia, const float *Qloa, float *x,
+                              float *chi, long long total_cells, cudaStream_t s);
 int launch_flux_ens(const EnsInst *inst, const EnsItem *items, int nitems, int blocks, int mixed,
-                    const void *fsa, const double *Qa, const double *dt_arr, double *fra,
-                    int *status, cudaStream_t s);
+                    const void *fsa, const float *Qhia, const float *Qloa, const double *dt_arr,
+                    double *fra, int *status, cudaStream_t s);
 int launch_dt_ens(const EnsInst *inst, int ninst, const EnsItem *items, int nitems, int blocks,
                   const double *Qa, double *red, double *dt_arr, double *t_arr, double t_stop,
                   cudaStream_t s);

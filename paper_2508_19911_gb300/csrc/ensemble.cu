@@ -38,6 +38,9 @@ struct gks_ensemble {
     int nitems = 0, items_cap = 0;
     int sms = 152;
     void *fs = nullptr;
+    // FP32 gradients [15 total] and float-float averages (hi, lo: [5 total]
+    // each) for the mixed kernels and the indicator dump
+    float *Gf = nullptr, *Qv = nullptr;
     double *frec = nullptr, *Qs = nullptr, *Gs = nullptr, *Acc = nullptr, *S1 = nullptr;
     double *dt = nullptr, *t = nullptr, *red = nullptr;
     int *status = nullptr;
@@ -102,13 +105,17 @@ int enqueue_step(gks_ensemble *e, double *Q, double *G, double t_stop) {
     if (launch_dt_ens(e->dinst, e->ninst, e->ditems, e->nitems, light, Q, e->red, e->dt, e->t,
                       t_stop, e->s))
         return GKS_ERR_CUDA;
+    const long long N = e->total;
     for (int stage = 1; stage <= 2; ++stage) {
         const double *Qi = stage == 1 ? Q : e->Qs;
         const double *Gi = stage == 1 ? G : e->Gs;
+        if (e->mixed && (launch_g_to_f32(15 * N, Gi, e->Gf, e->s) ||
+                         launch_q_to_ff(5 * N, Qi, e->Qv, e->Qv + 5 * N, e->s)))
+            return GKS_ERR_CUDA;
         if (launch_recon5_ens(e->dinst, e->ditems, e->nitems, heavy, e->mixed, e->indicator_on, Qi,
-                              Gi, e->fs, e->skips, e->s) ||
-            launch_flux_ens(e->dinst, e->ditems, e->nitems, heavy, e->mixed, e->fs, Qi, e->dt,
-                            e->frec, e->status, e->s) ||
+                              Gi, e->Gf, e->Qv, e->Qv + 5 * N, e->fs, e->skips, e->s) ||
+            launch_flux_ens(e->dinst, e->ditems, e->nitems, heavy, e->mixed, e->fs, e->Qv,
+                            e->Qv + 5 * N, e->dt, e->frec, e->status, e->s) ||
             launch_update_ens(e->dinst, e->ditems, e->nitems, light, stage, e->frec, e->dt, Q, G,
                               e->Qs, e->Gs, e->Acc, e->S1, e->status, e->s))
             return GKS_ERR_CUDA;
@@ -165,6 +172,8 @@ void gks_ensemble_destroy(gks_ensemble *e) {
     cudaFree(e->dinst);
     cudaFree(e->ditems);
     cudaFree(e->fs);
+    cudaFree(e->Gf);
+    cudaFree(e->Qv);
     cudaFree(e->frec);
     cudaFree(e->Qs);
     cudaFree(e->Gs);
@@ -237,6 +246,7 @@ int gks_ensemble_create(gks_ensemble **out, int n, const int *dims, const double
     const size_t N = (size_t)e->total;
     if ((rc = ealloc(&e->dinst, n)) ||
         (rc = ealloc((char **)&e->fs, 480 * N * (e->mixed ? 4 : 8))) ||
+        (rc = ealloc(&e->Gf, 15 * N)) || (rc = ealloc(&e->Qv, 10 * N)) ||
         (rc = ealloc(&e->frec, 90 * N)) || (rc = ealloc(&e->Qs, 5 * N)) ||
         (rc = ealloc(&e->Gs, 15 * N)) || (rc = ealloc(&e->Acc, 5 * N)) ||
         (rc = ealloc(&e->S1, 15 * N)) || (rc = ealloc(&e->dt, n)) || (rc = ealloc(&e->t, n)) ||
@@ -352,8 +362,11 @@ int gks_ensemble_dump(gks_ensemble *e, const double *Q, const double *G, float l
         cudaStreamWaitEvent(e->s, e->ev_in, 0) != cudaSuccess)
         return GKS_ERR_CUDA;
     const int heavy = std::min(e->nitems, 2 * e->sms);
-    if (launch_indicator_dump_ens(e->dinst, e->ditems, e->nitems, heavy, Q, G, x, chi, e->total,
-                                  e->s) ||
+    const long long N = e->total;
+    if (launch_g_to_f32(15 * N, G, e->Gf, e->s) ||
+        launch_q_to_ff(5 * N, Q, e->Qv, e->Qv + 5 * N, e->s) ||
+        launch_indicator_dump_ens(e->dinst, e->ditems, e->nitems, heavy, e->Gf, e->Qv,
+                                  e->Qv + 5 * N, x, chi, e->total, e->s) ||
         launch_labels(chi, y, 5 * e->total, label_eps, e->s))
         return GKS_ERR_CUDA;
     if (cudaEventRecord(e->ev_out, e->s) != cudaSuccess ||

@@ -537,32 +537,29 @@ __device__ __forceinline__ PrimFF to_prim_ff(const ff s[5], ff gm1) {
 // 10.7 at n = 4, costs one digit to cancellation); otherwise the FP64 erfc
 // and exp.
 constexpr int kSeriesTerms = 32;
-__device__ __forceinline__ ffc series_inv(int n) {  // 1/n, n = 1..32
-    constexpr ffc t[kSeriesTerms + 1] = {
-        ff_const(0.0), ff_const(1.0 / 1), ff_const(1.0 / 2), ff_const(1.0 / 3),
-        ff_const(1.0 / 4), ff_const(1.0 / 5), ff_const(1.0 / 6), ff_const(1.0 / 7),
-        ff_const(1.0 / 8), ff_const(1.0 / 9), ff_const(1.0 / 10), ff_const(1.0 / 11),
-        ff_const(1.0 / 12), ff_const(1.0 / 13), ff_const(1.0 / 14), ff_const(1.0 / 15),
-        ff_const(1.0 / 16), ff_const(1.0 / 17), ff_const(1.0 / 18), ff_const(1.0 / 19),
-        ff_const(1.0 / 20), ff_const(1.0 / 21), ff_const(1.0 / 22), ff_const(1.0 / 23),
-        ff_const(1.0 / 24), ff_const(1.0 / 25), ff_const(1.0 / 26), ff_const(1.0 / 27),
-        ff_const(1.0 / 28), ff_const(1.0 / 29), ff_const(1.0 / 30), ff_const(1.0 / 31),
-        ff_const(1.0 / 32)};
-    return t[n];
-}
-__device__ __forceinline__ ffc series_inv_odd(int n) {  // 1/(2n+1), n = 0..32
-    constexpr ffc t[kSeriesTerms + 1] = {
-        ff_const(1.0 / 1), ff_const(1.0 / 3), ff_const(1.0 / 5), ff_const(1.0 / 7),
-        ff_const(1.0 / 9), ff_const(1.0 / 11), ff_const(1.0 / 13), ff_const(1.0 / 15),
-        ff_const(1.0 / 17), ff_const(1.0 / 19), ff_const(1.0 / 21), ff_const(1.0 / 23),
-        ff_const(1.0 / 25), ff_const(1.0 / 27), ff_const(1.0 / 29), ff_const(1.0 / 31),
-        ff_const(1.0 / 33), ff_const(1.0 / 35), ff_const(1.0 / 37), ff_const(1.0 / 39),
-        ff_const(1.0 / 41), ff_const(1.0 / 43), ff_const(1.0 / 45), ff_const(1.0 / 47),
-        ff_const(1.0 / 49), ff_const(1.0 / 51), ff_const(1.0 / 53), ff_const(1.0 / 55),
-        ff_const(1.0 / 57), ff_const(1.0 / 59), ff_const(1.0 / 61), ff_const(1.0 / 63),
-        ff_const(1.0 / 65)};
-    return t[n];
-}
+// 1/n and 1/(2n+1), n = 0..32, as float-float constants (the series loop is
+// not unrolled: the kernel's instruction footprint, not its arithmetic,
+// stalled the mixed flux)
+__constant__ ffc cSeriesInv[kSeriesTerms + 1] = {
+    ff_const(0.0), ff_const(1.0 / 1), ff_const(1.0 / 2), ff_const(1.0 / 3),
+    ff_const(1.0 / 4), ff_const(1.0 / 5), ff_const(1.0 / 6), ff_const(1.0 / 7),
+    ff_const(1.0 / 8), ff_const(1.0 / 9), ff_const(1.0 / 10), ff_const(1.0 / 11),
+    ff_const(1.0 / 12), ff_const(1.0 / 13), ff_const(1.0 / 14), ff_const(1.0 / 15),
+    ff_const(1.0 / 16), ff_const(1.0 / 17), ff_const(1.0 / 18), ff_const(1.0 / 19),
+    ff_const(1.0 / 20), ff_const(1.0 / 21), ff_const(1.0 / 22), ff_const(1.0 / 23),
+    ff_const(1.0 / 24), ff_const(1.0 / 25), ff_const(1.0 / 26), ff_const(1.0 / 27),
+    ff_const(1.0 / 28), ff_const(1.0 / 29), ff_const(1.0 / 30), ff_const(1.0 / 31),
+    ff_const(1.0 / 32)};
+__constant__ ffc cSeriesInvOdd[kSeriesTerms + 1] = {
+    ff_const(1.0 / 1), ff_const(1.0 / 3), ff_const(1.0 / 5), ff_const(1.0 / 7),
+    ff_const(1.0 / 9), ff_const(1.0 / 11), ff_const(1.0 / 13), ff_const(1.0 / 15),
+    ff_const(1.0 / 17), ff_const(1.0 / 19), ff_const(1.0 / 21), ff_const(1.0 / 23),
+    ff_const(1.0 / 25), ff_const(1.0 / 27), ff_const(1.0 / 29), ff_const(1.0 / 31),
+    ff_const(1.0 / 33), ff_const(1.0 / 35), ff_const(1.0 / 37), ff_const(1.0 / 39),
+    ff_const(1.0 / 41), ff_const(1.0 / 43), ff_const(1.0 / 45), ff_const(1.0 / 47),
+    ff_const(1.0 / 49), ff_const(1.0 / 51), ff_const(1.0 / 53), ff_const(1.0 / 55),
+    ff_const(1.0 / 57), ff_const(1.0 / 59), ff_const(1.0 / 61), ff_const(1.0 / 63),
+    ff_const(1.0 / 65)};
 
 template <int SGN>
 __device__ __forceinline__ void half_start_ff(const PrimFF &S, ff &m0, ff &m1) {
@@ -571,11 +568,11 @@ __device__ __forceinline__ void half_start_ff(const PrimFF &S, ff &m0, ff &m1) {
     if (fabsf(y.hi) <= 2.0f) {
         const ff w = ff_neg(ff_mul(y, y));
         ff t = ff_make(1.0f, 0.0f), se = t, sf = t;
-#pragma unroll
+#pragma unroll 1
         for (int n = 1; n <= kSeriesTerms; ++n) {
-            t = ff_mul(ff_mul(t, w), ff_of(series_inv(n)));
+            t = ff_mul(ff_mul(t, w), ff_of(cSeriesInv[n]));
             se = ff_add(se, t);
-            sf = ff_add(sf, ff_mul(t, ff_of(series_inv_odd(n))));
+            sf = ff_add(sf, ff_mul(t, ff_of(cSeriesInvOdd[n])));
             if (fabsf(t.hi) < 1e-16f) break;
         }
         constexpr ffc k2rpi = ff_const(1.1283791670955125739);   // 2/sqrt(pi)
@@ -766,14 +763,14 @@ __device__ __forceinline__ int global_var(int c, int d) {
 // l: the right cell's position in the face-state buffer S (the face is its
 // low face along d); face states are read at buffer positions (stride
 // S.nb), the averages Q and the records at global cells (stride g.n).
-// mixed: the averages from Qv (VIEWQ: float-float pairs hi [5][n], lo
-// [5][n], written once per stage) or split here from the FP64 Q
-template <bool kCGKS, bool MIXED, bool VIEWQ = false>
+// mixed: the averages as float-float pairs Qhi, Qlo ([5][n] each, written
+// once per stage by q_to_ff_kernel)
+template <bool kCGKS, bool MIXED>
 __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S,
                                                 const PhysParams &P,
                                                 const void *__restrict__ fsv,
-                                                const double *__restrict__ Q,
-                                                const float *__restrict__ Qv, double dt,
+                                                const float *__restrict__ Qhi,
+                                                const float *__restrict__ Qlo, double dt,
                                                 double *__restrict__ frec, int *status, int d,
                                                 long long l, int k, bool valid) {
     constexpr int K = kCGKS ? 4 : 1;
@@ -837,13 +834,8 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             const int v = global_var(q, d);
-            if constexpr (VIEWQ) {
-                Ql[q] = ff_make(__ldg(Qv + (long long)v * n + left), __ldg(Qv + (long long)(5 + v) * n + left));
-                Qr[q] = ff_make(__ldg(Qv + (long long)v * n + c), __ldg(Qv + (long long)(5 + v) * n + c));
-            } else {
-                Ql[q] = ff_from_double(__ldg(Q + (long long)v * n + left));
-                Qr[q] = ff_from_double(__ldg(Q + (long long)v * n + c));
-            }
+            Ql[q] = ff_make(__ldg(Qhi + (long long)v * n + left), __ldg(Qlo + (long long)v * n + left));
+            Qr[q] = ff_make(__ldg(Qhi + (long long)v * n + c), __ldg(Qlo + (long long)v * n + c));
             ol[q] = __ldg(pl + (long long)q * nb);
             orr[q] = __ldg(pr + (long long)q * nb);
         }
@@ -891,7 +883,8 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S
 template <bool kCGKS, bool MIXED>
 __global__ void __launch_bounds__(128, MIXED ? 3 : 1) flux_faces_kernel(GridDesc g, Slab S, PhysParams P,
                                                          const void *__restrict__ fs,
-                                                         const float *__restrict__ Qv,
+                                                         const float *__restrict__ Qhi,
+                                                         const float *__restrict__ Qlo,
                                                          const double *__restrict__ dt_dev,
                                                          double *__restrict__ frec, int *status) {
     const double dt = *dt_dev;
@@ -907,8 +900,8 @@ __global__ void __launch_bounds__(128, MIXED ? 3 : 1) flux_faces_kernel(GridDesc
     const long long fc = gid / K;
     const int d = (int)(fc / cnt);
     const long long t = fc - (long long)d * cnt;
-    flux_face_point<kCGKS, MIXED, MIXED>(g, S, P, fs, nullptr, Qv, dt, frec, status, d,
-                                         S.p0 * nxy + t, k, valid);
+    flux_face_point<kCGKS, MIXED>(g, S, P, fs, Qhi, Qlo, dt, frec, status, d, S.p0 * nxy + t, k,
+                                  valid);
 }
 
 // Persistent ensemble flux (CGKS-5th): blocks stride over the work items
@@ -917,7 +910,8 @@ template <bool MIXED>
 __global__ void __launch_bounds__(128) flux_ens_kernel(const EnsInst *__restrict__ inst,
                                                        const EnsItem *__restrict__ items,
                                                        int nitems, const void *__restrict__ fsa,
-                                                       const double *__restrict__ Qa,
+                                                       const float *__restrict__ Qhia,
+                                                       const float *__restrict__ Qloa,
                                                        const double *__restrict__ dt_arr,
                                                        double *__restrict__ fra, int *status) {
     for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
@@ -937,9 +931,10 @@ __global__ void __launch_bounds__(128) flux_ens_kernel(const EnsInst *__restrict
             const long long rem = gid >> 2;
             const int d = (int)(rem / T);
             const long long c = it.c0 + rem % T;
-            flux_face_point<true, MIXED, false>(I.g, whole_grid(I.g), I.P, fs, Qa + 5 * I.off,
-                                                nullptr, dt, fra + 90 * I.off, status, d, c, k,
-                                                valid);
+            flux_face_point<true, MIXED>(I.g, whole_grid(I.g), I.P, fs,
+                                         MIXED ? Qhia + 5 * I.off : nullptr,
+                                         MIXED ? Qloa + 5 * I.off : nullptr, dt, fra + 90 * I.off,
+                                         status, d, c, k, valid);
         }
     }
 }
@@ -964,37 +959,36 @@ __global__ void __launch_bounds__(128) flux_points_kernel(PhysParams P, const do
 
 }  // namespace
 
-// float-float split of the averages: Qv hi [5][n] then lo [5][n]
-__global__ void q_to_ff_kernel(const double *__restrict__ Q, float *__restrict__ Qv, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 5 * n;
+// float-float split of m FP64 values: hi[i] + lo[i] = x[i] (to 2^-48)
+__global__ void q_to_ff_kernel(const double *__restrict__ x, float *__restrict__ hi,
+                               float *__restrict__ lo, long long m) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (long long)gridDim.x * blockDim.x) {
-        const ff x = ff_from_double(Q[i]);
-        const long long v = i / n, c = i - v * n;
-        Qv[v * n + c] = x.hi;
-        Qv[(5 + v) * n + c] = x.lo;
+        const ff v = ff_from_double(x[i]);
+        hi[i] = v.hi;
+        lo[i] = v.lo;
     }
 }
 
-int launch_q_to_ff(const GridDesc &g, const double *Q, float *Qv, cudaStream_t s) {
-    const long long m = 5 * g.n;
+int launch_q_to_ff(long long m, const double *x, float *hi, float *lo, cudaStream_t s) {
     const long long blocks = (m + 255) / 256;
-    q_to_ff_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(Q, Qv, g.n);
+    q_to_ff_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(x, hi, lo, m);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 int launch_flux_faces_mixed(const GridDesc &g, const Slab &S, const PhysParams &P,
-                            const float *fs, const float *Qv, const double *dt_dev, double *frec,
-                            int *status, cudaStream_t s) {
+                            const float *fs, const float *Qhi, const float *Qlo,
+                            const double *dt_dev, double *frec, int *status, cudaStream_t s) {
     const int K = P.scheme ? 4 : 1;
     const long long total = 3 * (long long)(S.nzb - S.p0) * g.nx * g.ny * K;
     const int block = 128;
     const long long grid = (total + block - 1) / block;
     if (P.scheme)
-        flux_faces_kernel<true, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Qv, dt_dev,
-                                                                        frec, status);
+        flux_faces_kernel<true, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Qhi, Qlo,
+                                                                        dt_dev, frec, status);
     else
-        flux_faces_kernel<false, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Qv, dt_dev,
-                                                                         frec, status);
+        flux_faces_kernel<false, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Qhi, Qlo,
+                                                                         dt_dev, frec, status);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -1006,20 +1000,25 @@ int launch_flux_faces(const GridDesc &g, const Slab &S, const PhysParams &P, con
     const long long grid = (total + block - 1) / block;
     if (P.scheme)
         flux_faces_kernel<true, false><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, nullptr,
-                                                                         dt_dev, frec, status);
+                                                                         nullptr, dt_dev, frec,
+                                                                         status);
     else
         flux_faces_kernel<false, false><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, nullptr,
-                                                                          dt_dev, frec, status);
+                                                                          nullptr, dt_dev, frec,
+                                                                          status);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
+// mixed: Qhia, Qloa are the float-float split of the averages' arena
 int launch_flux_ens(const EnsInst *inst, const EnsItem *items, int nitems, int blocks, int mixed,
-                    const void *fsa, const double *Qa, const double *dt_arr, double *fra,
-                    int *status, cudaStream_t s) {
+                    const void *fsa, const float *Qhia, const float *Qloa, const double *dt_arr,
+                    double *fra, int *status, cudaStream_t s) {
     if (mixed)
-        flux_ens_kernel<true><<<blocks, 128, 0, s>>>(inst, items, nitems, fsa, Qa, dt_arr, fra, status);
+        flux_ens_kernel<true><<<blocks, 128, 0, s>>>(inst, items, nitems, fsa, Qhia, Qloa, dt_arr,
+                                                     fra, status);
     else
-        flux_ens_kernel<false><<<blocks, 128, 0, s>>>(inst, items, nitems, fsa, Qa, dt_arr, fra, status);
+        flux_ens_kernel<false><<<blocks, 128, 0, s>>>(inst, items, nitems, fsa, nullptr, nullptr,
+                                                      dt_arr, fra, status);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

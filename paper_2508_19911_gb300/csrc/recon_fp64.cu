@@ -1,0 +1,345 @@
+// FP64 reconstruction kernels (Sec. 3.2 CGKS-5th, Sec. 3.3 GKS-2nd), the
+// FP64 ensemble reconstruction and the upload of the FP64 tables. Compiled
+// with the default multiply-add contraction.
+//
+// CGKS-5th, one thread per (cell, conserved variable): the data vector
+// orbit by orbit, a = R d by parity-class blocks, GENO, and the 24 face
+// Gauss points by a Walsh-Hadamard transform of the class sums (see
+// recon.cu). GKS-2nd, one thread per cell: central least-squares gradient,
+// the Venkatakrishnan limiter phi0 = min over the six faces, midpoint states.
+#include "recon_common.cuh"
+
+namespace gks {
+namespace {
+
+__constant__ double cR[kNumBasis][kNumData];
+__constant__ double cRs[kNumData][kMaxClass];  // R in the symmetrised data basis
+__constant__ double cH[kNumBasis][kNumBasis];
+__constant__ double cMean[kNumBasis];
+__constant__ double cMval[3][kNumBasis];
+__constant__ double cMder[3][3][kNumBasis];
+// Value of data column K for one (cell, variable) (layout in basis.h)
+template <int K>
+__device__ __forceinline__ double data_col(const double *__restrict__ Qv,
+                                           const double *__restrict__ Gv, long long n, long long c,
+                                           const long long nbF[6], const long long nbE[12],
+                                           double q0, const double h[3]) {
+    if constexpr (K < kColEdge) {
+        return __ldg(Qv + nbF[K]) - q0;
+    } else if constexpr (K < kColFaceGrad) {
+        return __ldg(Qv + nbE[K - kColEdge]) - q0;
+    } else if constexpr (K < kColEdgeGrad) {
+        constexpr int m = (K - kColFaceGrad) / 3, j = (K - kColFaceGrad) % 3;
+        return h[j] * __ldg(Gv + j * n + nbF[m]);
+    } else if constexpr (K < kColCentreGrad) {
+        constexpr int e = (K - kColEdgeGrad) / 2;
+        constexpr int ea = edge_axis_a(e), eb = edge_axis_b(e), ee = edge_axis_e(e);
+        if constexpr ((K - kColEdgeGrad) % 2 == 0) {
+            constexpr double oa = edge_off(e, ea), ob = edge_off(e, eb);
+            const double da = h[ea] * __ldg(Gv + ea * n + nbE[e]);
+            const double db = h[eb] * __ldg(Gv + eb * n + nbE[e]);
+            return (oa * da - ob * db) * kRs2;
+        } else {
+            return h[ee] * __ldg(Gv + ee * n + nbE[e]);
+        }
+    } else {
+        constexpr int j = K - kColCentreGrad;
+        return h[j] * __ldg(Gv + j * n + c);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void eval_faces(double *__restrict__ fs, long long n, long long c,
+                                           int v, const double a[kNumBasis], double base,
+                                           double chi, const double bbar[3], double q0,
+                                           bool nonlinear, const double ih[3]) {
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    double S[8], Dq[3][8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        S[k] = 0.0;
+        Dq[0][k] = Dq[1][k] = Dq[2][k] = 0.0;
+    }
+    static_for<kNumBasis>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int cls = basis_class(i);
+        S[cls] = fma(a[i], cMval[D][i], S[cls]);
+        static_for<3>([&](auto Qc) {
+            constexpr int q = decltype(Qc)::value;
+            if constexpr (has_deriv(i, q)) {
+                constexpr int dc = deriv_class(i, q);
+                Dq[q][dc] = fma(a[i], cMder[D][q][i], Dq[q][dc]);
+            }
+        });
+    });
+    class_to_points(S);
+    class_to_points(Dq[0]);
+    class_to_points(Dq[1]);
+    class_to_points(Dq[2]);
+    const int cmp = frame_comp(v, D);
+#pragma unroll
+    for (int side = 0; side < 2; ++side)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int p = (side << D) | ((kk & 1) << T1) | (((kk >> 1) & 1) << T2);
+            double val = base + S[p], der[3] = {Dq[0][p], Dq[1][p], Dq[2][p]};
+            if (nonlinear) {
+                double x[3];
+                x[D] = side ? 0.5 : -0.5;
+                x[T1] = (kk & 1) ? kG : -kG;
+                x[T2] = (kk & 2) ? kG : -kG;
+                const double p1 = fma(bbar[0], x[0], fma(bbar[1], x[1], fma(bbar[2], x[2], q0)));
+                val = fma(chi, val - p1, p1);  // chi P4 + (1 - chi) P1
+#pragma unroll
+                for (int q = 0; q < 3; ++q) der[q] = fma(chi, der[q] - bbar[q], bbar[q]);
+            }
+            double *o = fs + ((long long)((2 * D + side) * 4 + kk) * 20) * n + c;
+            o[(long long)cmp * n] = val;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int jf = (q - D + 3) % 3;
+                o[(long long)(5 + 5 * jf + cmp) * n] = der[q] * ih[q];
+            }
+        }
+}
+
+// cell c (global), variable v; face states to buffer position l (stride nb)
+__device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
+                                            const double *__restrict__ Q,
+                                            const double *__restrict__ G,
+                                            double *__restrict__ fs, long long c, int v,
+                                            long long nb, long long l) {
+    const long long n = g.n;
+    const int i = (int)(c % g.nx);
+    const int j = (int)((c / g.nx) % g.ny);
+    const int k = (int)(c / ((long long)g.nx * g.ny));
+    long long nbF[6], nbE[12];
+#pragma unroll
+    for (int m = 0; m < 6; ++m)
+        nbF[m] = cell_index(g, wrap(i + face_off(m, 0), g.nx), wrap(j + face_off(m, 1), g.ny),
+                            wrap(k + face_off(m, 2), g.nz));
+#pragma unroll
+    for (int e = 0; e < 12; ++e)
+        nbE[e] = cell_index(g, wrap(i + edge_off(e, 0), g.nx), wrap(j + edge_off(e, 1), g.ny),
+                            wrap(k + edge_off(e, 2), g.nz));
+    const double h[3] = {g.h[0], g.h[1], g.h[2]};
+    const double ih[3] = {1.0 / h[0], 1.0 / h[1], 1.0 / h[2]};
+
+    const double *Qv = Q + (long long)v * n;
+    const double *Gv = G + (long long)v * 3 * n;
+    const double q0 = __ldg(Qv + c);
+    double a[kNumBasis];
+#pragma unroll
+    for (int ii = 0; ii < kNumBasis; ++ii) a[ii] = 0.0;
+    double dface[6], dctr[3];
+    // a = R d orbit by orbit: load the orbit's columns, form its symmetrised
+    // combinations, multiply each with its class block of R
+    double ov[8];
+    static_for<kNumData>([&](auto Rr) {
+        constexpr int r = decltype(Rr)::value;
+        constexpr int nm = kSym.nm[r];
+        if constexpr (kSym.orbit[r] == r) {
+            static_for<nm>([&](auto Qq) {
+                constexpr int q = decltype(Qq)::value;
+                constexpr int col = kSym.mem[r][q];
+                ov[q] = data_col<col>(Qv, Gv, n, c, nbF, nbE, q0, h);
+                if constexpr (col < kColEdge) dface[col] = ov[q];
+                if constexpr (col >= kColCentreGrad) dctr[col - kColCentreGrad] = ov[q];
+            });
+        }
+        double ds = kSym.sgn[r][0] > 0 ? ov[0] : -ov[0];
+        static_for<nm - 1>([&](auto Qq) {
+            constexpr int q = decltype(Qq)::value + 1;
+            if constexpr (kSym.sgn[r][q] > 0) ds += ov[q];
+            else ds -= ov[q];
+        });
+        constexpr int cls = kSym.cls[r];
+        static_for<kClass.n[cls]>([&](auto J) {
+            constexpr int jj = decltype(J)::value;
+            constexpr int ib = kClass.member[cls][jj];
+            a[ib] = fma(cRs[r][jj], ds, a[ib]);
+        });
+    });
+
+    // P4(x) = Q0 - sum_i a_i mean_i + sum_i a_i x^{e_i}/e_i!
+    double K = 0.0;
+    static_for<kNumBasis>([&](auto I) {
+        constexpr int ii = decltype(I)::value;
+        if constexpr (basis_class(ii) == 0) K = fma(a[ii], cMean[ii], K);
+    });
+    const double base = q0 - K;
+
+    double chi = 1.0, bbar[3] = {0.0, 0.0, 0.0};
+    if (nonlinear) {
+        const double eps = 1e-15;
+        double w[6], IS[6], wsum = 0.0;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            const int ax = m / 2;
+            const double bn = (m & 1) ? dface[m] : -dface[m];
+            double s = bn * bn;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (q != ax) s = fma(dctr[q], dctr[q], s);
+            IS[m] = s;
+            const double t = s + eps, t2 = t * t;
+            w[m] = (1.0 / 6.0) / (t2 * t2 * t);
+            wsum += w[m];
+        }
+        double ISL = 0.0;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            w[m] /= wsum;
+            ISL = fma(w[m], IS[m], ISL);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            // sum_m w_m b^m_q: tangential slopes from the own gradient,
+            // the normal one from the neighbour difference
+            bbar[q] = (1.0 - w[2 * q] - w[2 * q + 1]) * dctr[q] - w[2 * q] * dface[2 * q] +
+                      w[2 * q + 1] * dface[2 * q + 1];
+        }
+        double ISH = 0.0;
+        static_for<kNumBasis>([&](auto I) {
+            constexpr int ii = decltype(I)::value;
+            double t = 0.0;
+            static_for<kNumBasis>([&](auto J) {
+                constexpr int jj = decltype(J)::value;
+                if constexpr (basis_class(ii) == basis_class(jj)) t = fma(cH[ii][jj], a[jj], t);
+            });
+            ISH = fma(a[ii], t, ISH);
+        });
+        const double r = fabs(ISH - ISL) / (ISH + ISL + eps);
+        const double rr = r * 10.0;
+        chi = 1.0 / (1.0 + rr * rr * rr);
+    }
+    eval_faces<0>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
+    eval_faces<1>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
+    eval_faces<2>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
+}
+
+__global__ void __launch_bounds__(128) recon5_kernel(GridDesc g, Slab S, int nonlinear,
+                                                     const double *__restrict__ Q,
+                                                     const double *__restrict__ G,
+                                                     double *__restrict__ fs) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < S.nb)
+        recon5_cell(g, nonlinear, Q, G, fs, slab_global(g, S, l), (int)blockIdx.y, S.nb, l);
+}
+
+__global__ void __launch_bounds__(128) recon2_kernel(GridDesc g, Slab S, int nonlinear,
+                                                     double eps2, const double *__restrict__ Q,
+                                                     double *__restrict__ fs) {
+    const long long n = g.n;
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= S.nb) return;
+    const long long c = slab_global(g, S, l);
+    const int i = (int)(c % g.nx);
+    const int j = (int)((c / g.nx) % g.ny);
+    const int k = (int)(c / ((long long)g.nx * g.ny));
+    long long nb[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m)
+        nb[m] = cell_index(g, wrap(i + face_off(m, 0), g.nx), wrap(j + face_off(m, 1), g.ny),
+                           wrap(k + face_off(m, 2), g.nz));
+#pragma unroll 1
+    for (int v = 0; v < 5; ++v) {
+        const double *Qv = Q + (long long)v * n;
+        const double q0 = __ldg(Qv + c);
+        double qn[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) qn[m] = __ldg(Qv + nb[m]);
+        // least-squares gradient of the face-neighbour averages on a uniform
+        // grid: the central difference (normalised units)
+        double b[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) b[d] = 0.5 * (qn[2 * d + 1] - qn[2 * d]);
+        double phi = 1.0;
+        if (nonlinear) {
+            double qmax = q0, qmin = q0;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                qmax = fmax(qmax, qn[m]);
+                qmin = fmin(qmin, qn[m]);
+            }
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                const double d2 = (f & 1) ? 0.5 * b[f / 2] : -0.5 * b[f / 2];
+                if (d2 != 0.0) {
+                    const double dp = d2 > 0.0 ? qmax - q0 : qmin - q0;
+                    const double pf = (dp * dp + eps2 + 2.0 * d2 * dp) /
+                                      (dp * dp + 2.0 * d2 * d2 + d2 * dp + eps2);
+                    phi = fmin(phi, pf);
+                }
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const int d = f / 2;
+            const int cmp = frame_comp(v, d);
+            double *o = fs + ((long long)f * 20) * S.nb + l;
+            o[(long long)cmp * S.nb] = q0 + phi * ((f & 1) ? 0.5 : -0.5) * b[d];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int jf = (q - d + 3) % 3;
+                o[(long long)(5 + 5 * jf + cmp) * S.nb] = phi * b[q] / g.h[q];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) recon5_ens_fp64_kernel(const EnsInst *__restrict__ inst,
+                                                              const EnsItem *__restrict__ items,
+                                                              int nitems,
+                                                              const double *__restrict__ Qa,
+                                                              const double *__restrict__ Ga,
+                                                              double *__restrict__ fsa) {
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const EnsItem it = items[w];
+        const EnsInst I = inst[it.inst];
+        const double *Q = Qa + 5 * I.off;
+        const double *G = Ga + 15 * I.off;
+        const long long T = it.c1 - it.c0;
+        for (long long t = threadIdx.x; t < 5 * T; t += blockDim.x)
+            recon5_cell(I.g, I.P.nonlinear, Q, G, fsa + 480 * I.off, it.c0 + t % T, (int)(t / T),
+                        I.g.n, it.c0 + t % T);
+    }
+}
+
+}  // namespace
+
+int upload_recon_tables_fp64(const ReconTables &t) {
+    if (cudaMemcpyToSymbol(cR, t.R, sizeof(t.R)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(cRs, t.Rs, sizeof(t.Rs)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(cH, t.H, sizeof(t.H)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(cMean, t.mean, sizeof(t.mean)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(cMval, t.mval, sizeof(t.mval)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(cMder, t.mder, sizeof(t.mder)) != cudaSuccess) return -2;
+    return 0;
+}
+
+int launch_recon5_ens_fp64(const EnsInst *inst, const EnsItem *items, int nitems, int blocks,
+                           const double *Qa, const double *Ga, double *fsa, cudaStream_t s) {
+    recon5_ens_fp64_kernel<<<blocks, 128, 0, s>>>(inst, items, nitems, Qa, Ga, fsa);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_recon5(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
+                  const double *G, double *fs, cudaStream_t s) {
+    const int block = 128;
+    const long long grid = (S.nb + block - 1) / block;
+    recon5_kernel<<<dim3((unsigned)grid, 5), block, 0, s>>>(g, S, P.nonlinear, Q, G, fs);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int launch_recon2(const GridDesc &g, const Slab &S, const PhysParams &P, const double *Q,
+                  double *fs, cudaStream_t s) {
+    const double hv = cbrt(g.h[0] * g.h[1] * g.h[2]);
+    const double eps2 = hv * hv * hv;  // (K h)^3 with K = 1
+    const int block = 128;
+    const long long grid = (S.nb + block - 1) / block;
+    recon2_kernel<<<(unsigned)grid, block, 0, s>>>(g, S, P.nonlinear, eps2, Q, fs);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+}  // namespace gks
