@@ -528,8 +528,8 @@ __device__ __forceinline__ PrimFF to_prim_ff(const ff s[5], ff gm1) {
     return P;
 }
 
-// Half-line starting moments of one side (SGN = +1: u > 0; -1: u < 0):
-// with y = sqrt(lam) U, m0 = (1 + SGN erf(y))/2 and m1 = U m0 + SGN
+// Half-line starting moments of one side (sgn = +1: u > 0; -1: u < 0):
+// with y = sqrt(lam) U, m0 = (1 + sgn erf(y))/2 and m1 = U m0 + sgn
 // e^{-y^2}/(2 sqrt(pi lam)). For |y| <= 2 (every state below a component
 // Mach number of ~2.4) erf and the exponential come from one series in
 // t_n = (-y^2)^n/n!: e^{-y^2} = sum t_n, erf(y) = 2y/sqrt(pi) sum t_n/(2n+1),
@@ -561,8 +561,7 @@ __constant__ ffc cSeriesInvOdd[kSeriesTerms + 1] = {
     ff_const(1.0 / 57), ff_const(1.0 / 59), ff_const(1.0 / 61), ff_const(1.0 / 63),
     ff_const(1.0 / 65)};
 
-template <int SGN>
-__device__ __forceinline__ void half_start_ff(const PrimFF &S, ff &m0, ff &m1) {
+__device__ __forceinline__ void half_start_ff(const PrimFF &S, int sgn, ff &m0, ff &m1) {
     const ff sl = ff_sqrt(S.lam);
     const ff y = ff_mul(sl, S.U);
     if (fabsf(y.hi) <= 2.0f) {
@@ -578,12 +577,12 @@ __device__ __forceinline__ void half_start_ff(const PrimFF &S, ff &m0, ff &m1) {
         constexpr ffc k2rpi = ff_const(1.1283791670955125739);   // 2/sqrt(pi)
         constexpr ffc krpi = ff_const(0.56418958354775628695);   // 1/sqrt(pi)
         const ff erf = ff_mul(ff_mul(y, ff_of(k2rpi)), sf);
-        m0 = ff_half(SGN > 0 ? ff_add_f(erf, 1.0f) : ff_sub(ff_make(1.0f, 0.0f), erf));
+        m0 = ff_half(sgn > 0 ? ff_add_f(erf, 1.0f) : ff_sub(ff_make(1.0f, 0.0f), erf));
         const ff edge = ff_half(ff_div(ff_mul(se, ff_of(krpi)), sl));
-        m1 = SGN > 0 ? ff_add(ff_mul(S.U, m0), edge) : ff_sub(ff_mul(S.U, m0), edge);
+        m1 = sgn > 0 ? ff_add(ff_mul(S.U, m0), edge) : ff_sub(ff_mul(S.U, m0), edge);
     } else {
         double d0, d1;
-        half_start(ff_to_double(S.U), ff_to_double(S.lam), (double)SGN, d0, d1);
+        half_start(ff_to_double(S.U), ff_to_double(S.lam), (double)sgn, d0, d1);
         m0 = ff_from_double(d0);
         m1 = ff_from_double(d1);
     }
@@ -591,11 +590,10 @@ __device__ __forceinline__ void half_start_ff(const PrimFF &S, ff &m0, ff &m1) {
 
 // rho <psi> and rho <u psi> of one side over its half line, added to W0 and
 // X4; returns the half-line starting moments for the FP32 core
-template <int SGN>
-__device__ __forceinline__ void half_side_ff(const PrimFF &S, ff N, ff W0[5], ff X4[5],
+__device__ __forceinline__ void half_side_ff(const PrimFF &S, int sgn, ff N, ff W0[5], ff X4[5],
                                              float &m0f, float &m1f) {
     ff u[4];
-    half_start_ff<SGN>(S, u[0], u[1]);
+    half_start_ff(S, sgn, u[0], u[1]);
     m0f = u[0].hi;
     m1f = u[1].hi;
     const ff inv2l = ff_half(ff_recip(S.lam));
@@ -651,8 +649,8 @@ __device__ void flux_point_mixed(const PhysParams &P, const ff Ql[5], const floa
 #pragma unroll
     for (int i = 0; i < 5; ++i) W0[i] = X4[i] = ff_make(0.0f, 0.0f);
     float ul0, ul1, ur0, ur1;
-    half_side_ff<1>(L, N, W0, X4, ul0, ul1);
-    half_side_ff<-1>(R, N, W0, X4, ur0, ur1);
+    half_side_ff(L, 1, N, W0, X4, ul0, ul1);
+    half_side_ff(R, -1, N, W0, X4, ur0, ur1);
     const PrimFF Z = to_prim_ff(W0, gm1);
     if (!(Z.rho.hi > 0.0f && Z.p.hi > 0.0f)) {
         flag_status(status, kStatusNonphysical);
@@ -684,8 +682,23 @@ __device__ void flux_point_mixed(const PhysParams &P, const ff Ql[5], const floa
     for (int k = 0; k < 6; ++k)
 #pragma unroll
         for (int i = 0; i < 5; ++i) X[k][i] = 0.0f;
-    side_terms<1>(dl, Lf, Nf, ul0, ul1, Zf.U, Zf.V, Zf.W, dW0, X[3], X[4], X[5], q + 3, dtWl);
-    side_terms<-1>(dr, Rf, Nf, ur0, ur1, Zf.U, Zf.V, Zf.W, dW0, X[3], X[4], X[5], q + 3, dtWr);
+    // both sides through one copy of the code (left, then right: the order
+    // of two inlined calls); the kernel is bound by instruction issue and
+    // fetch, and one copy of the side terms halves their footprint
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        float ds[15], dtW[5];
+#pragma unroll
+        for (int i = 0; i < 15; ++i) ds[i] = side ? dr[i] : dl[i];
+        const PrimT<float> S = side ? Rf : Lf;
+        side_terms<1>(ds, S, Nf, side ? ur0 : ul0, side ? ur1 : ul1, Zf.U, Zf.V, Zf.W, dW0, X[3],
+                      X[4], X[5], q + 3, dtW);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            if (side) dtWr[i] = dtW[i];
+            else dtWl[i] = dtW[i];
+        }
+    }
     equilibrium_terms<false>(Zf, Nf, dW0, X, q, dtW0);  // a Maxwellian carries no heat flux: q1 = 0
 
     // collision time (Sec. 4) in FP32; time coefficients in FP32 for
