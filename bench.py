@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=128, help="cells per axis")
+    ap.add_argument("--n", type=int, default=None,
+                    help="cells per axis (default 128; --c2 64, --c3 256, --c5 512)")
     ap.add_argument("--scheme", default="cgks5", choices=["cgks5", "gks2"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--indicator", action="store_true",
@@ -86,7 +87,21 @@ def parse():
                          "four-quadrant Riemann problems), autotuned tiles, graph-replayed steps")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="--c5: FP64 steps (an FP64 step at 512^3 takes ~23 s)")
-    return ap.parse_args()
+    ap.add_argument("--c2", action="store_true",
+                    help="Taylor-Green vortex to t_end with E_k, eps_S, eps_D histories, FP64 "
+                         "and mixed on one grid (default 64^3)")
+    ap.add_argument("--t-end", type=float, default=10.0, help="--c2: final time (U0 = L = 1)")
+    ap.add_argument("--every", type=float, default=0.1, help="--c2: sampling interval")
+    ap.add_argument("--precisions", default="fp64,mixed", help="--c2: paths to run")
+    ap.add_argument("--c3", action="store_true",
+                    help="isotropic turbulence Mt 0.5 and 1.0 (Re_lambda 72), FP64 vs mixed vs "
+                         "mixed + learned indicator, per-step E_k, eps_S, eps_D (default 256^3)")
+    ap.add_argument("--history", default=None,
+                    help="--c2/--c3: write the sampled histories to this JSON file")
+    args = ap.parse_args()
+    if args.n is None:
+        args.n = 64 if args.c2 else 256 if args.c3 else 512 if args.c5 else 128
+    return args
 
 
 # ---------------------------------------------------------------------------
@@ -156,13 +171,13 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(scheme, seconds_hint=15.0):
+def cpu_baseline(scheme):
     """The FP64 oracle as it stands, OpenMP over cells on all host cores,
-    on a bounded sample: the same Taylor-Green workload at 24^3 (CGKS-5th)
-    or 48^3 (GKS-2nd), 2 time steps."""
+    on a bounded sample (about 15 s on 16 cores): the same Taylor-Green
+    workload at 48^3 (CGKS-5th) or 96^3 (GKS-2nd), 2 time steps."""
     import oracle
     from paper_2508_19911_gb300 import workloads as wl
-    n = 24 if scheme == "cgks5" else 48
+    n = 48 if scheme == "cgks5" else 96
     steps = 2
     Q, G, grid = wl.taylor_green(n)
     cores = os.cpu_count() or 1
@@ -435,6 +450,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "cell-stage/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "cell_steps_per_s": value / stages,
         "dtype": "f64" if prec == "fp64" else "f32+f64",
         "indicator": ind_info if args.indicator else None,
         "data": wdata,
@@ -545,6 +561,179 @@ def run_c5(args):
     return line
 
 
+def _dump_history(path, obj):
+    if path:
+        with open(path, "w") as f:
+            json.dump(obj, f)
+
+
+def run_c2(args):
+    """Taylor-Green vortex (Ma 0.1, Re 1600, U0 = L = 1), CGKS-5th
+    nonlinear, from t = 0 to t_end: the kinetic energy E_k and the
+    solenoidal and dilatational dissipation eps_S, eps_D sampled every
+    `every` time units on each path (FP64, mixed); -dE_k/dt from centred
+    differences of the samples; the mixed history's largest deviation from
+    FP64. Each sample time is hit exactly (the last step before it is
+    clamped on the device); steps past it are no-ops."""
+    import torch
+
+    from paper_2508_19911_gb300 import gks
+    from paper_2508_19911_gb300 import workloads as wl
+
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    n = args.n
+    Qh, Gh, grid = wl.taylor_green(n)
+    nsamp = int(round(args.t_end / args.every))
+    times = [args.every * j for j in range(nsamp + 1)]
+    hist, paths = {"times": times}, {}
+    for prec in args.precisions.split(","):
+        s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision=prec), stream)
+        Q = torch.tensor(Qh, device=dev)
+        G = torch.tensor(Gh, device=dev)
+        t = torch.zeros(1, dtype=torch.float64, device=dev)
+        diag = [s.diagnostics(Q, G)]
+        steps, ms = 0, 0.0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            for ts in times[1:]:
+                while True:
+                    t_now = float(t.item())
+                    if ts - t_now <= 1e-9 * ts:
+                        break
+                    dt_est = float(s.compute_dt(Q).item())
+                    k = max(1, math.ceil((ts - t_now) / dt_est - 1e-6))
+                    e0.record(stream)
+                    s.step(Q, G, nsteps=k, t_stop=ts, t=t, sync=False)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                    steps += k
+                diag.append(s.diagnostics(Q, G))  # raises on a non-physical state
+        s.close()
+        del Q, G
+        torch.cuda.empty_cache()
+        d = np.array(diag)
+        ek, es, ed = d[:, 0], d[:, 1], d[:, 2]
+        rate = -(ek[2:] - ek[:-2]) / (2 * args.every)
+        j = int(np.argmax(rate))
+        hist[prec] = {"E_k": ek.tolist(), "eps_S": es.tolist(), "eps_D": ed.tolist()}
+        paths[prec] = {
+            "steps": steps, "ms_per_step": ms / steps,
+            "value": n ** 3 * 2 * steps / (ms / 1e3), "unit": "cell-stage/s",
+            "E_k_end_over_E_k0": float(ek[-1] / ek[0]),
+            "peak_minus_dEk_dt": float(rate[j]), "peak_time": times[j + 1],
+            "eps_S_at_peak": float(es[j + 1]), "eps_D_at_peak": float(ed[j + 1]),
+            "peak_eps_S": float(es.max()), "peak_eps_S_time": times[int(np.argmax(es))],
+            "clocks": clk.summary()}
+    if "fp64" in hist:
+        ref = hist["fp64"]
+        for prec in paths:
+            if prec == "fp64":
+                continue
+            h = hist[prec]
+            paths[prec]["max_dev_E_k_vs_fp64"] = float(
+                np.max(np.abs(np.array(h["E_k"]) - ref["E_k"])) / ref["E_k"][0])
+            paths[prec]["max_dev_eps_S_vs_fp64"] = float(
+                np.max(np.abs(np.array(h["eps_S"]) - ref["eps_S"])) / np.max(ref["eps_S"]))
+    _dump_history(args.history, hist)
+    first = paths[next(iter(paths))]
+    return {
+        "metric": METRIC, "value": first["value"], "unit": "cell-stage/s", "n_gpus": 1,
+        "steps": first["steps"], "warmup": 0, "ms_per_step": first["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if "fp64" in paths else "f32+f64",
+        "data": "synthetic (Taylor-Green cell averages)",
+        "config": {"workload": f"taylor_green_{n}^3_cgks5_to_t{args.t_end:g}", "cells": n ** 3,
+                   "Ma": 0.1, "Re": 1600, "sample_every": args.every},
+        "paths": paths,
+    }
+
+
+def run_c3(args):
+    """Decaying isotropic turbulence on [0, 2 pi]^3 (k0 = 8; mu = rho0
+    u_rms lambda/Re_lambda with Re_lambda = 72 and lambda the Taylor
+    microscale of the discrete initial field): Mt 0.5 (seed 101) and Mt 1.0
+    (seed 102), CGKS-5th nonlinear on three paths (FP64, mixed, mixed +
+    learned indicator) for the same steps; E_k, eps_S and eps_D after every
+    step, the device time of each path, the indicator's skip fraction, and
+    the mixed paths' deviations from FP64 (per-cell kinetic energy, relative
+    L2, at the end; dissipation histories)."""
+    import torch
+
+    from paper_2508_19911_gb300 import gks
+    from paper_2508_19911_gb300 import workloads as wl
+
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    n = args.n
+    cells = n ** 3
+    params, ind_info = trained_indicator(torch, dev)
+    steps = args.steps
+    hist, cases = {}, {}
+    for Mt, seed in ((0.5, 101), (1.0, 102)):
+        Qh, Gh, grid, info = wl.isotropic_turbulence(n, Mt=Mt, k0=8.0, seed=seed)
+        mu = info["u_rms"] * info["taylor_lambda"] / 72.0
+        key = f"Mt{Mt:g}"
+        hist[key], res, kes = {}, {}, {}
+        for prec, learned in (("fp64", False), ("mixed", False), ("mixed", True)):
+            tag = "learned" if learned else prec
+            s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision=prec,
+                                      indicator=learned, mu=mu), stream)
+            if learned:
+                s.set_indicator(params, theta=ind_info["theta"])
+            Q = torch.tensor(Qh, device=dev)
+            G = torch.tensor(Gh, device=dev)
+            diag = [s.diagnostics(Q, G)]
+            ms = 0.0
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            for _ in range(steps):
+                e0.record(stream)
+                s.step(Q, G, nsteps=1, sync=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                diag.append(s.diagnostics(Q, G))  # raises on a non-physical state
+            d = np.array(diag)
+            hist[key][tag] = {"E_k": d[:, 0].tolist(), "eps_S": d[:, 1].tolist(),
+                              "eps_D": d[:, 2].tolist(), "min_p": d[:, 4].tolist()}
+            res[tag] = {"ms_per_step": ms / steps, "value": cells * 2 * steps / (ms / 1e3),
+                        "unit": "cell-stage/s", "E_k_end_over_E_k0": float(d[-1, 0] / d[0, 0]),
+                        "eps_D_over_eps_S_end": float(d[-1, 2] / d[-1, 1])}
+            if learned:
+                res[tag]["skip_fraction"] = s.indicator_skips() / (5 * cells * 2 * steps)
+            kes[tag] = 0.5 * (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0]
+            s.close()
+            del Q, G
+            torch.cuda.empty_cache()
+        ref = hist[key]["fp64"]
+        for tag in ("mixed", "learned"):
+            dk = kes[tag] - kes["fp64"]
+            res[tag]["ke_rel_l2_vs_fp64"] = float(torch.linalg.vector_norm(dk) /
+                                                  torch.linalg.vector_norm(kes["fp64"]))
+            for q in ("eps_S", "eps_D"):
+                r = np.array(ref[q])
+                res[tag][f"max_dev_{q}_vs_fp64"] = float(
+                    np.max(np.abs(np.array(hist[key][tag][q]) - r)) / np.max(np.abs(r)))
+        del kes
+        torch.cuda.empty_cache()
+        cases[key] = {"seed": seed, "mu": mu, "u_rms": info["u_rms"],
+                      "taylor_lambda": info["taylor_lambda"], "paths": res}
+    _dump_history(args.history, hist)
+    lead = cases["Mt0.5"]["paths"]["learned"]
+    return {
+        "metric": METRIC, "value": lead["value"], "unit": "cell-stage/s", "n_gpus": 1,
+        "steps": steps, "warmup": 0, "ms_per_step": lead["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded isotropic turbulence)",
+        "config": {"workload": f"isotropic_turbulence_{n}^3_cgks5_Mt0.5_Mt1.0", "cells": cells,
+                   "k0": 8, "Re_lambda": 72, "indicator": ind_info},
+        "cases": cases,
+    }
+
+
 def run_c4(args):
     """The batched ensemble (row a9): 64 seeded 2D instances of 64^2..512^2
     cells advanced together by persistent launches over one work list,
@@ -601,6 +790,12 @@ def main():
         return
     if args.c5:
         print(json.dumps(run_c5(args)))
+        return
+    if args.c2:
+        print(json.dumps(run_c2(args)))
+        return
+    if args.c3:
+        print(json.dumps(run_c3(args)))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
