@@ -171,6 +171,18 @@ int gks_flux_points(gks_ctx *ctx, const double *s_l, const double *s_r,
 int gks_step(gks_ctx *ctx, double *Q, double *gradQ, int nsteps,
              double t_stop, double *t_dev, double *dt_host_last);
 
+/* a0-a4 for callers that hold the state in HOST memory: copies Q (and, for
+ * CGKS-5th, gradQ) host -> device into buffers the context owns, advances
+ * nsteps steps exactly as gks_step, and copies the state (and *t) back.
+ * Q, gradQ: caller-owned host arrays in the layouts of gks_step (pinned
+ * memory for full copy bandwidth; pageable memory works); t: host scalar,
+ * in/out simulation time, or NULL (no time tracking, t_stop ignored).
+ * Synchronising. The device buffers (the state's size plus one double) are
+ * allocated on the first call and kept until gks_destroy; GKS_ERR_NOMEM if
+ * that fails. Returns GKS_ERR_NONPHYSICAL if the status word was set. */
+int gks_step_host(gks_ctx *ctx, double *Q, double *gradQ, int nsteps, double t_stop,
+                  double *t);
+
 /* a5 -- diagnostics (Sec. 4.1/4.2), synchronising; out (host, 12 doubles):
  *  [0] E_k  = (1/|Omega|) sum rho |U|^2/2 h^3 (divide by rho0 U0^2 for the
  *            paper's normalisation)

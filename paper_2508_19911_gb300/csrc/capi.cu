@@ -32,6 +32,7 @@ struct gks_ctx {
     int *status;
     double *partials;
     int diag_blocks;
+    double *hQ, *hG, *hT;  // device state of gks_step_host (allocated on its first call)
 };
 
 namespace {
@@ -110,6 +111,9 @@ void gks_destroy(gks_ctx *c) {
     cudaFree(c->status);
     cudaFree(c->partials);
     cudaFree(c->skips);
+    cudaFree(c->hQ);
+    cudaFree(c->hG);
+    cudaFree(c->hT);
     if (prev >= 0) cudaSetDevice(prev);
     delete c;
 }
@@ -336,6 +340,45 @@ int gks_step(gks_ctx *c, double *Q, double *G, int nsteps, double t_stop, double
         if (st) return GKS_ERR_NONPHYSICAL;
     }
     return GKS_OK;
+}
+
+int gks_step_host(gks_ctx *c, double *Q, double *G, int nsteps, double t_stop, double *t) {
+    if (!c || !Q || nsteps < 0) return GKS_ERR_ARG;
+    const bool cgks = c->P.scheme == GKS_SCHEME_CGKS5;
+    if (cgks && !G) return GKS_ERR_ARG;
+    const size_t qn = (size_t)5 * c->g.n;
+    if (!c->hQ) {
+        int rc;
+        if ((rc = dalloc(&c->hT, 1)) || (cgks && (rc = dalloc(&c->hG, 3 * qn))) ||
+            (rc = dalloc(&c->hQ, qn))) {
+            cudaFree(c->hT);
+            cudaFree(c->hG);
+            c->hT = nullptr;
+            c->hG = nullptr;
+            return rc;
+        }
+    }
+    const size_t qb = qn * sizeof(double);
+    if (cudaMemcpyAsync(c->hQ, Q, qb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        (cgks && cudaMemcpyAsync(c->hG, G, 3 * qb, cudaMemcpyHostToDevice, c->stream) !=
+                     cudaSuccess) ||
+        (t && cudaMemcpyAsync(c->hT, t, sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
+                  cudaSuccess))
+        return GKS_ERR_CUDA;
+    const int rc = gks_step(c, c->hQ, cgks ? c->hG : nullptr, nsteps, t_stop, t ? c->hT : nullptr,
+                            nullptr);
+    if (rc) return rc;
+    int st = 0;
+    if (cudaMemcpyAsync(Q, c->hQ, qb, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        (cgks && cudaMemcpyAsync(G, c->hG, 3 * qb, cudaMemcpyDeviceToHost, c->stream) !=
+                     cudaSuccess) ||
+        (t && cudaMemcpyAsync(t, c->hT, sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+                  cudaSuccess) ||
+        cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return GKS_ERR_CUDA;
+    return st ? GKS_ERR_NONPHYSICAL : GKS_OK;
 }
 
 int gks_diagnostics(gks_ctx *c, const double *Q, const double *G, double *out) {

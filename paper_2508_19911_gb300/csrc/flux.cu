@@ -33,9 +33,9 @@ __device__ __forceinline__ void full_line(T C, T inv2l, T *m) {
 
 // starting values of the half-line moments: sgn = +1 for u > 0, -1 for u < 0
 __device__ __forceinline__ void half_start(double C, double lam, double sgn, double &m0, double &m1) {
-    const double sl = sqrt(lam);
+    const double rsl = rsqrt(lam), sl = lam * rsl;
     m0 = 0.5 * erfc(-sgn * sl * C);
-    const double edge = 0.5 * exp(-lam * C * C) / (sl * 1.7724538509055160273);  // sqrt(pi)
+    const double edge = 0.28209479177387814347 * exp(-lam * C * C) * rsl;  // 1/(2 sqrt(pi))
     m1 = C * m0 + sgn * edge;
 }
 
@@ -110,15 +110,17 @@ __device__ __forceinline__ void dir_acc(const T a[3][5], const T *u, const T *v,
     apsi_acc<E, 0, 1>(a[2], u, v, w, x2, x4, s, acc);
 }
 
-// Slope of a Maxwellian (U, V, W, lam) with N internal degrees of freedom:
-// the a with <(a.psi) psi> = d, solved in closed form.
+// Slope of a Maxwellian (U, V, W, lam; il = 1/(2 lam)) with N internal
+// degrees of freedom: the a with <(a.psi) psi> = d, solved in closed form.
+// c4 = 4/(N + 3).
 template <typename T>
-__device__ __forceinline__ void maxwell_slope(const T d[5], T U, T V, T W, T lam, T N, T a[5]) {
+__device__ __forceinline__ void maxwell_slope(const T d[5], T U, T V, T W, T lam, T il, T N,
+                                              T c4, T a[5]) {
     const T q2 = U * U + V * V + W * W;
-    const T K = (N + T(3)) / (T(2) * lam);
+    const T K = (N + T(3)) * il;
     const T R1 = d[1] - U * d[0], R2 = d[2] - V * d[0], R3 = d[3] - W * d[0];
     const T R4 = T(2) * d[4] - (q2 + K) * d[0];
-    a[4] = T(4) * lam * lam / (N + T(3)) * (R4 - T(2) * (U * R1 + V * R2 + W * R3));
+    a[4] = c4 * lam * lam * (R4 - T(2) * (U * R1 + V * R2 + W * R3));
     a[1] = T(2) * lam * R1 - U * a[4];
     a[2] = T(2) * lam * R2 - V * a[4];
     a[3] = T(2) * lam * R3 - W * a[4];
@@ -274,10 +276,11 @@ __device__ __forceinline__ Prim to_prim(const double *s, double gamma) {
 // state over u < 0) to W0's slopes and to terms 4-6 of Eq. flux.
 // ds: the 15 derivatives d/dn, d/dt1, d/dt2 of the 5 conserved variables.
 template <int SGN, typename T>
-__device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, T uh0, T uh1,
+__device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, T c4, T uh0, T uh1,
                                            T U0, T V0, T W0, T dW0[3][5], T X4[5], T X5[5],
                                            T X6[5], T q[3], T dtW[5]) {
-    const T inv2l = T(0.5) / S.lam;
+    const T ir = T(1) / S.rho;
+    const T inv2l = S.p * ir;  // 1/(2 lam)
     T uf[kNU], uh[kNU], v[kNV], w[kNV];
     full_line<kNU>(S.U, inv2l, uf);
     half_line<kNU>(S.U, inv2l, uh0, uh1, uh);
@@ -286,13 +289,12 @@ __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, 
     const T x2 = N * inv2l, x4 = (N * N + T(2) * N) * inv2l * inv2l;
     // one-sided Maxwellian slopes a_j
     T a[3][5];
-    const T ir = T(1) / S.rho;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         T d[5];
 #pragma unroll
         for (int i = 0; i < 5; ++i) d[i] = ds[5 * j + i] * ir;
-        maxwell_slope(d, S.U, S.V, S.W, S.lam, N, a[j]);
+        maxwell_slope(d, S.U, S.V, S.W, S.lam, inv2l, N, c4, a[j]);
     }
     // A from the compatibility condition: <(A.psi) psi> = -<(a.u) psi>
     T Tv[5] = {0, 0, 0, 0, 0}, A[5];
@@ -304,7 +306,7 @@ __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, 
             mT[i] = -Tv[i];
             dtW[i] = -S.rho * Tv[i];  // Euler time derivative of W_s
         }
-        maxwell_slope(mT, S.U, S.V, S.W, S.lam, N, A);
+        maxwell_slope(mT, S.U, S.V, S.W, S.lam, inv2l, N, c4, A);
     }
     // slopes of the interface equilibrium, collected from both sides
 #pragma unroll
@@ -337,22 +339,22 @@ __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, 
 // Equilibrium part: abar from the collided slopes dW0, Abar by
 // compatibility; X1..X3 (term 1 only if kTerm1), q1..q3, dW0/dt.
 template <bool kTerm1, typename T>
-__device__ __forceinline__ void equilibrium_terms(const PrimT<T> &Z, T N, const T dW0[3][5],
+__device__ __forceinline__ void equilibrium_terms(const PrimT<T> &Z, T N, T c4, const T dW0[3][5],
                                                   T X[6][5], T q[6], T dtW0[5]) {
-    const T inv2l = T(0.5) / Z.lam;
+    const T ir = T(1) / Z.rho;
+    const T inv2l = Z.p * ir;  // 1/(2 lam)
     T u[kNU], v[kNV], w[kNV];
     full_line<kNU>(Z.U, inv2l, u);
     full_line<kNV>(Z.V, inv2l, v);
     full_line<kNV>(Z.W, inv2l, w);
     const T x2 = N * inv2l, x4 = (N * N + T(2) * N) * inv2l * inv2l;
     T ab[3][5];
-    const T ir = T(1) / Z.rho;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         T d[5];
 #pragma unroll
         for (int i = 0; i < 5; ++i) d[i] = dW0[j][i] * ir;
-        maxwell_slope(d, Z.U, Z.V, Z.W, Z.lam, N, ab[j]);
+        maxwell_slope(d, Z.U, Z.V, Z.W, Z.lam, inv2l, N, c4, ab[j]);
     }
     T T0[5] = {0, 0, 0, 0, 0}, Ab[5];
     dir_acc<0>(ab, u, v, w, x2, x4, T(1), T0);
@@ -360,7 +362,7 @@ __device__ __forceinline__ void equilibrium_terms(const PrimT<T> &Z, T N, const 
         T mT[5];
 #pragma unroll
         for (int i = 0; i < 5; ++i) mT[i] = -T0[i];
-        maxwell_slope(mT, Z.U, Z.V, Z.W, Z.lam, N, Ab);
+        maxwell_slope(mT, Z.U, Z.V, Z.W, Z.lam, inv2l, N, c4, Ab);
     }
     T Y[5];
     if (kTerm1) {
@@ -394,7 +396,7 @@ __device__ __forceinline__ void interface_state(const Prim &L, const Prim &R, do
     half_start(L.U, L.lam, 1.0, ul0, ul1);
     half_start(R.U, R.lam, -1.0, ur0, ur1);
     double u[4], v[3], w[3], o[5];
-    const double il = 0.5 / L.lam, ir = 0.5 / R.lam;
+    const double il = L.p * (1.0 / L.rho), ir = R.p * (1.0 / R.rho);  // 1/(2 lam)
     half_line<4>(L.U, il, ul0, ul1, u);
     full_line<3>(L.V, il, v);
     full_line<3>(L.W, il, w);
@@ -478,9 +480,10 @@ __device__ void flux_point(const PhysParams &P, const double *sl, const double *
     for (int k = 0; k < 6; ++k)
 #pragma unroll
         for (int i = 0; i < 5; ++i) X[k][i] = 0.0;
-    side_terms<1>(sl + 5, L, N, ul0, ul1, Z.U, Z.V, Z.W, dW0, X[3], X[4], X[5], q + 3, dtWl);
-    side_terms<-1>(sr + 5, R, N, ur0, ur1, Z.U, Z.V, Z.W, dW0, X[3], X[4], X[5], q + 3, dtWr);
-    equilibrium_terms<true>(Z, N, dW0, X, q, dtW0);
+    const double c4 = 4.0 / (N + 3.0);
+    side_terms<1>(sl + 5, L, N, c4, ul0, ul1, Z.U, Z.V, Z.W, dW0, X[3], X[4], X[5], q + 3, dtWl);
+    side_terms<-1>(sr + 5, R, N, c4, ur0, ur1, Z.U, Z.V, Z.W, dW0, X[3], X[4], X[5], q + 3, dtWr);
+    equilibrium_terms<true>(Z, N, c4, dW0, X, q, dtW0);
     double dpr;
     combine_terms(P, L, R, Z, dt, X, q, out, dpr);
     if (kInterface) {
@@ -510,7 +513,7 @@ __device__ void flux_point(const PhysParams &P, const double *sl, const double *
 // products with moments FP32; the slopes and moments of terms 2, 3, 5, 6
 // are the FP32 core shared with the FP32 part of the previous design.
 struct PrimFF {
-    ff rho, U, V, W, p, lam;
+    ff rho, U, V, W, p, lam, il;  // il = 1/(2 lam) = p/rho
 };
 
 __device__ __forceinline__ ff ff_half(ff a) { return ff_make(0.5f * a.hi, 0.5f * a.lo); }
@@ -525,6 +528,7 @@ __device__ __forceinline__ PrimFF to_prim_ff(const ff s[5], ff gm1) {
     const ff q2 = ff_add(ff_add(ff_mul(P.U, P.U), ff_mul(P.V, P.V)), ff_mul(P.W, P.W));
     P.p = ff_mul(gm1, ff_sub(s[4], ff_half(ff_mul(P.rho, q2))));
     P.lam = ff_div(ff_half(P.rho), P.p);
+    P.il = ff_mul(P.p, ir);
     return P;
 }
 
@@ -596,7 +600,7 @@ __device__ __forceinline__ void half_side_ff(const PrimFF &S, int sgn, ff N, ff 
     half_start_ff(S, sgn, u[0], u[1]);
     m0f = u[0].hi;
     m1f = u[1].hi;
-    const ff inv2l = ff_half(ff_recip(S.lam));
+    const ff inv2l = S.il;
     u[2] = ff_add(ff_mul(S.U, u[1]), ff_mul(inv2l, u[0]));
     u[3] = ff_add(ff_mul(S.U, u[2]), ff_mul(ff_add(inv2l, inv2l), u[1]));
     // <v^2> + <w^2> + <xi^2> of the full lines
@@ -671,7 +675,7 @@ __device__ void flux_point_mixed(const PhysParams &P, const ff Ql[5], const floa
 
     // FP32 core: slopes and the moments of terms 2, 3, 5, 6 (and the heat
     // fluxes for the Prandtl fix)
-    const float Nf = N.hi;
+    const float Nf = N.hi, c4f = 4.0f / (Nf + 3.0f);
     const PrimT<float> Lf = prim_f(L), Rf = prim_f(R), Zf = prim_f(Z);
     float dW0[3][5], X[6][5], q[6] = {0, 0, 0, 0, 0, 0}, dtWl[5], dtWr[5], dtW0[5];
 #pragma unroll
@@ -691,7 +695,7 @@ __device__ void flux_point_mixed(const PhysParams &P, const ff Ql[5], const floa
 #pragma unroll
         for (int i = 0; i < 15; ++i) ds[i] = side ? dr[i] : dl[i];
         const PrimT<float> S = side ? Rf : Lf;
-        side_terms<1>(ds, S, Nf, side ? ur0 : ul0, side ? ur1 : ul1, Zf.U, Zf.V, Zf.W, dW0, X[3],
+        side_terms<1>(ds, S, Nf, c4f, side ? ur0 : ul0, side ? ur1 : ul1, Zf.U, Zf.V, Zf.W, dW0, X[3],
                       X[4], X[5], q + 3, dtW);
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
@@ -699,7 +703,7 @@ __device__ void flux_point_mixed(const PhysParams &P, const ff Ql[5], const floa
             else dtWl[i] = dtW[i];
         }
     }
-    equilibrium_terms<false>(Zf, Nf, dW0, X, q, dtW0);  // a Maxwellian carries no heat flux: q1 = 0
+    equilibrium_terms<false>(Zf, Nf, c4f, dW0, X, q, dtW0);  // a Maxwellian carries no heat flux: q1 = 0
 
     // collision time (Sec. 4) in FP32; time coefficients in FP32 for
     // dt >= 4 tau, else from the FP64 closed forms (dt >= tau/100) or series

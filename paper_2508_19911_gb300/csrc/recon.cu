@@ -365,7 +365,8 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
                 float tt = 0.0f;
                 static_for<kNumBasis>([&](auto J) {
                     constexpr int jj = decltype(J)::value;
-                    if constexpr (basis_class(ii) == basis_class(jj)) tt = fmaf(T[kTabH + ii * kPad + jj], a[jj], tt);
+                    if constexpr (jj >= ii && basis_class(ii) == basis_class(jj))
+                        tt = fmaf(T[kTabH + ii * kPad + jj], a[jj], tt);
                 });
                 ISH = fmaf(a[ii], tt, ISH);
             });
@@ -519,7 +520,10 @@ int upload_recon_tables(void) {
     for (int r = 0; r < kNumData; ++r)
         for (int j = 0; j < kMaxClass; ++j) tab[kTabRs + r * kPadS + j] = (float)t.Rs[r][j];
     for (int i = 0; i < kNumBasis; ++i) {
-        for (int j = 0; j < kNumBasis; ++j) tab[kTabH + i * kPad + j] = (float)t.H[i][j];
+        // IS_H from the upper triangle: H_ii and H_ij + H_ji (j > i)
+        for (int j = 0; j < kNumBasis; ++j)
+            tab[kTabH + i * kPad + j] =
+                j < i ? 0.0f : (float)(j == i ? t.H[i][i] : t.H[i][j] + t.H[j][i]);
         tab[kTabMean + i] = (float)t.mean[i];
         for (int d = 0; d < 3; ++d) {
             tab[kTabMval + d * kPad + i] = (float)t.mval[d][i];

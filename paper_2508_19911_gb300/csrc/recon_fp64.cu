@@ -205,7 +205,8 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
             double t = 0.0;
             static_for<kNumBasis>([&](auto J) {
                 constexpr int jj = decltype(J)::value;
-                if constexpr (basis_class(ii) == basis_class(jj)) t = fma(cH[ii][jj], a[jj], t);
+                if constexpr (jj >= ii && basis_class(ii) == basis_class(jj))
+                    t = fma(cH[ii][jj], a[jj], t);
             });
             ISH = fma(a[ii], t, ISH);
         });
@@ -311,7 +312,12 @@ __global__ void __launch_bounds__(128) recon5_ens_fp64_kernel(const EnsInst *__r
 int upload_recon_tables_fp64(const ReconTables &t) {
     if (cudaMemcpyToSymbol(cR, t.R, sizeof(t.R)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cRs, t.Rs, sizeof(t.Rs)) != cudaSuccess) return -2;
-    if (cudaMemcpyToSymbol(cH, t.H, sizeof(t.H)) != cudaSuccess) return -2;
+    // IS_H = a^T H a from the upper triangle: H_ii and H_ij + H_ji (j > i)
+    static double Hu[kNumBasis][kNumBasis];
+    for (int i = 0; i < kNumBasis; ++i)
+        for (int j = 0; j < kNumBasis; ++j)
+            Hu[i][j] = j < i ? 0.0 : (j == i ? t.H[i][i] : t.H[i][j] + t.H[j][i]);
+    if (cudaMemcpyToSymbol(cH, Hu, sizeof(Hu)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cMean, t.mean, sizeof(t.mean)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cMval, t.mval, sizeof(t.mval)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cMder, t.mder, sizeof(t.mder)) != cudaSuccess) return -2;

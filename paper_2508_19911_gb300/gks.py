@@ -66,6 +66,7 @@ SIGNATURES = {
     "gks_flux": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "gks_flux_points": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
     "gks_step": (_I, [_VP, _VP, _VP, _I, _D, _VP, ctypes.POINTER(_D)]),
+    "gks_step_host": (_I, [_VP, _VP, _VP, _I, _D, ctypes.POINTER(_D)]),
     "gks_diagnostics": (_I, [_VP, _VP, _VP, ctypes.POINTER(_D)]),
     "gks_status": (_I, [_VP, ctypes.POINTER(_I)]),
     "gks_recon_matrix": (_I, [ctypes.POINTER(_D)]),
@@ -276,6 +277,23 @@ class Solver:
                             ctypes.byref(last) if sync else None)
         _check(rc, "gks_step")
         return last.value if sync else None
+
+    def step_host(self, Q, G=None, nsteps=1, t_stop=math.inf, t=None):
+        """Advance a state held in host memory (contiguous float64 CPU
+        tensors, pinned for full copy speed) in place; the library copies
+        it to the device and back. t: None or a float (simulation time);
+        returns the new time."""
+        cg = self.cfg.scheme == "cgks5"
+        for x in (Q, G) if cg else (Q,):
+            if not (isinstance(x, self.torch.Tensor) and not x.is_cuda and
+                    x.dtype == self.torch.float64 and x.is_contiguous()):
+                raise TypeError("expected a contiguous float64 CPU tensor")
+        tt = _D(0.0 if t is None else float(t))
+        rc = lib().gks_step_host(self.ctx, ctypes.c_void_p(Q.data_ptr()),
+                                 ctypes.c_void_p(G.data_ptr()) if cg else None, int(nsteps),
+                                 float(t_stop), ctypes.byref(tt) if t is not None else None)
+        _check(rc, "gks_step_host")
+        return tt.value if t is not None else None
 
     def diagnostics(self, Q, G=None):
         out = (_D * 12)()

@@ -56,3 +56,4 @@ def test_init_rejects_bad_arguments_before_touching_the_gpu():
         assert rc == gks.GKS_ERR_ARG
         assert not ctx.value
     assert L.gks_step(None, None, None, 1, 0.0, None, None) == gks.GKS_ERR_ARG
+    assert L.gks_step_host(None, None, None, 1, 0.0, None) == gks.GKS_ERR_ARG

@@ -38,6 +38,7 @@ def solver(torch_dev, grid, **kw):
 def oparams(grid, **kw):
     m = {"cgks5": 1, "gks2": 0}
     kw = dict(kw)
+    kw.pop("precision", None)  # the oracle is FP64 only
     if "scheme" in kw:
         kw["scheme"] = m[kw["scheme"]]
     if "mu" in kw:
@@ -237,6 +238,52 @@ def test_linear_variant_and_ragged_grid_match_oracle(torch_dev, scheme):
     for nonlinear in (False, True):
         eq, eg, _ = run_parity(torch_dev, Q, G, grid, 3, scheme=scheme, nonlinear=nonlinear)
         assert eq < TOL and eg < TOL, (nonlinear, eq, eg)
+
+
+@pytest.mark.parametrize("n", [(1, 1, 1), (2, 3, 1), (3, 2, 2)])
+@pytest.mark.parametrize("scheme", ["gks2", "cgks5"])
+def test_grids_smaller_than_the_stencil_match_oracle(torch_dev, scheme, n):
+    """Periodic grids with fewer cells per axis than the stencil spans: the
+    face and edge neighbours alias onto the same cells (on 1 x 1 x 1 every
+    neighbour is the cell itself); nonlinear, 3 steps within 1e-11."""
+    Q, G, grid = wl.taylor_green(n)
+    Q, G = wl.perturb(Q, G, amp=0.03, seed=11)
+    eq, eg, s = run_parity(torch_dev, Q, G, grid, 3, scheme=scheme, nonlinear=True)
+    assert eq < TOL and eg < TOL, (eq, eg)
+    assert s.status() == 0
+    # the mixed-precision kernels on the same aliasing stencils: within the
+    # mixed path's stated bound (1e-5) of the FP64 oracle
+    eq, eg, s = run_parity(torch_dev, Q, G, grid, 3, scheme=scheme, nonlinear=True,
+                           precision="mixed")
+    assert eq < 1e-5 and eg < 1e-5, (eq, eg)
+    assert s.status() == 0
+
+
+@pytest.mark.parametrize("scheme", ["gks2", "cgks5"])
+def test_step_on_host_buffers_equals_device_step(torch_dev, scheme):
+    """gks_step_host (state in pinned host memory, copied by the library)
+    gives the bits of gks_step on device buffers, including the time
+    control (the last step clamped to t_stop, then no-op steps)."""
+    torch, dev = torch_dev
+    Q, G, grid = wl.taylor_green((12, 10, 8))
+    Q, G = wl.perturb(Q, G, amp=0.02, seed=8)
+    cg = scheme == "cgks5"
+    s = solver(torch_dev, grid, scheme=scheme)
+    Qd = torch.tensor(Q, device=dev)
+    Gd = torch.tensor(G, device=dev) if cg else None
+    t = torch.zeros(1, dtype=torch.float64, device=dev)
+    dt0 = s.compute_dt(Qd).item()
+    t_stop = 2.5 * dt0
+    s.step(Qd, Gd, nsteps=4, t_stop=t_stop, t=t)
+    s2 = solver(torch_dev, grid, scheme=scheme)
+    Qp = torch.tensor(Q).pin_memory()
+    Gp = torch.tensor(G).pin_memory() if cg else None
+    th = s2.step_host(Qp, Gp, nsteps=4, t_stop=t_stop, t=0.0)
+    assert th == t.item() and abs(th - t_stop) <= 1e-15 * t_stop
+    assert np.array_equal(Qp.numpy(), Qd.cpu().numpy())
+    if cg:
+        assert np.array_equal(Gp.numpy(), Gd.cpu().numpy())
+    s2.close()
 
 
 @pytest.mark.parametrize("scheme", ["gks2", "cgks5"])
