@@ -19,7 +19,8 @@
  *       in-plane (o_a e_a - o_b e_b)/sqrt(2) and the edge direction (with
  *       only the two displaced axes the quartic's xyz-type terms are left
  *       undetermined: the 19-cell data then has rank 30 of 34);
- *   R3  LS scaling h1 = h2 = h3 = h (unit weight in normalised coordinates);
+ *   R3  LS scaling h1 = h3 = h, h2 = 0.1 h (edge rows), near the minimum of
+ *       the weighted system's condition number;
  *   R4  sub-stencil P1_m: normal slope from Q_{1,m}-Q_0, tangential slopes
  *       from the target cell's own gradient;
  *   R5  IS_m = |b^m|^2, IS_H = sum_{1<=|a|<=4} int (D^a P4)^2 over the unit

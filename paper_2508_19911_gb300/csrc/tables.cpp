@@ -126,6 +126,18 @@ int build_recon_tables(ReconTables *t) {
     }
     for (int q = 0; q < 3; ++q, ++r)
         for (int i = 0; i < nb; ++i) B(r, i) = cell_avg_deriv(zero, i, q);
+    // row weights (the h_1, h_2, h_3 of Eq. compact-big-5, relative to the
+    // cell size that already scales the derivative data): 1 for the face
+    // neighbours' gradients and the own gradient, kEdgeWeight for the edge
+    // neighbours' tangential derivatives -- near the minimum of the
+    // condition number of the weighted least-squares system on the
+    // constraints' null space (5.07; 29.6 with unit weights, which also
+    // leaves the linear scheme with a growing grid-scale vortical mode)
+    constexpr double kEdgeWeight = 0.1;
+    std::vector<double> wrow(nl, 1.0);
+    for (int k = 18; k < 42; ++k) wrow[k] = kEdgeWeight;
+    for (int k = 0; k < nl; ++k)
+        for (int i = 0; i < nb; ++i) B(k, i) *= wrow[k];
 
     // null-space method
     Mat Ct(nb, ne);
@@ -157,7 +169,7 @@ int build_recon_tables(ReconTables *t) {
     std::vector<double> dC(ne), dB(nl), y(ne), res(nl), z(nz), rhs(nz);
     for (int col = 0; col < kNumData; ++col) {
         for (int k = 0; k < ne; ++k) dC[k] = (col == k) ? 1.0 : 0.0;
-        for (int k = 0; k < nl; ++k) dB[k] = (col == ne + k) ? 1.0 : 0.0;
+        for (int k = 0; k < nl; ++k) dB[k] = (col == ne + k) ? wrow[k] : 0.0;
         // R_c^T y = d_C (forward substitution)
         for (int i = 0; i < ne; ++i) {
             double s = dC[i];
