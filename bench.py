@@ -43,11 +43,11 @@ HBM_FALLBACK_GBS = 6800.0
 # for a reconstruction, one face Gauss point for a flux kernel (12 per cell
 # for CGKS-5th: 3 faces x 4 points; 3 per cell for GKS-2nd).
 KERNEL_OPS = {
-    "recon5": {"fp64": 14879.0, "fp32": 130.0, "bytes": 160 + 3840, "dram": 3772.7},
-    "flux_cgks5": {"fp64": 5223.5, "fp32": 34.0, "bytes": (3840 + 720) / 12, "dram": 379.2},
-    "recon5_mixed": {"fp64": 0.0, "fp32": 14001.5, "bytes": 40 + 60 + 1920, "dram": 1789.5},
-    "flux_cgks5_mixed": {"fp64": 21.5, "fp32": 9124.1, "bytes": (1920 + 40 + 720) / 12,
-                         "dram": 224.1},
+    "recon5": {"fp64": 14159.0, "fp32": 130.0, "bytes": 160 + 3840, "dram": 3771.7},
+    "flux_cgks5": {"fp64": 5087.0, "fp32": 14.0, "bytes": (3840 + 720) / 12, "dram": 386.9},
+    "recon5_mixed": {"fp64": 0.0, "fp32": 13281.5, "bytes": 40 + 60 + 1920, "dram": 1791.5},
+    "flux_cgks5_mixed": {"fp64": 21.5, "fp32": 8938.1, "bytes": (1920 + 40 + 720) / 12,
+                         "dram": 225.5},
 }
 KERNEL_OPS["recon5_learned"] = KERNEL_OPS["recon5_mixed"]
 KERNEL_OPS["flux_cgks5_learned"] = KERNEL_OPS["flux_cgks5_mixed"]
