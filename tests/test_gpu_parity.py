@@ -286,6 +286,29 @@ def test_step_on_host_buffers_equals_device_step(torch_dev, scheme):
     s2.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_linear_cgks_taylor_green_energy_decays(torch_dev, precision):
+    """The linear CGKS-5th (the paper's choice for the subsonic vortex,
+    Sec. 4.1) over 1500 steps of the Taylor-Green vortex at 32^3 (t ~ 8):
+    the kinetic energy never rises by more than 1e-6 of itself between
+    samples 100 steps apart (viscous decay; the weakly compressible flow
+    moves a little energy back and forth). With unit least-squares weights
+    in Eq. compact-big-5 a grid-scale mode grew after ~1000 steps and the
+    energy rose to many times its initial value."""
+    torch, dev = torch_dev
+    Q, G, grid = wl.taylor_green(32)
+    s = solver(torch_dev, grid, scheme="cgks5", nonlinear=False, precision=precision)
+    Qd, Gd = torch.tensor(Q, device=dev), torch.tensor(G, device=dev)
+    ek = [s.diagnostics(Qd, Gd)[0]]
+    for _ in range(15):
+        s.step(Qd, Gd, nsteps=100)
+        ek.append(s.diagnostics(Qd, Gd)[0])
+    ek = np.array(ek)
+    assert np.all(ek[1:] <= ek[:-1] * (1 + 1e-6)), ek
+    assert ek[-1] < 0.9 * ek[0], ek
+    s.close()
+
+
 @pytest.mark.parametrize("scheme", ["gks2", "cgks5"])
 def test_sod_tube_matches_oracle(torch_dev, scheme):
     """Quasi-1D grid (ny = nz = 1), discontinuous data, inviscid collision
