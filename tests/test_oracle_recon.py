@@ -228,3 +228,90 @@ def test_gks2_reconstruction(orc):
     out, phi = orc.recon2_cell(q7.ravel(), (0.1, 0.1, 0.1), nonlinear=1)
     assert np.all(phi < 0.01)
     assert out[:, 0].max() <= 3.0 and out[:, 0].min() >= 0.99
+
+
+# ---- the least-squares matrix of Eq. compact-big-5, from its definition ----
+BASIS5 = [(i, j, d - i - j) for d in range(1, 5) for i in range(d, -1, -1)
+          for j in range(d - i, -1, -1)]  # monomials by degree, x exponent first
+
+
+def _mean1(o, n):
+    """mean of t^n over [o - 1/2, o + 1/2]"""
+    return ((o + 0.5) ** (n + 1) - (o - 0.5) ** (n + 1)) / (n + 1)
+
+
+def _mean_mono(o, e):
+    if min(e) < 0:
+        return 0.0
+    return (_mean1(o[0], e[0]) * _mean1(o[1], e[1]) * _mean1(o[2], e[2]) /
+            (math.factorial(e[0]) * math.factorial(e[1]) * math.factorial(e[2])))
+
+
+def _ls_rows(w_edge):
+    """Constraint rows C (neighbour averages of the zero-mean basis) and the
+    weighted derivative rows W B (face neighbours' gradients, the edge
+    neighbours' two tangential derivatives, the own gradient), in the data
+    order of the C-ABI's gks_recon_matrix."""
+    def dmean(o, e, j):
+        e2 = list(e)
+        e2[j] -= 1
+        return _mean_mono(o, e2)
+    C = np.array([[_mean_mono(o, e) - _mean_mono((0, 0, 0), e) for e in BASIS5]
+                  for o in FACE + EDGE])
+    rows, w = [], []
+    for o in FACE:
+        for j in range(3):
+            rows.append([dmean(o, e, j) for e in BASIS5])
+            w.append(1.0)
+    for o in EDGE:
+        a, b = [j for j in range(3) if o[j]]
+        ez = [j for j in range(3) if not o[j]][0]
+        rows.append([(o[a] * dmean(o, e, a) - o[b] * dmean(o, e, b)) / math.sqrt(2)
+                     for e in BASIS5])
+        rows.append([dmean(o, e, ez) for e in BASIS5])
+        w += [w_edge, w_edge]
+    for j in range(3):
+        rows.append([dmean((0, 0, 0), e, j) for e in BASIS5])
+        w.append(1.0)
+    return C, np.array(w)[:, None] * np.array(rows), np.array(w)
+
+
+def test_recon_matrix_is_the_weighted_constrained_least_squares_solution(orc):
+    """Eq. compact-big-5 with the row weights h1 = h3 = 1, h2 = 0.1 (edge
+    tangential derivatives): for each data column, the quartic whose
+    neighbour averages match exactly and whose weighted derivative residual
+    is least. Solved here through its KKT system, independently of the
+    oracle's elimination; a wrong weight, sign or row order fails."""
+    C, WB, w = _ls_rows(0.1)
+    n, m = 34, 18
+    K = np.zeros((n + m, n + m))
+    K[:n, :n] = WB.T @ WB
+    K[:n, n:] = C.T
+    K[n:, :n] = C
+    R = np.zeros((34, 63))
+    for col in range(63):
+        rhs = np.zeros(n + m)
+        if col < 18:
+            rhs[n + col] = 1.0
+        else:
+            rhs[:n] = WB.T[:, col - 18] * w[col - 18]
+        R[:, col] = np.linalg.solve(K, rhs)[:n]
+    got = orc.recon5_matrix()
+    assert np.abs(got - R).max() <= 1e-10 * np.abs(R).max(), np.abs(got - R).max()
+
+
+def test_edge_weight_is_near_the_condition_number_minimum():
+    """The reading of h2: the edge rows' weight 0.1 lies within 1% of the
+    smallest 2-norm condition number of the weighted least-squares system
+    on the null space of the exact constraints (weights of the other rows
+    1), which unit weights exceed by more than 5x."""
+    def cond(we):
+        C, WB, _ = _ls_rows(we)
+        _, s, vt = np.linalg.svd(C)
+        Z = vt[np.sum(s > 1e-12):].T
+        sv = np.linalg.svd(WB @ Z, compute_uv=False)
+        return sv[0] / sv[-1]
+    grid = np.linspace(0.02, 1.0, 99)
+    best = min(cond(x) for x in grid)
+    assert cond(0.1) <= 1.01 * best, (cond(0.1), best)
+    assert cond(1.0) > 5 * cond(0.1)
