@@ -245,6 +245,39 @@ def trained_indicator(torch, dev):
     return params.cpu().numpy(), info
 
 
+def _dist_ready():
+    import torch.distributed as dist
+    return dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+
+
+def barrier_ranks():
+    """Barrier over the ranks (no-op in a single process)."""
+    if _dist_ready():
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(torch, x):
+    """The largest value of a host float over the ranks: the slowest rank
+    sets a replica run's time (NCCL: reduced on this rank's GPU; gloo: on
+    the host)."""
+    if not _dist_ready():
+        return float(x)
+    import torch.distributed as dist
+    dev = (torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl"
+           else torch.device("cpu"))
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, cells, stages, steps, ms):
+    """Whole-job cell-stage updates per second of `world` independent
+    replicas, each advancing `cells` cells `steps` steps, timed by the
+    slowest rank (ms)."""
+    return world * cells * stages * steps / (ms / 1e3)
+
+
 def time_steps(torch, solver, Q, G, steps, stream):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -311,18 +344,14 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         solver.step(Q, G, nsteps=1, sync=False)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier_ranks()
     with ClockSampler(local_rank) as clk:
         ms = time_steps(torch, solver, Q, G, args.steps, stream)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(torch, ms)
     st = solver.status()
     if st:
         raise RuntimeError(f"non-physical state during the benchmark (status {st})")
-    value = world * cells * stages * args.steps / (ms / 1e3)
+    value = replica_throughput(world, cells, stages, args.steps, ms)
     if args.indicator:
         ind_info["skip_fraction"] = solver.indicator_skips() / (
             5 * cells * stages * (args.steps + args.warmup))
@@ -395,6 +424,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_steps = max(1, min(args.steps, 3))
         solver.step_host(Qp, Gp, nsteps=1)  # first call allocates the device copy
         torch.cuda.synchronize()
+        barrier_ranks()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -402,9 +432,9 @@ def run_ours(args, rank, world, local_rank):
             solver.step_host(Qp, Gp, nsteps=1)
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        e2e_ms = max_over_ranks(torch, e0.elapsed_time(e1) / e2e_steps)
         state_bytes = Qh.nbytes + (Gh.nbytes if cg else 0)
-        e2e = {"value": world * cells * stages / (e2e_ms / 1e3), "unit": "cell-stage/s",
+        e2e = {"value": replica_throughput(world, cells, stages, 1, e2e_ms), "unit": "cell-stage/s",
                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
                "ms_per_step": e2e_ms}
 
