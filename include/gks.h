@@ -202,6 +202,9 @@ int gks_status(gks_ctx *ctx, int *status);
 
 /* Host-only, no GPU needed: the CGKS-5th reconstruction matrix R (34 x 63,
  * row major) with a = R d, the least-squares solution of Eq. compact-big-5
+ * (neighbour averages exact; derivative rows weighted 1, except the edge
+ * neighbours' tangential derivatives, weighted 0.1 -- the paper's h2,
+ * chosen near the minimum of the system's condition number)
  * for the normalised data vector d of S^data-5th (column order: the 6
  * face-neighbour differences, the 12 edge-neighbour differences, the 18
  * scaled face-neighbour gradients, the 24 scaled edge-neighbour tangential
