@@ -85,7 +85,8 @@ void gks_default_options(gks_options *opt);
 /* Create a context for one grid (Sec. 4 problem statement: gamma, Pr, mu,
  * grid and CFL).
  *   gamma > 1, Pr > 0, mu >= 0 (mu0 of the Sutherland law when mu_law = 1),
- *   0 < cfl <= 1, nx, ny, nz >= 1, Lx, Ly, Lz > 0 (periodic box).
+ *   0 < cfl <= 1, nx, ny, nz >= 1 with nx ny nz <= 2^31 cells, Lx, Ly,
+ *   Lz > 0 (periodic box).
  *   opt        : NULL for gks_default_options.
  *   cuda_stream: a cudaStream_t (or NULL); the context enqueues all of its
  *                work there.

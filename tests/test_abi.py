@@ -51,7 +51,8 @@ def test_init_rejects_bad_arguments_before_touching_the_gpu():
     o = gks.Options()
     L.gks_default_options(ctypes.byref(o))
     for args in [(1.0, 0.72, 1e-3, 0.3, 8, 8, 8), (1.4, 0.72, 1e-3, 0.0, 8, 8, 8),
-                 (1.4, 0.72, -1.0, 0.3, 8, 8, 8), (1.4, 0.72, 1e-3, 0.3, 0, 8, 8)]:
+                 (1.4, 0.72, -1.0, 0.3, 8, 8, 8), (1.4, 0.72, 1e-3, 0.3, 0, 8, 8),
+                 (1.4, 0.72, 1e-3, 0.3, 2048, 2048, 1024)]:  # 2^32 cells: above the 2^31 limit
         rc = L.gks_init(ctypes.byref(ctx), *args, 1.0, 1.0, 1.0, ctypes.byref(o), None)
         assert rc == gks.GKS_ERR_ARG
         assert not ctx.value
