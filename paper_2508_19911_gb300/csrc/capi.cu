@@ -331,12 +331,15 @@ int gks_step(gks_ctx *c, double *Q, double *G, int nsteps, double t_stop, double
     }
     if (dt_host_last) {
         int st = 0;
+        // an enqueued copy into st must finish before st goes out of scope
         if (cudaMemcpyAsync(dt_host_last, dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
                 cudaSuccess ||
             cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(c->stream) != cudaSuccess)
+                cudaSuccess) {
+            cudaStreamSynchronize(c->stream);
             return GKS_ERR_CUDA;
+        }
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return GKS_ERR_CUDA;
         if (st) return GKS_ERR_NONPHYSICAL;
     }
     return GKS_OK;
@@ -359,15 +362,22 @@ int gks_step_host(gks_ctx *c, double *Q, double *G, int nsteps, double t_stop, d
         }
     }
     const size_t qb = qn * sizeof(double);
+    // on any failure after a copy was enqueued, wait for the stream before
+    // returning: the copies read and write the caller's host buffers
     if (cudaMemcpyAsync(c->hQ, Q, qb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
         (cgks && cudaMemcpyAsync(c->hG, G, 3 * qb, cudaMemcpyHostToDevice, c->stream) !=
                      cudaSuccess) ||
         (t && cudaMemcpyAsync(c->hT, t, sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
-                  cudaSuccess))
+                  cudaSuccess)) {
+        cudaStreamSynchronize(c->stream);
         return GKS_ERR_CUDA;
+    }
     const int rc = gks_step(c, c->hQ, cgks ? c->hG : nullptr, nsteps, t_stop, t ? c->hT : nullptr,
                             nullptr);
-    if (rc) return rc;
+    if (rc) {
+        cudaStreamSynchronize(c->stream);
+        return rc;
+    }
     int st = 0;
     if (cudaMemcpyAsync(Q, c->hQ, qb, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         (cgks && cudaMemcpyAsync(G, c->hG, 3 * qb, cudaMemcpyDeviceToHost, c->stream) !=
@@ -375,9 +385,11 @@ int gks_step_host(gks_ctx *c, double *Q, double *G, int nsteps, double t_stop, d
         (t && cudaMemcpyAsync(t, c->hT, sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
                   cudaSuccess) ||
         cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
+            cudaSuccess) {
+        cudaStreamSynchronize(c->stream);
         return GKS_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return GKS_ERR_CUDA;
     return st ? GKS_ERR_NONPHYSICAL : GKS_OK;
 }
 
@@ -390,9 +402,11 @@ int gks_diagnostics(gks_ctx *c, const double *Q, const double *G, double *out) {
     if (cudaMemcpyAsync(out, od, 12 * sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
             cudaSuccess ||
         cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
+            cudaSuccess) {
+        cudaStreamSynchronize(c->stream);
         return GKS_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return GKS_ERR_CUDA;
     return st ? GKS_ERR_NONPHYSICAL : GKS_OK;
 }
 
@@ -408,10 +422,11 @@ int gks_indicator_skips(gks_ctx *c, unsigned long long *count) {
     if (!c || !count) return GKS_ERR_ARG;
     if (cudaMemcpyAsync(count, c->skips, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                         c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->skips, 0, sizeof(unsigned long long), c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        cudaMemsetAsync(c->skips, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
+        cudaStreamSynchronize(c->stream);  // no copy into *count left in flight
         return GKS_ERR_CUDA;
-    return GKS_OK;
+    }
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? GKS_OK : GKS_ERR_CUDA;
 }
 
 int gks_indicator_dump(gks_ctx *c, const double *Q, const double *G, float label_eps, float *x,
@@ -444,10 +459,11 @@ int gks_status(gks_ctx *c, int *status) {
     if (cudaMemcpyAsync(status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
             cudaSuccess ||
         cudaMemsetAsync(c->status, 0, sizeof(int), c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->skips, 0, sizeof(unsigned long long), c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        cudaMemsetAsync(c->skips, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
+        cudaStreamSynchronize(c->stream);  // no copy into *status left in flight
         return GKS_ERR_CUDA;
-    return GKS_OK;
+    }
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? GKS_OK : GKS_ERR_CUDA;
 }
 
 }  // extern "C"
