@@ -271,6 +271,16 @@ def max_over_ranks(torch, x):
     return float(t.item())
 
 
+def kinetic_energy(Q):
+    """per-cell rho |U|^2 / 2 of a state [5][...] (device tensor)"""
+    return 0.5 * (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0]
+
+
+def rel_l2(a, b):
+    import torch
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
 def replica_throughput(world, cells, stages, steps, ms):
     """Whole-job cell-stage updates per second of `world` independent
     replicas, each advancing `cells` cells `steps` steps, timed by the
@@ -348,6 +358,11 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         ms = time_steps(torch, solver, Q, G, args.steps, stream)
     ms = max_over_ranks(torch, ms)
+    # per-cell kinetic energy after the warm-up and timed steps: the FP64
+    # reference for the mixed variants' error (same initial state and steps)
+    ke_ref = {}
+    if prec == "fp64" and not args.indicator:
+        ke_ref[scheme] = kinetic_energy(Q)
     st = solver.status()
     if st:
         raise RuntimeError(f"non-physical state during the benchmark (status {st})")
@@ -455,22 +470,33 @@ def run_ours(args, rank, world, local_rank):
                     s2.set_indicator(params, theta=ind_info["theta"])
                 Q2 = torch.tensor(Qh, device=dev)
                 G2 = torch.tensor(Gh, device=dev) if other == "cgks5" else None
-                for _ in range(2):
+                # the main run's warm-up and timed step counts, so that the
+                # final state is comparable with the FP64 one
+                w2, k2 = args.warmup, args.steps
+                for _ in range(w2):
                     s2.step(Q2, G2, nsteps=1, sync=False)
-                k2 = max(2, args.steps)
                 ms2 = time_steps(torch, s2, Q2, G2, k2, stream)
                 st2 = 2 if other == "cgks5" else 1
+                ke2 = kinetic_energy(Q2)
                 fs2 = s2.reconstruct(Q2, G2)
                 d2 = s2.compute_dt(Q2)
                 tr = time_kernel(torch, lambda: s2.reconstruct(Q2, G2, out=fs2), 2, stream)
                 fr2 = s2.flux(fs2, d2, Q=Q2)
                 tf = time_kernel(torch, lambda: s2.flux(fs2, d2, out=fr2, Q=Q2), 2, stream)
-                variants[f"{other}_{oprec}_{n}^3"] = {
+                vk = f"{other}_{oprec}_{n}^3"
+                variants[vk] = {
                     "value": cells * st2 * k2 / (ms2 / 1e3), "unit": "cell-stage/s",
                     "ms_per_step": ms2 / k2, "recon_ms": tr, "flux_ms": tf}
+                if oprec == "fp64":
+                    ke_ref[other] = ke2
+                elif other in ke_ref:
+                    # the stated error: per-cell KE against FP64 after the same steps
+                    variants[vk]["ke_rel_l2_vs_fp64"] = rel_l2(ke2, ke_ref[other])
+                    variants[vk]["ke_steps"] = w2 + k2
                 if oprec == "learned":
-                    variants[f"{other}_{oprec}_{n}^3"]["skip_fraction"] = s2.indicator_skips() / (
-                        5 * cells * st2 * (k2 + 2) + 5 * cells * 3)
+                    variants[vk]["skip_fraction"] = s2.indicator_skips() / (
+                        5 * cells * st2 * (w2 + k2) + 5 * cells * 3)
+                del ke2
                 s2.close()
                 del Q2, G2, fs2, fr2
                 torch.cuda.empty_cache()
