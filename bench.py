@@ -92,7 +92,9 @@ def parse():
                          "and mixed on one grid (default 64^3)")
     ap.add_argument("--t-end", type=float, default=10.0, help="--c2: final time (U0 = L = 1)")
     ap.add_argument("--every", type=float, default=0.1, help="--c2: sampling interval")
-    ap.add_argument("--precisions", default="fp64,mixed", help="--c2: paths to run")
+    ap.add_argument("--precisions", default="fp64,mixed",
+                    help="--c2: paths to run (fp64, mixed, fp64p: FP64 from the initial "
+                         "state perturbed by 1e-14 relative, the FP64 path's own sensitivity)")
     ap.add_argument("--linear", action="store_true",
                     help="--c2: the linear scheme (chi = 1 / no limiter), as the paper runs the "
                          "subsonic Taylor-Green vortex")
@@ -647,9 +649,14 @@ def run_c2(args):
     times = [args.every * j for j in range(nsamp + 1)]
     hist, paths, kes = {"times": times}, {}, {}
     for prec in args.precisions.split(","):
-        s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=scheme, precision=prec,
+        s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=scheme,
+                                  precision="fp64" if prec == "fp64p" else prec,
                                   nonlinear=not args.linear), stream)
-        Q = torch.tensor(Qh, device=dev)
+        Q0 = Qh
+        if prec == "fp64p":
+            rng = np.random.default_rng(2024)
+            Q0 = Qh * (1.0 + 1e-14 * rng.uniform(-1.0, 1.0, Qh.shape))
+        Q = torch.tensor(Q0, device=dev)
         G = torch.tensor(Gh, device=dev) if cg else None
         t = torch.zeros(1, dtype=torch.float64, device=dev)
         diag = [s.diagnostics(Q, G)]
