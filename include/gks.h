@@ -156,7 +156,9 @@ int gks_flux(gks_ctx *ctx, const double *Q, const void *face_states,
 
 /* The same flux (FP64 arithmetic) at n independent Gauss points:
  * s_l, s_r device double[20][n] face-frame states (layout of one Gauss point
- * of gks_reconstruct), out device double[30][n] in the face frame. */
+ * of gks_reconstruct), out device double[30][n] in the face frame.
+ * n = 0: returns GKS_OK without reading or writing (the pointers may then
+ * be NULL). */
 int gks_flux_points(gks_ctx *ctx, const double *s_l, const double *s_r,
                     int n, const double *dt_dev, double *out);
 

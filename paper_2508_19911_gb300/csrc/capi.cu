@@ -300,8 +300,9 @@ int gks_flux(gks_ctx *c, const double *Q, const void *face_states, const double 
 
 int gks_flux_points(gks_ctx *c, const double *s_l, const double *s_r, int n,
                     const double *dt_dev, double *out) {
-    if (!c || !s_l || !s_r || !dt_dev || !out || n < 0) return GKS_ERR_ARG;
-    if (n == 0) return GKS_OK;
+    if (!c || n < 0) return GKS_ERR_ARG;
+    if (n == 0) return GKS_OK;  // no points: nothing is read or written
+    if (!s_l || !s_r || !dt_dev || !out) return GKS_ERR_ARG;
     return launch_ok(launch_flux_points(c->P, s_l, s_r, n, dt_dev, out, c->status, c->stream));
 }
 

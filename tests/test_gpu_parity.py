@@ -152,6 +152,19 @@ def run_parity(torch_dev, Q, G, grid, steps, **kw):
     return eq, eg, s
 
 
+def test_flux_points_empty_input(torch_dev):
+    """No Gauss points: the call succeeds without work (empty tensors,
+    whose data pointers may be null)."""
+    torch, dev = torch_dev
+    Q, G, grid = wl.taylor_green(4)
+    s = solver(torch_dev, grid, scheme="cgks5")
+    empty = torch.zeros(20, 0, dtype=torch.float64, device=dev)
+    dt = torch.full((1,), 1e-3, dtype=torch.float64, device=dev)
+    out = s.flux_points(empty, empty.clone(), dt)
+    assert out.shape == (30, 0)
+    assert s.status() == 0
+
+
 @pytest.mark.parametrize("scheme", ["gks2", "cgks5"])
 def test_face_states_match_oracle(torch_dev, scheme):
     torch, dev = torch_dev
