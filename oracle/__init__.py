@@ -87,7 +87,8 @@ def lib():
                 "orc_flux_gp": [_P, _D, _D, ctypes.c_double, _D],
                 "orc_fbar": [_P, _D, _D, ctypes.c_double, ctypes.c_double, _D],
                 "orc_recon5_matrix": [_D],
-                "orc_is_matrix": [_D],
+                "orc_geno_misfit": [_D, _D, _D],
+                "orc_chi_field": [_P, _D, _D, _D],
                 "orc_recon5_cell": [_D, _D, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, _D, _D],
                 "orc_recon2_cell": [_D, ctypes.c_double, ctypes.c_double,
@@ -159,10 +160,20 @@ def recon5_matrix():
     return R
 
 
-def is_matrix():
-    H = np.zeros((34, 34))
-    _check(lib().orc_is_matrix(_ptr(H)), "is_matrix")
-    return H
+def geno_misfit(q0, dvec):
+    """GENO's misfit sigma (reading R5) of one cell's five variables."""
+    out = np.zeros(5)
+    _check(lib().orc_geno_misfit(_ptr(np.ascontiguousarray(q0, float)),
+                                 _ptr(np.ascontiguousarray(dvec, float)), _ptr(out)), "geno_misfit")
+    return out
+
+
+def chi_field(P, Q, G):
+    """GENO's chi of every (variable, cell) of a CGKS-5th state: [5][cells]."""
+    n = P.nx * P.ny * P.nz
+    chi = np.zeros((5, n))
+    _check(lib().orc_chi_field(ctypes.byref(P), _ptr(Q), _ptr(G), _ptr(chi)), "chi_field")
+    return chi
 
 
 def recon5_cell(q0, dvec, h=(1.0, 1.0, 1.0), nonlinear=1):

@@ -23,9 +23,12 @@
  *       the weighted system's condition number;
  *   R4  sub-stencil P1_m: normal slope from Q_{1,m}-Q_0, tangential slopes
  *       from the target cell's own gradient;
- *   R5  IS_m = |b^m|^2, IS_H = sum_{1<=|a|<=4} int (D^a P4)^2 over the unit
- *       cell, chi = 1/(1+(r/0.1)^3), r = |IS_H-IS_L|/(IS_H+IS_L+eps),
- *       IS_L = sum_m w_m IS_m; component-wise;
+ *   R5  chi from the weighted least-squares misfit of P4 (what the quartic
+ *       of Eq. compact-big-5 cannot meet of the derivative data), relative
+ *       to the data's norm plus (0.01 S)^2, S the cell's own magnitude:
+ *       chi = 1/(1 + s + s^2), s = sigma/5e-4; IS_m = |b^m|^2 in the ENO
+ *       weights;
+ *       component-wise on the conserved variables;
  *   R6  slopes of the interface equilibrium g0 by the same kinetic collision
  *       as W0 applied to the one-sided Maxwellian slopes;
  *   R7  Prandtl correction F_E += (1/Pr-1) q with q the heat flux of the
@@ -83,7 +86,10 @@ int orc_fbar(const orc_params *P, const double *s_l, const double *s_r,
 
 /* --- Reconstruction (Sec. 3.2, 3.3) ----------------------------------- */
 int orc_recon5_matrix(double *R34x63);
-int orc_is_matrix(double *H34x34);
+/* GENO's misfit sigma of reading R5 for the five variables of one cell
+ * (q0[5], dvec[5*63] as for orc_recon5_cell): chi = 1/(1 + s + s^2) with
+ * s = sigma/5e-4. */
+int orc_geno_misfit(const double *q0, const double *dvec, double *sigma5);
 /* CGKS-5th reconstruction of one cell from its data vectors.
  * q0[5], dvec[5*63] (per variable: see recon.cpp), out[6*4*20]:
  * per face f (x-,x+,y-,y+,z-,z+), per Gauss point k, the 20 face-frame
@@ -106,6 +112,8 @@ int orc_run(const orc_params *P, double *Q, double *G, int nsteps,
  * L, Lt [5][cells]; face records [3][30][cells] (see scheme.cpp).        */
 int orc_stage(const orc_params *P, const double *Q, const double *G,
               double dt, double *L, double *Lt, double *faces);
+/* GENO's chi of every (variable, cell) of a CGKS-5th state: chi[5][cells]. */
+int orc_chi_field(const orc_params *P, const double *Q, const double *G, double *chi);
 /* Reconstructed face states of all cells: [6][4][20][cells] (CGKS-5th) or
  * [6][1][20][cells] (GKS-2nd).                                            */
 int orc_face_states(const orc_params *P, const double *Q, const double *G,

@@ -40,6 +40,8 @@ int flux_gp(const orc_params &P, const double *sl, const double *sr,
             double dt, double *out30);
 
 /* recon.cpp */
+double geno_misfit(const double *q0, const double *d, const double *a, int v);
+double geno_chi(double sigma);
 void recon5_cell(const double *q0, const double *dvec, double hx, double hy,
                  double hz, int nonlinear, double *out480, double *chi5);
 void recon2_cell(const double *q7, double hx, double hy, double hz,

@@ -114,7 +114,9 @@ int gauss_jordan(int n, int m, std::vector<ld> &A) {
 
 struct Recon5Tables {
     double R[34][63];          /* coefficients a = R d                      */
-    double H[34][34];          /* IS_H = a^T H a                            */
+    double B[45][34];          /* derivative rows of Eq. compact-big-5
+                                  (unweighted)                              */
+    double wq[45];             /* their least-squares weights (R3)          */
     double mean0[34];          /* mean of delta^d/d! over the target cell   */
     int ok;
 };
@@ -163,6 +165,10 @@ Recon5Tables build_tables() {
      * null space of the constraints (5.07 against 29.6 with unit weights). */
     ld wq[45];
     for (int q = 0; q < 45; ++q) wq[q] = (q >= 18 && q < 42) ? 0.1L : 1.0L;
+    for (int q = 0; q < 45; ++q) {
+        T.wq[q] = (double)wq[q];
+        for (int i = 0; i < 34; ++i) T.B[q][i] = (double)B[q][i];
+    }
     for (int q = 0; q < 45; ++q)
         for (int i = 0; i < 34; ++i) B[q][i] *= wq[q];
     const int n = 34 + 18, m = 63, w = n + m;
@@ -185,39 +191,6 @@ Recon5Tables build_tables() {
     for (int i = 0; i < 34; ++i)
         for (int c = 0; c < 63; ++c) T.R[i][c] = (double)A[i * w + n + c];
 
-    /* smoothness quadratic form: sum over 1 <= |alpha| <= 4 of
-     * int_{[-1/2,1/2]^3} D^alpha p_d D^alpha p_e                         */
-    auto cell_int = [](int e0, int e1, int e2) -> ld {
-        const int e[3] = {e0, e1, e2};
-        ld v = 1;
-        for (int j = 0; j < 3; ++j) {
-            if (e[j] % 2) return 0;
-            v *= ipow(0.5L, e[j]) / (e[j] + 1);
-        }
-        return v;
-    };
-    for (int i = 0; i < 34; ++i)
-        for (int j = 0; j < 34; ++j) {
-            ld s = 0;
-            for (int a0 = 0; a0 <= 4; ++a0)
-                for (int a1 = 0; a0 + a1 <= 4; ++a1)
-                    for (int a2 = 0; a0 + a1 + a2 <= 4; ++a2) {
-                        if (a0 + a1 + a2 == 0) continue;
-                        const int al[3] = {a0, a1, a2};
-                        int ei[3], ej[3];
-                        bool ok = true;
-                        for (int q = 0; q < 3; ++q) {
-                            ei[q] = b.d[i][q] - al[q];
-                            ej[q] = b.d[j][q] - al[q];
-                            if (ei[q] < 0 || ej[q] < 0) ok = false;
-                        }
-                        if (!ok) continue;
-                        s += cell_int(ei[0] + ej[0], ei[1] + ej[1], ei[2] + ej[2]) /
-                             (fact(ei[0]) * fact(ei[1]) * fact(ei[2]) *
-                              fact(ej[0]) * fact(ej[1]) * fact(ej[2]));
-                    }
-            T.H[i][j] = (double)s;
-        }
     for (int i = 0; i < 34; ++i) T.mean0[i] = (double)avg_mono(z, b.d[i]);
     T.ok = 1;
     return T;
@@ -258,6 +231,47 @@ void eval_basis(const double x[3], double p[34], double dp[3][34]) {
 
 }  // namespace
 
+/* GENO's switch chi (reading R5). The quartic P4 of Eq. compact-big-5
+ * meets the 18 neighbour averages exactly and the 45 derivative data in
+ * the weighted least-squares sense; what it cannot meet measures how far
+ * the stencil's data are from one smooth function:
+ *   sigma = |W (B a - d_B)|^2 / (|d_C|^2 + |W d_B|^2 + (kappa S)^2 + eps),
+ * W the row weights of R3, d_C the 18 average differences, d_B the 45
+ * derivative data. sigma = 0 for data sampled from any quartic, O(h^8) for
+ * a smooth field (the least-squares residual is the quintic remainder,
+ * O(h^4) relative to the data), O(1) across a discontinuity. S is the
+ * cell's own magnitude (rho; rho E; sqrt(rho rho E) for a momentum
+ * component) and kappa = 0.01: variations below about a percent of it are
+ * not limited. chi = 1/(1 + s + s^2), s = sigma/sigma0, sigma0 = 5e-4:
+ * 1 - chi = O(h^8) on smooth data and grows only linearly with a small
+ * misfit (no sharp switch on smooth but under-resolved data, whose
+ * rounding it would amplify), chi ~ s^-2 at a discontinuity (chi < 1e-3
+ * where sigma > 0.016; a jump through the cell gives 0.02 to 0.1). */
+double geno_misfit(const double *q0, const double *d, const double *a, int v) {
+    const Recon5Tables &T = tables();
+    const double eps = 1e-15, kappa = 0.01;
+    double res2 = 0.0, norm2 = 0.0;
+    for (int k = 0; k < 18; ++k) norm2 += d[k] * d[k];
+    for (int q = 0; q < 45; ++q) {
+        double Ba = 0.0;
+        for (int i = 0; i < 34; ++i) Ba += T.B[q][i] * a[i];
+        const double r = T.wq[q] * (Ba - d[18 + q]);
+        const double wd = T.wq[q] * d[18 + q];
+        res2 += r * r;
+        norm2 += wd * wd;
+    }
+    double S;
+    if (v == 0) S = q0[0];
+    else if (v == 4) S = q0[4];
+    else S = std::sqrt(std::fabs(q0[0] * q0[4]));
+    return res2 / (norm2 + kappa * kappa * S * S + eps);
+}
+
+double geno_chi(double sigma) {
+    const double s = sigma / 5e-4;
+    return 1.0 / (1.0 + s + s * s);
+}
+
 void recon5_cell(const double *q0, const double *dvec, double hx, double hy,
                  double hz, int nonlinear, double *out, double *chi5) {
     const Recon5Tables &T = tables();
@@ -275,26 +289,20 @@ void recon5_cell(const double *q0, const double *dvec, double hx, double hy,
         }
         double chi = 1.0, w[6] = {0, 0, 0, 0, 0, 0}, bm[6][3];
         if (nonlinear) {
-            /* linear sub-stencil polynomials P1_m (reading R4) */
-            double IS[6], wsum = 0.0;
+            /* linear sub-stencil polynomials P1_m (reading R4) and their
+             * ENO weights of Eq. weno-new */
+            double wsum = 0.0;
             for (int m = 0; m < 6; ++m) {
                 const int ax = m / 2;
                 const double sg = (m % 2) ? 1.0 : -1.0;
                 for (int j = 0; j < 3; ++j) bm[m][j] = d[60 + j];
                 bm[m][ax] = sg * d[m];
-                IS[m] = bm[m][0] * bm[m][0] + bm[m][1] * bm[m][1] + bm[m][2] * bm[m][2];
-                w[m] = dm / std::pow(IS[m] + eps, 5);
+                const double IS = bm[m][0] * bm[m][0] + bm[m][1] * bm[m][1] + bm[m][2] * bm[m][2];
+                w[m] = dm / std::pow(IS + eps, 5);
                 wsum += w[m];
             }
-            double ISL = 0.0;
-            for (int m = 0; m < 6; ++m) { w[m] /= wsum; ISL += w[m] * IS[m]; }
-            double ISH = 0.0;
-            for (int i = 0; i < 34; ++i)
-                for (int j = 0; j < 34; ++j) ISH += a[i] * T.H[i][j] * a[j];
-            /* project-defined chi (reading R5) */
-            const double rr = std::fabs(ISH - ISL) / (ISH + ISL + eps);
-            const double q = rr / 0.1;
-            chi = 1.0 / (1.0 + q * q * q);
+            for (int m = 0; m < 6; ++m) w[m] /= wsum;
+            chi = geno_chi(geno_misfit(q0, d, a, v));
         }
         if (chi5) chi5[v] = chi;
         for (int f = 0; f < 6; ++f)
@@ -413,10 +421,18 @@ extern "C" int orc_recon5_matrix(double *R) {
     return 0;
 }
 
-extern "C" int orc_is_matrix(double *H) {
-    const orc::Recon5Tables &T = orc::tables();
-    if (!T.ok) return -1;
-    std::memcpy(H, T.H, sizeof(T.H));
+extern "C" int orc_geno_misfit(const double *q0, const double *dvec, double *sigma5) {
+    if (!orc::tables().ok) return -1;
+    for (int v = 0; v < 5; ++v) {
+        const double *d = dvec + 63 * v;
+        double a[34];
+        for (int i = 0; i < 34; ++i) {
+            double s = 0.0;
+            for (int c = 0; c < 63; ++c) s += orc::tables().R[i][c] * d[c];
+            a[i] = s;
+        }
+        sigma5[v] = orc::geno_misfit(q0, d, a, v);
+    }
     return 0;
 }
 

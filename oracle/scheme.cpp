@@ -53,7 +53,7 @@ int nthreads(const orc_params &P) { return P.threads > 0 ? P.threads : 1; }
 
 /* Face states of cell c (Sec. 3.2 / 3.3): o[6][ngp][20]. */
 void cell_face_states(const orc_params &P, const Grid &g, const double *Q,
-                      const double *G, long c, double *o) {
+                      const double *G, long c, double *o, double *chi5 = nullptr) {
     const long n = g.n;
     int i, j, k;
     g.ijk(c, i, j, k);
@@ -84,7 +84,7 @@ void cell_face_states(const orc_params &P, const Grid &g, const double *Q,
             }
             for (int a = 0; a < 3; ++a) dv[60 + a] = g.h[a] * G[(v * 3 + a) * n + c];
         }
-        recon5_cell(q0, d, g.h[0], g.h[1], g.h[2], P.nonlinear, o, nullptr);
+        recon5_cell(q0, d, g.h[0], g.h[1], g.h[2], P.nonlinear, o, chi5);
     } else {
         double q7[35];
         for (int v = 0; v < 5; ++v) q7[v] = Q[v * n + c];
@@ -227,6 +227,20 @@ extern "C" int orc_face_states(const orc_params *P, const double *Q,
                 for (int q = 0; q < 20; ++q)
                     fs_out[(((size_t)f * ngp + k) * 20 + q) * g.n + c] =
                         fs[(((size_t)c * 6 + f) * ngp + k) * 20 + q];
+    return 0;
+}
+
+extern "C" int orc_chi_field(const orc_params *P, const double *Q, const double *G,
+                             double *chi) {
+    if (!P->scheme) return -1;
+    const Grid g = make_grid(*P);
+    const long n = g.n;
+#pragma omp parallel for num_threads(nthreads(*P)) schedule(static)
+    for (long c = 0; c < n; ++c) {
+        double o[6 * 4 * 20], c5[5];
+        cell_face_states(*P, g, Q, G, c, o, c5);
+        for (int v = 0; v < 5; ++v) chi[(size_t)v * n + c] = c5[v];
+    }
     return 0;
 }
 
