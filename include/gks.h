@@ -222,9 +222,9 @@ int gks_recon_matrix(double *R);
  * reconstruction collapsing to the linear quartic -- so that confident
  * (cell, variable) pairs skip the nonlinear weights; all others run the
  * full reconstruction. Network: x = the 63-entry data vector of S^data-5th,
- * xh = x/(max|x| + 1e-30), h = max(W1 xh + b1, 0) (16 units),
- * logit = w2 . h + b2. Parameters (gks_mlp_nparams() floats): W1 [16][63]
- * row major, b1 [16], w2 [16], b2. */
+ * xh = x/(max|x| + 1e-30), h = max(W1 xh + b1, 0) (8 units),
+ * logit = w2 . h + b2. Parameters (gks_mlp_nparams() floats): W1 [8][63]
+ * row major, b1 [8], w2 [8], b2. */
 int gks_mlp_nparams(void);
 
 /* Training data from the method itself (CGKS-5th context, any precision):
@@ -307,6 +307,38 @@ int gks_ensemble_dump(gks_ensemble *e, const double *Q, const double *gradQ,
                       float label_eps, float *x, float *chi, float *y);
 /* The learned indicator for a mixed-precision ensemble (see gks_set_indicator). */
 int gks_ensemble_set_indicator(gks_ensemble *e, const float *params, float theta);
+
+/* Per-kernel device time of the steps that follow (no counterpart in the
+ * paper; it gives the benchmark each kernel's launch duration inside its
+ * timed region). on = 1 synchronises the stream, discards earlier records
+ * and starts recording a CUDA event on the context's stream before and
+ * after every launch gks_step makes (time step, reconstruction, flux,
+ * update; one reconstruction and one flux launch per z-slab); the events
+ * add no synchronisation. on = 0 stops recording (the records are kept).
+ * Do not capture gks_step in a CUDA graph while recording is on.
+ * Returns GKS_ERR_ARG for a NULL context or on not 0/1, GKS_ERR_NOMEM,
+ * GKS_ERR_CUDA. */
+int gks_kernel_timing(gks_ctx *ctx, int on);
+
+/* The recorded times: synchronises the stream, then ms[k] = summed
+ * milliseconds and launches[k] = number of launches of kind k = 0
+ * reconstruction, 1 flux, 2 update, 3 time step (host arrays of 4) since
+ * the last gks_kernel_timing(ctx, 1); zeros if nothing was recorded.
+ * Returns GKS_ERR_ARG for NULL arguments, GKS_ERR_CUDA. */
+int gks_kernel_times(gks_ctx *ctx, double *ms, long long *launches);
+
+/* Measured fused multiply-add throughput of this device (no counterpart in
+ * the paper; it is the denominator of the FP64 and FP32 roofline fractions
+ * of the ALU-bound kernels). precision: GKS_PREC_FP64 times double FMAs,
+ * GKS_PREC_MIXED float FMAs. One kernel of independent FMA chains over
+ * 4 x (SM count) blocks of 256 threads, best of three launches timed with
+ * CUDA events on cuda_stream (NULL = legacy default stream), after one
+ * warm-up launch; *flops = 2 FMAs per FMA instruction lane / second,
+ * *ms = the best launch's duration (~30 ms at GB300's nominal rates).
+ * Allocates and frees a 1.2 MB device buffer and synchronises the stream.
+ * Returns GKS_ERR_ARG for a bad precision or NULL outputs, GKS_ERR_NOMEM,
+ * GKS_ERR_CUDA. */
+int gks_fma_rate(int precision, void *cuda_stream, double *flops, double *ms);
 
 /* Diagnostics without any device allocation (the paper has no counterpart:
  * this serves callers of this library, not the method).

@@ -103,6 +103,20 @@ constexpr float kMlpDelta = 1e-30f;
 
 constexpr int kColFace = 0, kColEdge = 6, kColFaceGrad = 18, kColEdgeGrad = 36,
               kColCentreGrad = 60;
+// least-squares weight of data column k (the h_1, h_2, h_3 of Eq.
+// compact-big-5 relative to the cell size that scales the derivative data):
+// 1 for the averages, the face neighbours' gradients and the own gradient,
+// kEdgeWeight for the edge neighbours' tangential derivatives
+constexpr double kEdgeWeight = 0.1;
+GKS_HD constexpr double col_weight(int k) {
+    return (k >= kColEdgeGrad && k < kColCentreGrad) ? kEdgeWeight : 1.0;
+}
+// GENO's switch (reading of Eq. weno-new's chi): the misfit sigma of the
+// quartic against the derivative data, relative to the data's norm plus
+// (kGenoKappa S)^2 with S the cell's own magnitude; chi = 1/(1 + s + s^2),
+// s = sigma / kGenoSigma0
+constexpr double kGenoSigma0 = 5e-4;
+constexpr double kGenoKappa = 0.01;
 
 // ---- reflection structure of the data vector ---------------------------
 // The stencil and the least-squares problem are invariant under the eight
@@ -227,7 +241,9 @@ static_assert(sym_table_ok(), "reflection table of the data vector is incomplete
 struct ReconTables {
     double R[kNumBasis][kNumData];      // coefficients a = R d
     double Rs[kNumData][kMaxClass];     // a_{class(r), j} += Rs[r][j] d^s_r
-    double H[kNumBasis][kNumBasis];     // IS_H = a^T H a
+    double Bs[kNumData][kMaxClass];     // weighted derivative rows W B of the
+                                        // least squares in the symmetrised
+                                        // basis (zero for the average rows)
     double mean[kNumBasis];             // mean of delta^d/d! over Omega_0
     double mval[3][kNumBasis];          // |value| factors at the Gauss points
                                         // of the faces normal to axis d

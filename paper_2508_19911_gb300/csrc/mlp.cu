@@ -2,7 +2,7 @@
 // on the GPU, and its C-ABI.
 //
 // Network: x (the 63-entry CGKS-5th data vector) -> xh = x/(max|x| + delta)
-// -> z = W1 xh + b1 (16) -> h = max(z, 0) -> logit = w2 . h + b2,
+// -> z = W1 xh + b1 (kMlpHidden = 8) -> h = max(z, 0) -> logit = w2 . h + b2,
 // p = sigmoid(logit) = probability that GENO's chi equals 1 (within the
 // label tolerance), i.e. that the nonlinear reconstruction is the linear P4.
 // Loss: mean over the batch of w_y (softplus(logit) - y logit), w_0 = the

@@ -10,9 +10,12 @@
 //      reflections, form the symmetrised combinations and accumulate
 //      a = R d by parity-class blocks (basis.h: kSym, kClass);
 //   2. GENO (Eq. weno-new): the six sub-stencil slopes b^m (Eq.
-//      compact-sub-2), IS_m = |b^m|^2, w_m = d_m/(IS_m + eps)^5 normalised,
-//      IS_H = a^T H a (H block-diagonal by parity class),
-//      chi = 1/(1 + (r/0.1)^3), r = |IS_H - IS_L|/(IS_H + IS_L + eps);
+//      compact-sub-2), IS_m = |b^m|^2, w_m = d_m/(IS_m + eps)^5 normalised;
+//      chi from the misfit of the quartic against the derivative data,
+//      sigma = |W (B a - d_B)|^2 / (|d_C|^2 + |W d_B|^2 + (kappa S)^2 + eps)
+//      (W B block-diagonal by parity class in the symmetrised basis, the
+//      derivative columns loaded a second time), chi = 1/(1 + s + s^2),
+//      s = sigma/sigma0;
 //   3. evaluate P4 and its gradient at the 24 face Gauss points: the
 //      monomials are summed into 8 parity classes per face axis and the 8
 //      points of a face follow by a Walsh-Hadamard transform.
@@ -31,15 +34,15 @@ constexpr int kPadS = 12;                                 // kMaxClass padded to
 constexpr int kTabRs = 0;                                 // [63][kPadS]: class block of R per combination
 constexpr int kTabMval = kTabRs + kNumData * kPadS;       // [3][kPad]
 constexpr int kTabMder = kTabMval + 3 * kPad;             // [3][3][kPad]
-constexpr int kTabH = kTabMder + 9 * kPad;                // [34][kPad]
-constexpr int kTabMean = kTabH + kNumBasis * kPad;        // [kPad]
+constexpr int kTabBs = kTabMder + 9 * kPad;               // [63][kPadS]: class block of W B
+constexpr int kTabMean = kTabBs + kNumData * kPadS;       // [kPad]
 constexpr int kTabW1 = kTabMean + kPad;                   // [63][kMlpHidden]: column c of W1
 constexpr int kTabB1 = kTabW1 + kNumData * kMlpHidden;    // [kMlpHidden]
 constexpr int kTabW2 = kTabB1 + kMlpHidden;               // [kMlpHidden]
 constexpr int kTabB2 = kTabW2 + kMlpHidden;               // b2, logit(theta), 2 unused
 constexpr int kTabFloats = kTabB2 + 4;
 static_assert(kMaxClass <= kPadS && kPadS % 4 == 0, "class block padding");
-static_assert(kTabMval % 4 == 0 && kTabMder % 4 == 0 && kTabH % 4 == 0 && kTabMean % 4 == 0 &&
+static_assert(kTabMval % 4 == 0 && kTabMder % 4 == 0 && kTabBs % 4 == 0 && kTabMean % 4 == 0 &&
                   kTabW1 % 4 == 0 && kMlpHidden % 4 == 0 && kTabFloats % 4 == 0,
               "sections of the FP32 table must be float4 aligned");
 // the learned smoothness indicator's network lives in the same table (one
@@ -258,6 +261,7 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
 #pragma unroll
         for (int jj = 0; jj < kMlpHidden; ++jj) hid[jj] = 0.0f;
         float dface[6], dctr[3];
+        float norm2 = 0.0f;  // |d_C|^2 + |W d_B|^2 for GENO's misfit
         // a = R d orbit by orbit (see recon5_cell); the network and the dump
         // see the raw columns as they are loaded. Dump mode: data entry COL
         // of (cell, variable) -> dump_x[COL * dump_ld + dump_base + 5 c + v]
@@ -271,6 +275,8 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
                     constexpr int col = kSym.mem[r][q];
                     ov[q] = data_col_f<col, VIEW>(Qv, Gv, qh, ql, Gfv, n, c, nbF, nbE, q0, h0, l0,
                                                   hf);
+                    constexpr float wc = (float)(col_weight(col) * col_weight(col));
+                    norm2 = fmaf(wc * ov[q], ov[q], norm2);
                     if constexpr (col < kColEdge) dface[col] = ov[q];
                     if constexpr (col >= kColCentreGrad) dctr[col - kColCentreGrad] = ov[q];
                     if constexpr (MODE == kModeIndicator) add_hidden_f<col>(T, hid, amax, ov[q]);
@@ -322,7 +328,7 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
         float chi = 1.0f, bbar[3] = {0.0f, 0.0f, 0.0f};
         if (geno) {
             const float eps = 1e-15f;
-            float w[6], IS[6], t[6];
+            float w[6], t[6];
 #pragma unroll
             for (int m = 0; m < 6; ++m) {
                 const int ax = m / 2;
@@ -331,7 +337,6 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
                     if (q != ax) s = fmaf(dctr[q], dctr[q], s);
-                IS[m] = s;
                 t[m] = s + eps;
             }
             // w_m = (1/t_m^5) / sum_k (1/t_k^5) with t = IS + eps, written with
@@ -349,30 +354,63 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
                 usum += u5[m];
             }
             const float iusum = 1.0f / usum;
-            float ISL = 0.0f;
 #pragma unroll
-            for (int m = 0; m < 6; ++m) {
-                w[m] = u5[m] * iusum;
-                ISL = fmaf(w[m], IS[m], ISL);
-            }
+            for (int m = 0; m < 6; ++m) w[m] = u5[m] * iusum;
 #pragma unroll
             for (int q = 0; q < 3; ++q)
                 bbar[q] = (1.0f - w[2 * q] - w[2 * q + 1]) * dctr[q] - w[2 * q] * dface[2 * q] +
                           w[2 * q + 1] * dface[2 * q + 1];
-            float ISH = 0.0f;
-            static_for<kNumBasis>([&](auto I) {
-                constexpr int ii = decltype(I)::value;
-                float tt = 0.0f;
-                static_for<kNumBasis>([&](auto J) {
-                    constexpr int jj = decltype(J)::value;
-                    if constexpr (jj >= ii && basis_class(ii) == basis_class(jj))
-                        tt = fmaf(T[kTabH + ii * kPad + jj], a[jj], tt);
-                });
-                ISH = fmaf(a[ii], tt, ISH);
+            // GENO's misfit (see recon_fp64.cu), derivative columns reloaded
+            float res2 = 0.0f;
+            static_for<kNumData>([&](auto Rr) {
+                constexpr int r = decltype(Rr)::value;
+                constexpr int nm = kSym.nm[r];
+                if constexpr (kSym.mem[r][0] >= kColFaceGrad) {
+                    if constexpr (kSym.orbit[r] == r) {
+                        static_for<nm>([&](auto Qq) {
+                            constexpr int q = decltype(Qq)::value;
+                            constexpr int col = kSym.mem[r][q];
+                            ov[q] = data_col_f<col, VIEW>(Qv, Gv, qh, ql, Gfv, n, c, nbF, nbE, q0,
+                                                          h0, l0, hf);
+                        });
+                    }
+                    float ds = kSym.sgn[r][0] > 0 ? ov[0] : -ov[0];
+                    static_for<nm - 1>([&](auto Qq) {
+                        constexpr int q = decltype(Qq)::value + 1;
+                        if constexpr (kSym.sgn[r][q] > 0) ds += ov[q];
+                        else ds -= ov[q];
+                    });
+                    constexpr int cls = kSym.cls[r];
+                    constexpr float wr = (float)col_weight(kSym.mem[r][0]);
+                    float res = -wr * ds;
+                    static_for<(kClass.n[cls] + 3) / 4>([&](auto J4) {
+                        constexpr int j4 = decltype(J4)::value;
+                        const float4 bw = ld4(T, kTabBs + r * kPadS + 4 * j4);
+                        static_for<4>([&](auto K) {
+                            constexpr int jj = 4 * j4 + decltype(K)::value;
+                            if constexpr (jj < kClass.n[cls]) {
+                                constexpr int ib = kClass.member[cls][jj];
+                                res = fmaf(f4(bw, decltype(K)::value), a[ib], res);
+                            }
+                        });
+                    });
+                    res2 = fmaf(res * (1.0f / nm), res, res2);
+                }
             });
-            const float r = fabsf(ISH - ISL) / (ISH + ISL + eps);
-            const float rr = r * 10.0f;
-            chi = 1.0f / (1.0f + rr * rr * rr);
+            // the cell's own magnitude: rho, rho E, sqrt(rho rho E) for momenta
+            float r0, e0;
+            if constexpr (VIEW) {
+                r0 = __ldg(Qhi + c);
+                e0 = __ldg(Qhi + 4 * n + c);
+            } else {
+                r0 = (float)__ldg(Q + c);
+                e0 = (float)__ldg(Q + 4 * n + c);
+            }
+            const float S = v == 0 ? r0 : (v == 4 ? e0 : sqrtf(fabsf(r0 * e0)));
+            const float kap = (float)kGenoKappa;
+            const float sig = res2 / (norm2 + kap * kap * S * S + eps);
+            const float s = sig * (float)(1.0 / kGenoSigma0);
+            chi = 1.0f / (1.0f + s + s * s);
         }
         if (MODE == kModeDump) {
             dump_chi[dump_base + 5 * c + v] = chi;
@@ -518,12 +556,11 @@ int upload_recon_tables(void) {
     static float tab[kTabW1];
     for (int i = 0; i < kTabW1; ++i) tab[i] = 0.0f;
     for (int r = 0; r < kNumData; ++r)
-        for (int j = 0; j < kMaxClass; ++j) tab[kTabRs + r * kPadS + j] = (float)t.Rs[r][j];
+        for (int j = 0; j < kMaxClass; ++j) {
+            tab[kTabRs + r * kPadS + j] = (float)t.Rs[r][j];
+            tab[kTabBs + r * kPadS + j] = (float)t.Bs[r][j];
+        }
     for (int i = 0; i < kNumBasis; ++i) {
-        // IS_H from the upper triangle: H_ii and H_ij + H_ji (j > i)
-        for (int j = 0; j < kNumBasis; ++j)
-            tab[kTabH + i * kPad + j] =
-                j < i ? 0.0f : (float)(j == i ? t.H[i][i] : t.H[i][j] + t.H[j][i]);
         tab[kTabMean + i] = (float)t.mean[i];
         for (int d = 0; d < 3; ++d) {
             tab[kTabMval + d * kPad + i] = (float)t.mval[d][i];

@@ -14,7 +14,7 @@ namespace {
 
 __constant__ double cR[kNumBasis][kNumData];
 __constant__ double cRs[kNumData][kMaxClass];  // R in the symmetrised data basis
-__constant__ double cH[kNumBasis][kNumBasis];
+__constant__ double cBs[kNumData][kMaxClass];  // weighted derivative rows, same basis
 __constant__ double cMean[kNumBasis];
 __constant__ double cMval[3][kNumBasis];
 __constant__ double cMder[3][3][kNumBasis];
@@ -132,6 +132,7 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
 #pragma unroll
     for (int ii = 0; ii < kNumBasis; ++ii) a[ii] = 0.0;
     double dface[6], dctr[3];
+    double norm2 = 0.0;  // |d_C|^2 + |W d_B|^2 for GENO's misfit
     // a = R d orbit by orbit: load the orbit's columns, form its symmetrised
     // combinations, multiply each with its class block of R
     double ov[8];
@@ -143,6 +144,8 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
                 constexpr int q = decltype(Qq)::value;
                 constexpr int col = kSym.mem[r][q];
                 ov[q] = data_col<col>(Qv, Gv, n, c, nbF, nbE, q0, h);
+                constexpr double wc = col_weight(col);
+                norm2 = fma(wc * wc * ov[q], ov[q], norm2);
                 if constexpr (col < kColEdge) dface[col] = ov[q];
                 if constexpr (col >= kColCentreGrad) dctr[col - kColCentreGrad] = ov[q];
             });
@@ -172,7 +175,7 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
     double chi = 1.0, bbar[3] = {0.0, 0.0, 0.0};
     if (nonlinear) {
         const double eps = 1e-15;
-        double w[6], IS[6], wsum = 0.0;
+        double w[6], wsum = 0.0;
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
             const int ax = m / 2;
@@ -181,17 +184,12 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
 #pragma unroll
             for (int q = 0; q < 3; ++q)
                 if (q != ax) s = fma(dctr[q], dctr[q], s);
-            IS[m] = s;
             const double t = s + eps, t2 = t * t;
             w[m] = (1.0 / 6.0) / (t2 * t2 * t);
             wsum += w[m];
         }
-        double ISL = 0.0;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            w[m] /= wsum;
-            ISL = fma(w[m], IS[m], ISL);
-        }
+        for (int m = 0; m < 6; ++m) w[m] /= wsum;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             // sum_m w_m b^m_q: tangential slopes from the own gradient,
@@ -199,20 +197,44 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
             bbar[q] = (1.0 - w[2 * q] - w[2 * q + 1]) * dctr[q] - w[2 * q] * dface[2 * q] +
                       w[2 * q + 1] * dface[2 * q + 1];
         }
-        double ISH = 0.0;
-        static_for<kNumBasis>([&](auto I) {
-            constexpr int ii = decltype(I)::value;
-            double t = 0.0;
-            static_for<kNumBasis>([&](auto J) {
-                constexpr int jj = decltype(J)::value;
-                if constexpr (jj >= ii && basis_class(ii) == basis_class(jj))
-                    t = fma(cH[ii][jj], a[jj], t);
-            });
-            ISH = fma(a[ii], t, ISH);
+        // GENO's misfit: |W (B a - d_B)|^2 orbit by orbit in the symmetrised
+        // basis (sum over an orbit's combinations of res_r^2 / nm), the
+        // derivative columns loaded again (they were read moments ago)
+        double res2 = 0.0;
+        static_for<kNumData>([&](auto Rr) {
+            constexpr int r = decltype(Rr)::value;
+            constexpr int nm = kSym.nm[r];
+            if constexpr (kSym.mem[r][0] >= kColFaceGrad) {
+                if constexpr (kSym.orbit[r] == r) {
+                    static_for<nm>([&](auto Qq) {
+                        constexpr int q = decltype(Qq)::value;
+                        constexpr int col = kSym.mem[r][q];
+                        ov[q] = data_col<col>(Qv, Gv, n, c, nbF, nbE, q0, h);
+                    });
+                }
+                double ds = kSym.sgn[r][0] > 0 ? ov[0] : -ov[0];
+                static_for<nm - 1>([&](auto Qq) {
+                    constexpr int q = decltype(Qq)::value + 1;
+                    if constexpr (kSym.sgn[r][q] > 0) ds += ov[q];
+                    else ds -= ov[q];
+                });
+                constexpr int cls = kSym.cls[r];
+                constexpr double wr = col_weight(kSym.mem[r][0]);
+                double res = -wr * ds;
+                static_for<kClass.n[cls]>([&](auto J) {
+                    constexpr int jj = decltype(J)::value;
+                    constexpr int ib = kClass.member[cls][jj];
+                    res = fma(cBs[r][jj], a[ib], res);
+                });
+                res2 = fma(res * (1.0 / nm), res, res2);
+            }
         });
-        const double r = fabs(ISH - ISL) / (ISH + ISL + eps);
-        const double rr = r * 10.0;
-        chi = 1.0 / (1.0 + rr * rr * rr);
+        // the cell's own magnitude: rho, rho E, sqrt(rho rho E) for momenta
+        const double r0 = __ldg(Q + c), e0 = __ldg(Q + 4 * n + c);
+        const double S = v == 0 ? r0 : (v == 4 ? e0 : sqrt(fabs(r0 * e0)));
+        const double sig = res2 / (norm2 + kGenoKappa * kGenoKappa * S * S + eps);
+        const double s = sig * (1.0 / kGenoSigma0);
+        chi = 1.0 / (1.0 + s + s * s);
     }
     eval_faces<0>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
     eval_faces<1>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
@@ -312,12 +334,7 @@ __global__ void __launch_bounds__(128) recon5_ens_fp64_kernel(const EnsInst *__r
 int upload_recon_tables_fp64(const ReconTables &t) {
     if (cudaMemcpyToSymbol(cR, t.R, sizeof(t.R)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cRs, t.Rs, sizeof(t.Rs)) != cudaSuccess) return -2;
-    // IS_H = a^T H a from the upper triangle: H_ii and H_ij + H_ji (j > i)
-    static double Hu[kNumBasis][kNumBasis];
-    for (int i = 0; i < kNumBasis; ++i)
-        for (int j = 0; j < kNumBasis; ++j)
-            Hu[i][j] = j < i ? 0.0 : (j == i ? t.H[i][i] : t.H[i][j] + t.H[j][i]);
-    if (cudaMemcpyToSymbol(cH, Hu, sizeof(Hu)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(cBs, t.Bs, sizeof(t.Bs)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cMean, t.mean, sizeof(t.mean)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cMval, t.mval, sizeof(t.mval)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cMder, t.mder, sizeof(t.mder)) != cudaSuccess) return -2;

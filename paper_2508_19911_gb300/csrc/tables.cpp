@@ -133,9 +133,8 @@ int build_recon_tables(ReconTables *t) {
     // condition number of the weighted least-squares system on the
     // constraints' null space (5.07; 29.6 with unit weights, which also
     // leaves the linear scheme with a growing grid-scale vortical mode)
-    constexpr double kEdgeWeight = 0.1;
     std::vector<double> wrow(nl, 1.0);
-    for (int k = 18; k < 42; ++k) wrow[k] = kEdgeWeight;
+    for (int k = 0; k < nl; ++k) wrow[k] = col_weight(ne + k);
     for (int k = 0; k < nl; ++k)
         for (int i = 0; i < nb; ++i) B(k, i) *= wrow[k];
 
@@ -220,30 +219,34 @@ int build_recon_tables(ReconTables *t) {
         }
     }
 
-    // smoothness form and means on the unit cell [-1/2, 1/2]^3
+    // GENO's misfit: the weighted derivative rows W B (B was weighted in
+    // place above) in the symmetrised data basis, row r = sum_m T[r][m]
+    // (W B)_m over the orbit's columns; by the reflection symmetry it has
+    // entries on class(r) monomials only, which is checked here. Rows of
+    // the average combinations stay zero (those data are met exactly).
+    double bmax = 0.0;
+    for (int k = 0; k < nl; ++k)
+        for (int i = 0; i < nb; ++i) bmax = std::fmax(bmax, std::fabs(B(k, i)));
+    for (int r = 0; r < kNumData; ++r) {
+        if (kSym.mem[r][0] < kColFaceGrad) continue;
+        const int c = kSym.cls[r];
+        for (int i = 0; i < nb; ++i) {
+            double s = 0.0;
+            for (int q = 0; q < kSym.nm[r]; ++q)
+                s += kSym.sgn[r][q] * B(kSym.mem[r][q] - ne, i);
+            if (parity_class(kExp[i][0], kExp[i][1], kExp[i][2]) == c)
+                t->Bs[r][kClass.pos[i]] = s;
+            else if (std::fabs(s) > 1e-12 * bmax)
+                return -1;
+        }
+    }
+
+    // means of the monomials on the unit cell [-1/2, 1/2]^3
     auto mono_int = [](int n) { return (n % 2) ? 0.0 : std::pow(0.5, n) / (n + 1); };
     for (int i = 0; i < nb; ++i) {
         t->mean[i] = 1.0;
         for (int j = 0; j < 3; ++j) t->mean[i] *= mono_int(kExp[i][j]) / factorial(kExp[i][j]);
     }
-    for (int i = 0; i < nb; ++i)
-        for (int k = 0; k < nb; ++k) {
-            double s = 0.0;
-            for (int a0 = 0; a0 <= 4; ++a0)
-                for (int a1 = 0; a0 + a1 <= 4; ++a1)
-                    for (int a2 = 0; a0 + a1 + a2 <= 4; ++a2) {
-                        if (a0 + a1 + a2 == 0) continue;
-                        const int al[3] = {a0, a1, a2};
-                        double v = 1.0;
-                        for (int j = 0; j < 3 && v != 0.0; ++j) {
-                            const int ei = kExp[i][j] - al[j], ek = kExp[k][j] - al[j];
-                            if (ei < 0 || ek < 0) { v = 0.0; break; }
-                            v *= mono_int(ei + ek) / (factorial(ei) * factorial(ek));
-                        }
-                        s += v;
-                    }
-            t->H[i][k] = s;
-        }
 
     // magnitudes of x^e/e! and of its derivatives at the Gauss points of the
     // faces normal to axis d: |x_d| = 1/2, the two tangential |x| = g

@@ -168,7 +168,10 @@ def test_mixed_flux_shell_accuracy(torch_dev, case):
     the FP64 flux kernel on identical face states, per record block and
     group (density, momentum, energy), relative to the FP64 group scale:
     F^n (float-float parts) within 1e-7; F_t and dQ/dt (FP32 core, tau-sized
-    coefficients) within 2e-5; the interface values Q = W0 + e (W - W0)
+    coefficients) within 2e-5 of max(their scale, the scale of F^n or Q
+    over dt) -- on smooth, resolved flow the reconstruction leaves no jump
+    at the faces and F_t is the small physical time derivative; the
+    interface values Q = W0 + e (W - W0)
     within 1e-7 (W0 float-float; the blend weight e and the difference are
     FP32, so where the jump W - W0 is large the error is FP32-level: 1.5e-8
     on the double Sod, 1e-14 on smooth flow)."""
@@ -196,8 +199,14 @@ def test_mixed_flux_shell_accuracy(torch_dev, case):
     want = f64.flux(restore_offsets(torch, fsm, Qd).contiguous(), dtd).cpu().numpy()
     want = want.reshape(3, 6, 5, -1)
     bounds = {0: 1e-7, 1: 2e-5, 2: 1e-7, 3: 2e-5, 4: 1e-7, 5: 2e-5}
+    dt = float(dtd.item())
     for blk, bound in bounds.items():
         for gi in ([0], [1, 2, 3], [4]):
             scale = np.abs(want[:, blk, gi]).max()
+            if blk % 2:
+                # a time derivative enters the update multiplied by dt next
+                # to its quantity (Sec. 3.4: Q + dt L + dt^2/2 dL/dt, and
+                # Q_G^n + dt dQ_G/dt): its error counts against |quantity|/dt
+                scale = max(scale, np.abs(want[:, blk - 1, gi]).max() / dt)
             err = np.abs(got[:, blk, gi] - want[:, blk, gi]).max() / max(scale, 1e-300)
             assert err < bound, (case, blk, gi, err)

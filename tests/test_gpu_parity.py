@@ -211,37 +211,17 @@ def test_time_step_matches_oracle(torch_dev):
         assert dt == pytest.approx(ref, rel=1e-14), kw
 
 
-@pytest.mark.parametrize("scheme,nonlinear", [("gks2", True), ("gks2", False), ("cgks5", False)])
+@pytest.mark.parametrize("scheme,nonlinear", [("gks2", True), ("gks2", False), ("cgks5", False),
+                                              ("cgks5", True)])
 def test_tgv16_twenty_steps_match_oracle(torch_dev, scheme, nonlinear):
     """The parity gate: Taylor-Green vortex 16^3, Ma 0.1, Re 1600, Pr 0.72,
-    CFL 0.3, FP64, 20 steps, within 1e-11 (the subsonic case of Sec. 4.1
-    runs the linear schemes; GKS-2nd also with its limiter)."""
+    CFL 0.3, FP64, 20 steps, within 1e-11, for both schemes, linear (as the
+    subsonic case of Sec. 4.1 runs them) and nonlinear (GKS-2nd with its
+    limiter, CGKS-5th with GENO)."""
     Q, G, grid = wl.taylor_green(16)
     eq, eg, s = run_parity(torch_dev, Q, G, grid, 20, scheme=scheme, nonlinear=nonlinear)
     assert eq < TOL and eg < TOL, (eq, eg)
     assert s.status() == 0
-
-
-def test_tgv16_nonlinear_cgks_matches_oracle(torch_dev):
-    """Nonlinear CGKS-5th on the same workload: 5 steps within 1e-11; after
-    20 steps no further from the oracle than the oracle is from itself when
-    its input is perturbed by 1e-14 (relative, seeded) -- the GENO blend
-    (chi, the weights w_m ~ IS_m^-5) amplifies rounding differences by a
-    factor ~2-5 per step on this under-resolved grid, in any implementation,
-    while the linear scheme damps them."""
-    torch, dev = torch_dev
-    Q, G, grid = wl.taylor_green(16)
-    eq, eg, _ = run_parity(torch_dev, Q, G, grid, 5, scheme="cgks5", nonlinear=True)
-    assert eq < TOL and eg < TOL, (eq, eg)
-    eq20, eg20, _ = run_parity(torch_dev, Q, G, grid, 20, scheme="cgks5", nonlinear=True)
-    P = oparams(grid, scheme="cgks5", nonlinear=True)
-    Qa, Ga = Q.copy(), G.copy()
-    oracle.run(P, Qa, Ga, nsteps=20)
-    rng = np.random.default_rng(2024)
-    Qb, Gb = Q * (1 + 1e-14 * rng.uniform(-1, 1, Q.shape)), G.copy()
-    oracle.run(P, Qb, Gb, nsteps=20)
-    sq, sg = state_err(Qb, Qa), state_err(Gb, Ga)
-    assert eq20 <= 10 * sq + TOL and eg20 <= 10 * sg + TOL, (eq20, sq, eg20, sg)
 
 
 @pytest.mark.parametrize("scheme", ["gks2", "cgks5"])
