@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["flux.cu", "recon.cu", "recon_fp64.cu", "update.cu", "capi.cu", "noalloc.cu", "mlp.cu", "ensemble.cu"]
+CU_SOURCES = ["flux.cu", "recon.cu", "recon_fp64.cu", "update.cu", "capi.cu", "noalloc.cu", "mlp.cu", "ensemble.cu", "peak.cu"]
 CPP_SOURCES = ["tables.cpp"]
 HEADERS = ["basis.h", "common.cuh", "ff.cuh", "recon_common.cuh"]
 # recon.cu (the mixed-precision reconstruction): no implicit multiply-add

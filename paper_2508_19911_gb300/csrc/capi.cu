@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "basis.h"
 #include "common.cuh"
@@ -33,6 +34,14 @@ struct gks_ctx {
     double *partials;
     int diag_blocks;
     double *hQ, *hG, *hT;  // device state of gks_step_host (allocated on its first call)
+    int timing;            // gks_kernel_timing: record events around the step's launches
+    cudaEvent_t t_open;    // event before the launch being timed
+    std::vector<struct KernelRec> *t_recs;  // (kind, start, end) of the timed launches
+};
+
+struct KernelRec {
+    int kind;
+    cudaEvent_t e0, e1;
 };
 
 namespace {
@@ -60,6 +69,35 @@ double *red_slot(gks_ctx *c) { return c->scal + 1; }
 double *diag_slot(gks_ctx *c) { return c->scal + 3; }
 
 int launch_ok(int rc) { return rc == 0 ? GKS_OK : (rc == -1 ? GKS_ERR_ARG : GKS_ERR_CUDA); }
+
+// kernel timing (gks_kernel_timing): an event on the context's stream
+// before and after each timed launch; no synchronisation
+enum { kTimeRecon = 0, kTimeFlux = 1, kTimeUpdate = 2, kTimeDt = 3 };
+void time_open(gks_ctx *c) {
+    if (!c->timing) return;
+    if (cudaEventCreate(&c->t_open) != cudaSuccess) { c->t_open = nullptr; return; }
+    cudaEventRecord(c->t_open, c->stream);
+}
+void time_close(gks_ctx *c, int kind) {
+    if (!c->timing || !c->t_open) return;
+    cudaEvent_t e1;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(c->t_open);
+        c->t_open = nullptr;
+        return;
+    }
+    cudaEventRecord(e1, c->stream);
+    c->t_recs->push_back(KernelRec{kind, c->t_open, e1});
+    c->t_open = nullptr;
+}
+void time_clear(gks_ctx *c) {
+    if (!c->t_recs) return;
+    for (const KernelRec &r : *c->t_recs) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    c->t_recs->clear();
+}
 
 }  // namespace
 
@@ -114,6 +152,8 @@ void gks_destroy(gks_ctx *c) {
     cudaFree(c->hQ);
     cudaFree(c->hG);
     cudaFree(c->hT);
+    time_clear(c);
+    delete c->t_recs;
     if (prev >= 0) cudaSetDevice(prev);
     delete c;
 }
@@ -257,8 +297,12 @@ int stage_faces(gks_ctx *c, const double *Q, const double *G, const double *dt) 
     if ((rc = make_views(c, Q, G))) return rc;
     if (!c->slab_planes) {
         const Slab S = whole_grid(c->g);
-        if ((rc = recon_any(c, S, Q, G, c->fs)) || (rc = flux_any(c, S, Q, c->fs, dt, c->frec)))
-            return rc;
+        time_open(c);
+        if ((rc = recon_any(c, S, Q, G, c->fs))) return rc;
+        time_close(c, kTimeRecon);
+        time_open(c);
+        if ((rc = flux_any(c, S, Q, c->fs, dt, c->frec))) return rc;
+        time_close(c, kTimeFlux);
         return 0;
     }
     const int nz = c->g.nz;
@@ -271,8 +315,12 @@ int stage_faces(gks_ctx *c, const double *Q, const double *G, const double *dt) 
         S.p0 = 1;
         S.pad = 0;
         S.nb = nxy * S.nzb;
-        if ((rc = recon_any(c, S, Q, G, c->fs)) || (rc = flux_any(c, S, Q, c->fs, dt, c->frec)))
-            return rc;
+        time_open(c);
+        if ((rc = recon_any(c, S, Q, G, c->fs))) return rc;
+        time_close(c, kTimeRecon);
+        time_open(c);
+        if ((rc = flux_any(c, S, Q, c->fs, dt, c->frec))) return rc;
+        time_close(c, kTimeFlux);
     }
     return 0;
 }
@@ -313,21 +361,30 @@ int gks_step(gks_ctx *c, double *Q, double *G, int nsteps, double t_stop, double
     if (cgks && !G) return GKS_ERR_ARG;
     double *dt = dt_slot(c);
     for (int s = 0; s < nsteps; ++s) {
+        time_open(c);
         int rc = launch_dt(c->g, c->P, Q, red_slot(c), dt, t_dev, t_stop, c->stream);
         if (rc) return GKS_ERR_CUDA;
+        time_close(c, kTimeDt);
         if (!cgks) {
-            if ((rc = stage_faces(c, Q, nullptr, dt)) ||
-                (rc = launch_update(c->g, c->P, 0, c->frec, dt, Q, nullptr, nullptr, nullptr,
+            if ((rc = stage_faces(c, Q, nullptr, dt))) return GKS_ERR_CUDA;
+            time_open(c);
+            if ((rc = launch_update(c->g, c->P, 0, c->frec, dt, Q, nullptr, nullptr, nullptr,
                                     nullptr, nullptr, c->status, c->stream)))
                 return GKS_ERR_CUDA;
+            time_close(c, kTimeUpdate);
         } else {
-            if ((rc = stage_faces(c, Q, G, dt)) ||
-                (rc = launch_update(c->g, c->P, 1, c->frec, dt, Q, G, c->Qs, c->Gs, c->Acc, c->S1,
-                                    c->status, c->stream)) ||
-                (rc = stage_faces(c, c->Qs, c->Gs, dt)) ||
-                (rc = launch_update(c->g, c->P, 2, c->frec, dt, Q, G, c->Qs, c->Gs, c->Acc, c->S1,
+            if ((rc = stage_faces(c, Q, G, dt))) return GKS_ERR_CUDA;
+            time_open(c);
+            if ((rc = launch_update(c->g, c->P, 1, c->frec, dt, Q, G, c->Qs, c->Gs, c->Acc, c->S1,
                                     c->status, c->stream)))
                 return GKS_ERR_CUDA;
+            time_close(c, kTimeUpdate);
+            if ((rc = stage_faces(c, c->Qs, c->Gs, dt))) return GKS_ERR_CUDA;
+            time_open(c);
+            if ((rc = launch_update(c->g, c->P, 2, c->frec, dt, Q, G, c->Qs, c->Gs, c->Acc, c->S1,
+                                    c->status, c->stream)))
+                return GKS_ERR_CUDA;
+            time_close(c, kTimeUpdate);
         }
     }
     if (dt_host_last) {
@@ -455,12 +512,42 @@ int gks_recon_matrix(double *R) {
     return rc == 0 ? GKS_OK : GKS_ERR_ARG;
 }
 
+int gks_kernel_timing(gks_ctx *c, int on) {
+    if (!c || (on != 0 && on != 1)) return GKS_ERR_ARG;
+    if (on) {
+        if (!c->t_recs) {
+            c->t_recs = new (std::nothrow) std::vector<KernelRec>();
+            if (!c->t_recs) return GKS_ERR_NOMEM;
+        }
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return GKS_ERR_CUDA;
+        time_clear(c);
+    }
+    c->timing = on;
+    return GKS_OK;
+}
+
+int gks_kernel_times(gks_ctx *c, double *ms, long long *launches) {
+    if (!c || !ms || !launches) return GKS_ERR_ARG;
+    for (int k = 0; k < 4; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    if (!c->t_recs) return GKS_OK;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return GKS_ERR_CUDA;
+    for (const KernelRec &r : *c->t_recs) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, r.e0, r.e1) != cudaSuccess) return GKS_ERR_CUDA;
+        ms[r.kind] += t;
+        launches[r.kind] += 1;
+    }
+    return GKS_OK;
+}
+
 int gks_status(gks_ctx *c, int *status) {
     if (!c || !status) return GKS_ERR_ARG;
     if (cudaMemcpyAsync(status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
             cudaSuccess ||
-        cudaMemsetAsync(c->status, 0, sizeof(int), c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->skips, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
+        cudaMemsetAsync(c->status, 0, sizeof(int), c->stream) != cudaSuccess) {
         cudaStreamSynchronize(c->stream);  // no copy into *status left in flight
         return GKS_ERR_CUDA;
     }

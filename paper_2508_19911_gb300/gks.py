@@ -71,6 +71,9 @@ SIGNATURES = {
     "gks_status": (_I, [_VP, ctypes.POINTER(_I)]),
     "gks_recon_matrix": (_I, [ctypes.POINTER(_D)]),
     "gks_diagnostics_noalloc": (_I, [_VP, _VP, _I, _I, _I, _D, _D, _D, _D, _D, _I, _D, _VP, _VP]),
+    "gks_fma_rate": (_I, [_I, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "gks_kernel_timing": (_I, [_VP, _I]),
+    "gks_kernel_times": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
     "gks_mlp_nparams": (_I, []),
     "gks_indicator_dump": (_I, [_VP, _VP, _VP, ctypes.c_float, _VP, _VP, _VP]),
     "gks_mlp_loss_grad": (_I, [_VP, _VP, _VP, _I, ctypes.c_longlong, ctypes.c_float, _VP, _VP, _VP]),
@@ -116,6 +119,17 @@ def lib(build_if_missing: bool = True):
 def _check(rc, what):
     if rc != GKS_OK:
         raise GksError(rc, what)
+
+
+def fma_rate(precision="fp64", stream=None):
+    """Measured FMA throughput of the current device (FLOP/s, launch ms):
+    precision "fp64" (double FMAs) or "fp32" (float FMAs)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    flops, ms = _D(0.0), _D(0.0)
+    _check(lib().gks_fma_rate(0 if precision == "fp64" else 1, _VP(st.cuda_stream),
+                              ctypes.byref(flops), ctypes.byref(ms)), "gks_fma_rate")
+    return flops.value, ms.value
 
 
 def mlp_nparams() -> int:
@@ -327,6 +341,20 @@ class Solver:
         st = _I(0)
         _check(lib().gks_status(self.ctx, ctypes.byref(st)), "gks_status")
         return st.value
+
+    KERNEL_KINDS = ("recon", "flux", "update", "dt")
+
+    def kernel_timing(self, on=True):
+        """Start (discarding earlier records) or stop recording the device
+        time of every launch gks_step makes."""
+        _check(lib().gks_kernel_timing(self.ctx, 1 if on else 0), "gks_kernel_timing")
+
+    def kernel_times(self):
+        """{kind: (summed ms, launches)} of the recorded launches."""
+        ms = (_D * 4)()
+        n = (ctypes.c_longlong * 4)()
+        _check(lib().gks_kernel_times(self.ctx, ms, n), "gks_kernel_times")
+        return {k: (ms[i], n[i]) for i, k in enumerate(self.KERNEL_KINDS)}
 
 
 class Ensemble:

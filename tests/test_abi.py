@@ -58,3 +58,11 @@ def test_init_rejects_bad_arguments_before_touching_the_gpu():
         assert not ctx.value
     assert L.gks_step(None, None, None, 1, 0.0, None, None) == gks.GKS_ERR_ARG
     assert L.gks_step_host(None, None, None, 1, 0.0, None) == gks.GKS_ERR_ARG
+
+
+def test_fma_rate_rejects_bad_arguments_before_touching_the_gpu():
+    from paper_2508_19911_gb300 import gks
+    L = gks.lib()
+    f, ms = ctypes.c_double(), ctypes.c_double()
+    assert L.gks_fma_rate(7, None, ctypes.byref(f), ctypes.byref(ms)) == gks.GKS_ERR_ARG
+    assert L.gks_fma_rate(0, None, None, ctypes.byref(ms)) == gks.GKS_ERR_ARG
