@@ -347,17 +347,18 @@ int gks_fma_rate(int precision, void *cuda_stream, double *flops, double *ms);
  * thread, a checkpoint hook, code that holds only device pointers and no
  * gks_ctx). Large grids leave little free HBM, so an allocation made just to
  * sample diagnostics may fail or evict the simulation's own buffers.
- * Computes the same 12 values as gks_diagnostics (equal up to the order of
- * the floating-point sums) for the state Q / gradQ (gradQ may be NULL:
+ * Computes the same 12 values as gks_diagnostics (the same kernels and
+ * block count: equal bit for bit) for the state Q / gradQ (gradQ may be NULL:
  * central differences) of an nx x ny x nz periodic grid of extents Lx, Ly,
  * Lz, gas constant gamma, viscosity mu (Sutherland's law when mu_law = 1,
  * temperature normalised by T_ref). out_dev: caller-owned DEVICE memory for
  * 12 doubles, written asynchronously on cuda_stream (a cudaStream_t or
  * NULL); the call does not synchronise and reads no status word.
- * Scratch: a file-scope device array of 3 MiB (one block of 12 partial
- * results per 4096 cells) that every GPU which loads the library holds
- * until the process exits; grids above 2^27 cells (512^3) are rejected with
- * GKS_ERR_ARG. Every call overwrites the slots it later reads, so nothing
+ * Scratch: a file-scope device array of 57 KiB (12 partial results for
+ * each of at most 608 reduction blocks, whatever the grid size) that every
+ * GPU which loads the library holds until the process exits; grids above
+ * 2^31 cells (the limit of gks_init) are rejected with GKS_ERR_ARG.
+ * Every call overwrites the slots it later reads, so nothing
  * has to be cleared, but all calls on a device share the array: calls that
  * overlap on the GPU (other streams, other threads) race and must be
  * serialised by the caller. The first call on each device looks up the

@@ -133,6 +133,10 @@ int launch_dt(const GridDesc &g, const PhysParams &P, const double *Q, double *r
 int launch_update(const GridDesc &g, const PhysParams &P, int stage, const double *frec,
                   const double *dt_dev, double *Q, double *G, double *Qs, double *Gs,
                   double *Acc, double *S1, int *status, cudaStream_t s);
+// diagnostics: nblocks (1..kDiagMaxBlocks) blocks write kDiagSlots partial
+// results each to partials, one block reduces them into out_dev
+constexpr int kDiagSlots = 12;
+constexpr int kDiagMaxBlocks = 152 * 4;
 int launch_diagnostics(const GridDesc &g, const PhysParams &P, const double *Q,
                        const double *G, double *partials, int nblocks, double *out_dev,
                        cudaStream_t s);

@@ -13,8 +13,9 @@
 //     A = Q + dt L + dt^2/6 dL/dt and S1 = Gauss sum of Q_G^n; stage 2 writes
 //     Q^{n+1} = A + dt^2/3 dL*/dt and grad Q^{n+1} = S1 + dt Gauss sum of
 //     dQ_G*/dt.
-//   diagnostics (Sec. 4.1/4.2): per-block partial sums/minima/maxima in a
-//     fixed order, then one block reduces the partials in a fixed order
+//   diagnostics (Sec. 4.1/4.2): per-block partial sums/minima/maxima
+//     (warp shuffles, then across the block's warps), then one block
+//     reduces the partials the same way; a fixed order throughout
 //     (deterministic, no floating-point atomics).
 #include <cmath>
 
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(kBlock) update_ens_kernel(const EnsInst *__res
 // ---- diagnostics ---------------------------------------------------------
 // slots: 0 ek, 1 eps_S, 2 eps_D, 3 min rho, 4 min p, 5..9 sum Q, 10 bad,
 // 11 max speed; 3, 4 are minima, 11 a maximum, the rest sums
-constexpr int kDiag = 12;
+constexpr int kDiag = kDiagSlots;
 
 __device__ __forceinline__ double combine(int s, double a, double b) {
     if (s == 3 || s == 4) return fmin(a, b);
@@ -266,22 +267,29 @@ __device__ __forceinline__ double identity_of(int s) {
     return 0.0;
 }
 
+// block reduction of the 12 slots: each warp combines its 32 lanes with
+// shuffles (a fixed butterfly: deterministic), warp leaders meet in shared
+// memory, warp 0 combines the kBlock/32 warp results; thread 0 writes dst
 __device__ void block_reduce_store(double acc[kDiag], double *dst) {
-    __shared__ double sh[kDiag][kBlock];
+    constexpr int kWarps = kBlock / 32;
+    __shared__ double sh[kDiag][kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int s = 0; s < kDiag; ++s) sh[s][threadIdx.x] = acc[s];
-    __syncthreads();
-    for (int w = kBlock / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) {
+    for (int s = 0; s < kDiag; ++s) {
+        double v = acc[s];
 #pragma unroll
-            for (int s = 0; s < kDiag; ++s)
-                sh[s][threadIdx.x] = combine(s, sh[s][threadIdx.x], sh[s][threadIdx.x + w]);
-        }
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) v = combine(s, v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) sh[s][warp] = v;
     }
-    if (threadIdx.x == 0) {
+    __syncthreads();
+    if (warp == 0) {
 #pragma unroll
-        for (int s = 0; s < kDiag; ++s) dst[s] = sh[s][0];
+        for (int s = 0; s < kDiag; ++s) {
+            double v = lane < kWarps ? sh[s][lane] : identity_of(s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = combine(s, v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) dst[s] = v;
+        }
     }
 }
 
@@ -420,7 +428,7 @@ int launch_update_ens(const EnsInst *inst, const EnsItem *items, int nitems, int
 
 int diagnostics_blocks(const GridDesc &g) {
     long long blocks = (g.n + kBlock - 1) / kBlock;
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks > kDiagMaxBlocks) blocks = kDiagMaxBlocks;
     return (int)blocks;
 }
 

@@ -145,3 +145,24 @@ def test_ensemble_dump_equals_solo_dumps(env):
         assert torch.equal(x[:, 5 * o: 5 * (o + c)], xs)
         assert torch.equal(chi[5 * o: 5 * (o + c)], chis)
         assert torch.equal(y[5 * o: 5 * (o + c)], ys)
+
+
+def test_set_tile_right_after_an_asynchronous_step(env):
+    """set_tile rebuilds the work list while the previous step's persistent
+    kernels may still run on the ensemble's stream: the result must equal a
+    run with a host synchronisation in between."""
+    torch, dev, gks = env
+    insts = small_instances()
+    runs = []
+    for sync in (True, False):
+        e = build(env, insts, "fp64")
+        e.set_tile(512)
+        e.step(2, graph=False)
+        if sync:
+            torch.cuda.synchronize()
+        e.set_tile(2048)
+        e.step(2, graph=False)
+        torch.cuda.synchronize()
+        runs.append((e.Q.clone(), e.G.clone()))
+        e.close()
+    assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])

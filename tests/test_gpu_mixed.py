@@ -162,7 +162,7 @@ def restore_offsets(torch, fs_mixed, Qd):
     return out
 
 
-@pytest.mark.parametrize("case", ["tgv48", "hit64", "tgv_ma2_32", "sod256"])
+@pytest.mark.parametrize("case", ["tgv48", "hit64", "hit64_x2", "tgv_ma2_32", "sod256"])
 def test_mixed_flux_shell_accuracy(torch_dev, case):
     """The mixed flux (float-float W0, X1, D = X1 - X4; FP32 core) against
     the FP64 flux kernel on identical face states, per record block and
@@ -183,6 +183,11 @@ def test_mixed_flux_shell_accuracy(torch_dev, case):
     elif case == "hit64":
         Q, G, grid, _ = wl.isotropic_turbulence(64, Mt=0.5, k0=2.0, seed=303)
         kw = dict(mu=1e-3)
+    elif case == "hit64_x2":
+        # the 512^3 turbulence's regime on 64^3: same cells per wavelength
+        # (k0 8 -> 1) and dt/tau ~ 2 (mu 1e-3 -> 8e-3)
+        Q, G, grid, _ = wl.isotropic_turbulence(64, Mt=0.5, k0=1.0, seed=303)
+        kw = dict(mu=8e-3)
     elif case == "tgv_ma2_32":
         Q, G, grid = wl.taylor_green_supersonic(32)
         kw = dict(mu=math.sqrt(1.4) * 2 / 1600, mu_law=1, Pr=0.7)

@@ -401,3 +401,39 @@ def test_edge_weight_is_near_the_condition_number_minimum():
     best = min(cond(x) for x in grid)
     assert cond(0.1) <= 1.01 * best, (cond(0.1), best)
     assert cond(1.0) > 5 * cond(0.1)
+
+
+def _vk_smooth_min(y, e):
+    """Venkatakrishnan's limiter as the smooth minimum of (1, y) in the
+    ratio y = Delta_+ / Delta_2 of the admissible to the unlimited
+    increment, with the smoothing e = eps^2 / Delta_2^2:
+    phi = (y^2 + 2 y + e) / (y^2 + y + 2 + e)."""
+    return (y * y + 2.0 * y + e) / (y * y + y + 2.0 + e)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_venkatakrishnan_limiter_interior_values(orc, seed):
+    """The limiter of Sec. 3.3 away from its limits: a cell with neighbours
+    only along x (central gradient b = (q_+ - q_-)/2), so that the two x
+    faces carry the unlimited increments +-b/2 and the admissible ones
+    max - q0 and min - q0 (the y and z faces have none: phi = 1 there).
+    phi0 = the smaller of the two faces' smooth minima, with eps^2 = h^3
+    (reading R9); both signs of the increment are covered by each draw."""
+    rng = np.random.default_rng(seed)
+    for _ in range(5):
+        h = 10.0 ** rng.uniform(-2.0, -0.3)
+        a, b = rng.uniform(-1.0, 1.0, 2)
+        q7 = np.zeros((7, 5))
+        q7[1, :] = a        # -x neighbour
+        q7[2, :] = b        # +x neighbour
+        _, phi = orc.recon2_cell(q7.ravel(), (h, h, h), nonlinear=1)
+        grad = 0.5 * (b - a)
+        qmax, qmin = max(0.0, a, b), min(0.0, a, b)
+        e2 = h ** 3
+        want = 1.0
+        for d2 in (0.5 * grad, -0.5 * grad):  # the +x and -x faces
+            if d2 == 0.0:
+                continue
+            dp = qmax if d2 > 0 else qmin
+            want = min(want, _vk_smooth_min(dp / d2, e2 / (d2 * d2)))
+        np.testing.assert_allclose(phi, want, rtol=1e-13, atol=0)
