@@ -6,7 +6,8 @@
 // `tile` cells; each phase of a time step (dt reduction, reconstruction,
 // flux, update) is ONE persistent launch whose blocks stride over the work
 // items of all instances, each instance with its own dt, time and physics.
-// A whole time step (8 launches) is captured once into a CUDA graph and
+// A whole time step (8 launches; 12 in mixed precision, which adds the two
+// views of the state per stage) is captured once into a CUDA graph and
 // replayed; the autotuner times the graph for a set of tile sizes on a
 // scratch copy of the state and keeps the fastest. The same machinery
 // dumps the learned indicator's training data from all instances.
@@ -73,6 +74,10 @@ void drop_graph(gks_ensemble *e) {
 }
 
 int build_items(gks_ensemble *e, int tile) {
+    // the persistent kernels of earlier steps may still be reading the old
+    // item list on e->s (a non-blocking stream, which the synchronous copy
+    // below does not order against): let them finish first
+    if (e->s && cudaStreamSynchronize(e->s) != cudaSuccess) return GKS_ERR_CUDA;
     e->items.clear();
     for (int i = 0; i < e->ninst; ++i)
         for (long long c0 = 0; c0 < e->inst[i].g.n; c0 += tile) {

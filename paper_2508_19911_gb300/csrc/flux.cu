@@ -146,11 +146,14 @@ __device__ __forceinline__ void time_integrals(double T, double tau, double c[6]
     const double E = -expm1(-x);
     const double t2 = tau * tau;
     if (x < 1.0) {
+        // terms to n = 20: x^21/21! < 2e-20 of the smallest sum for x < 1;
+        // each step multiplies by the rounded reciprocal 1/n (an FP64
+        // division is a multi-instruction sequence, 18 of them per call)
         double term = 0.5 * x * x;  // (-1)^n x^n / n! at n = 2
         double s1 = term, s2 = 0.0, s3 = 0.0;
 #pragma unroll
-        for (int n = 3; n <= 26; ++n) {
-            term *= -x / n;
+        for (int n = 3; n <= 20; ++n) {
+            term *= -x * (1.0 / n);  // 1/n folds to a constant once unrolled
             s1 += term;
             s2 += (n - 2) * term;
             s3 -= term;
@@ -233,9 +236,10 @@ __device__ __forceinline__ void time_coefficients(double dt, double tau, double 
 }
 
 // The closed forms above in FP32 (for the mixed flux, whose coefficients
-// meet FP32 moments): for x = dt/tau >= 4 their relative error is below
-// 1e-6 (1e-7 for x >= 30), checked against a 50-digit reference; it grows
-// to 1e-5 at x = 1/2 through the cancellation in al_1, al_2.
+// meet FP32 moments): for x = dt/tau >= 1/2 their error is at most
+// ~1e-7 tau (tau^2/dt for be), FP32 rounding of the coefficients' own
+// scale, checked against a 50-digit reference (relative errors of the
+// small al_1, al_2 reach 8e-6 at x = 1/2 and grow like 1/x^2 below it).
 __device__ __forceinline__ void time_coefficients_f(float dt, float tau, float al[6], float be[6]) {
     const float a = -expm1f(-0.5f * dt / tau), b = 1.0f - a;
     const float idt = 1.0f / dt;
@@ -706,7 +710,7 @@ __device__ void flux_point_mixed(const PhysParams &P, const ff Ql[5], const floa
     equilibrium_terms<false>(Zf, Nf, c4f, dW0, X, q, dtW0);  // a Maxwellian carries no heat flux: q1 = 0
 
     // collision time (Sec. 4) in FP32; time coefficients in FP32 for
-    // dt >= 4 tau, else from the FP64 closed forms (dt >= tau/100) or series
+    // dt >= tau/2, else from the FP64 closed forms (dt >= tau/100) or series
     const float dpr = fabsf(ff_sub(L.p, R.p).hi / ff_add(L.p, R.p).hi);
     const float dtf = (float)dt;
     float tau;
@@ -721,7 +725,7 @@ __device__ void flux_point_mixed(const PhysParams &P, const ff Ql[5], const floa
         tau = mu / Zf.p + (float)P.C_tau * dpr * dtf;
     }
     float al[6], be[6];
-    if (tau > 0.0f && dtf >= 4.0f * tau) {
+    if (tau > 0.0f && dtf >= 0.5f * tau) {
         time_coefficients_f(dtf, tau, al, be);
     } else {
         double ald[6], bed[6];
@@ -960,7 +964,7 @@ __global__ void __launch_bounds__(128) flux_points_kernel(PhysParams P, const do
                                                           const double *__restrict__ sr_, int n,
                                                           const double *__restrict__ dt_dev,
                                                           double *__restrict__ out_, int *status) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double dt = *dt_dev;
     double sl[20], sr[20], out[30];

@@ -19,12 +19,12 @@ from . import gks
 from . import workloads as wl
 
 # label: GENO's chi within LABEL_EPS of 1; loss weight of label-0 samples;
-# skip threshold on the network's sigmoid output (chosen on held-out data
-# so that the kinetic-energy error against the plain nonlinear path stays
-# below 1e-5)
+# skip threshold on the network's sigmoid output (chosen on held-out data:
+# 0.9 skipped 47% of the smooth samples but 5% of the others, 0.99 almost
+# nothing; 0.97 in between keeps the false skips near 1%)
 LABEL_EPS = 1e-3
 NEG_WEIGHT = 1.0
-THETA = 0.9
+THETA = 0.97
 
 
 D = 63
