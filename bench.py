@@ -3,9 +3,14 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step = one full time step of the hot path (dt on the device,
-reconstruction, gas-kinetic flux, cell update; two stages for CGKS-5th) on
-the Taylor-Green vortex (Sec. 4.1; Ma 0.1, Re 1600, gamma 1.4, Pr 0.72,
-CFL 0.3) with synthetic cell-averaged initial data, FP64, nonlinear scheme.
+reconstruction, gas-kinetic flux, cell update; two stages for CGKS-5th).
+Default workload: CGKS-5th, FP64, nonlinear, on decaying isotropic
+turbulence at 512^3 (Mt 0.5, k0 8, seed 103, mu 1e-3; gamma 1.4, Pr 0.72,
+CFL 0.3) with synthetic cell-averaged initial data, inputs resident in HBM;
+the mixed-precision and mixed + learned-indicator paths of the same
+workload are reported under "variants" with their kinetic-energy error
+against FP64 after the same steps. --workload tgv runs the Taylor-Green
+vortex instead (Sec. 4.1; Ma 0.1, Re 1600; 128^3 by default).
 Metric: cell-stage updates/s (cells x stages x steps / device time).
 
 Multi-GPU: replicas only (the path does not shard on one box): every rank
@@ -30,32 +35,32 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-stage updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-SM_COUNT = 152
-FP64_FLOP_PER_CLK_PER_SM = 4     # nominal 1.25 TFLOP/s / (152 SMs x 2.07 GHz)
-FP32_FLOP_PER_CLK_PER_SM = 256   # 128 FP32 lanes x FMA
-SM_MAX_MHZ_NOMINAL = 2070.0
 HBM_FALLBACK_GBS = 6800.0
 # Work per unit of the hot kernels, from ncu's SASS op counters
 # (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul,ffma,fadd,fmul}_pred_on,
-# an FMA counted as 2 FLOP) and dram__bytes_{read,write} on TGV 64^3 (see
-# profiles/): FP64 and FP32 FLOP, algorithmic bytes (state and face-state
-# buffers read and written once) and measured DRAM bytes. A unit is one cell
-# for a reconstruction, one face Gauss point for a flux kernel (12 per cell
-# for CGKS-5th: 3 faces x 4 points; 3 per cell for GKS-2nd).
+# an FMA counted as 2 FLOP) and dram__bytes_{read,write} of one launch on
+# the 64^3 stand-in of the 512^3 turbulence (the same cells per wavelength
+# and dt/tau, so the flux takes the same branches; profiles/opcount_*.md):
+# FP64 and FP32 FLOP, algorithmic bytes
+# (state and face-state buffers read and written once) and measured DRAM
+# bytes. A unit is one reconstructed cell for a reconstruction, one face
+# Gauss point for a flux kernel (12 per cell for CGKS-5th: 3 faces x 4
+# points; 3 per cell for GKS-2nd).
+_DRAM_NOTE = ("ncu dram__bytes_read+write per unit of one launch on a 64^3 grid, times "
+              "this launch's units (the traffic grows with the units: one pass over state "
+              "and face buffers that exceed L2)")
 KERNEL_OPS = {
-    "recon5": {"fp64": 14159.0, "fp32": 130.0, "bytes": 160 + 3840, "dram": 3771.7},
-    "flux_cgks5": {"fp64": 5087.0, "fp32": 14.0, "bytes": (3840 + 720) / 12, "dram": 386.9},
-    "recon5_mixed": {"fp64": 0.0, "fp32": 13281.5, "bytes": 40 + 60 + 1920, "dram": 1791.5},
-    "flux_cgks5_mixed": {"fp64": 21.5, "fp32": 8938.1, "bytes": (1920 + 40 + 720) / 12,
-                         "dram": 225.5},
+    "recon5": {"fp64": 17062.0, "fp32": 130.0, "bytes": 160 + 3840, "dram": 3824.7,
+               "dram_note": _DRAM_NOTE},
+    "flux_cgks5": {"fp64": 5575.5, "fp32": 58.0, "bytes": (3840 + 720) / 12, "dram": 386.3,
+                   "dram_note": _DRAM_NOTE},
+    "recon5_mixed": {"fp64": 0.0, "fp32": 16181.2, "bytes": 40 + 60 + 1920, "dram": 1788.1,
+                     "dram_note": _DRAM_NOTE},
+    "flux_cgks5_mixed": {"fp64": 21.5, "fp32": 9628.4, "bytes": (1920 + 40 + 720) / 12,
+                         "dram": 225.4, "dram_note": _DRAM_NOTE},
 }
 KERNEL_OPS["recon5_learned"] = KERNEL_OPS["recon5_mixed"]
 KERNEL_OPS["flux_cgks5_learned"] = KERNEL_OPS["flux_cgks5_mixed"]
-# kernels of my own per step: dt (reduction + finalisation), then per stage
-# reconstruction, flux, update (+ mixed: the float-float split of Q for the
-# flux, and for CGKS-5th the FP32 gradient copy for the reconstruction)
-LAUNCHES_PER_STEP = {("cgks5", "fp64"): 8, ("cgks5", "mixed"): 12, ("gks2", "fp64"): 5,
-                     ("gks2", "mixed"): 6}
 
 
 def parse():
@@ -65,14 +70,18 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=None,
-                    help="cells per axis (default 128; --c2 64, --c3 256, --c5 512)")
+                    help="cells per axis (default 512; --workload tgv 128; --c2 64, --c3 256, "
+                         "--c5 512)")
     ap.add_argument("--scheme", default="cgks5", choices=["cgks5", "gks2"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--indicator", action="store_true",
                     help="mixed precision with the learned smoothness indicator (CGKS-5th)")
-    ap.add_argument("--workload", default="tgv", choices=["tgv", "hit"],
-                    help="tgv: Taylor-Green vortex (Ma 0.1, Re 1600); hit: decaying isotropic "
-                         "turbulence (Mt 0.5, k0 8, seed 103, mu 1e-3)")
+    ap.add_argument("--workload", default="hit", choices=["tgv", "hit"],
+                    help="hit: decaying isotropic turbulence (Mt 0.5, k0 8, seed 103, mu 1e-3); "
+                         "tgv: Taylor-Green vortex (Ma 0.1, Re 1600)")
+    ap.add_argument("--proxy-of", type=int, default=None,
+                    help="hit: a small grid standing in for this larger one (k0 and mu scaled "
+                         "so that cells per wavelength and dt/tau match; for op counts)")
     ap.add_argument("--slab-planes", type=int, default=0,
                     help="z-planes per reconstruction/flux slab (0: automatic)")
     ap.add_argument("--no-variants", action="store_true")
@@ -105,7 +114,8 @@ def parse():
                     help="--c2/--c3: write the sampled histories to this JSON file")
     args = ap.parse_args()
     if args.n is None:
-        args.n = 64 if args.c2 else 256 if args.c3 else 512 if args.c5 else 128
+        args.n = (64 if args.c2 else 256 if args.c3 else 512 if args.c5
+                  else 128 if args.workload == "tgv" else 512)
     return args
 
 
@@ -176,39 +186,51 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(scheme):
-    """The FP64 oracle as it stands, OpenMP over cells on all host cores,
-    on a bounded sample (about 15 s on 16 cores): the same Taylor-Green
-    workload at 48^3 (CGKS-5th) or 96^3 (GKS-2nd), 2 time steps."""
-    import oracle
+def sample_workload(args, n):
+    """The benchmark's workload at a size the CPU oracle finishes in seconds
+    (the same generator and parameters; only the grid is smaller)."""
     from paper_2508_19911_gb300 import workloads as wl
-    n = 48 if scheme == "cgks5" else 96
+    if getattr(args, "workload", "hit") == "tgv":
+        Q, G, grid = wl.taylor_green(n)
+        return Q, G, grid, 1.0 / 1600, "taylor_green"
+    Q, G, grid, _ = wl.isotropic_turbulence(n, Mt=0.5, k0=8.0, seed=103)
+    return Q, G, grid, 1e-3, "isotropic_turbulence"
+
+
+def cpu_baseline(args):
+    """The FP64 oracle as it stands, OpenMP over cells on all host cores,
+    on a bounded sample (about 15 s on 16 cores): the benchmark's workload
+    on a 48^3 grid (CGKS-5th; 96^3 for GKS-2nd), 2 time steps."""
+    import oracle
+    cg = args.scheme == "cgks5"
+    n = 48 if cg else 96
     steps = 2
-    Q, G, grid = wl.taylor_green(n)
+    Q, G, grid, mu, name = sample_workload(args, n)
     cores = os.cpu_count() or 1
-    P = oracle.params(n=grid.n, L=grid.L, scheme=1 if scheme == "cgks5" else 0,
-                      nonlinear=1, threads=cores)
-    oracle.run(P, Q.copy(), G.copy() if scheme == "cgks5" else None, nsteps=1)  # warm
+    P = oracle.params(n=grid.n, L=grid.L, scheme=1 if cg else 0, nonlinear=1, mu0=mu,
+                      threads=cores)
+    oracle.run(P, Q.copy(), G.copy() if cg else None, nsteps=1)  # warm
     t0 = time.perf_counter()
-    oracle.run(P, Q, G if scheme == "cgks5" else None, nsteps=steps)
+    oracle.run(P, Q, G if cg else None, nsteps=steps)
     el = time.perf_counter() - t0
-    stages = 2 if scheme == "cgks5" else 1
+    stages = 2 if cg else 1
     return {"value": n ** 3 * stages * steps / el, "unit": METRIC, "cores": cores,
             "kind": "oracle",
-            "sample": f"TGV {n}^3 {scheme} FP64 nonlinear, {steps} steps ({el:.1f} s)"}
+            "sample": f"{name} {n}^3 {args.scheme} FP64 nonlinear, {steps} steps ({el:.1f} s)"}
 
 
 def reference_arm(args, rank):
+    """The oracle timed on the host cores, each step a bounded sample of the
+    benchmark's workload (24^3 CGKS-5th, 48^3 GKS-2nd)."""
     if rank != 0:
         return None
-    steps_done, el_total = 0, 0.0
     import oracle
-    from paper_2508_19911_gb300 import workloads as wl
-    n = 24 if args.scheme == "cgks5" else 48
-    Q, G, grid = wl.taylor_green(n)
-    cores = os.cpu_count() or 1
     cg = args.scheme == "cgks5"
-    P = oracle.params(n=grid.n, L=grid.L, scheme=1 if cg else 0, nonlinear=1, threads=cores)
+    n = 24 if cg else 48
+    Q, G, grid, mu, name = sample_workload(args, n)
+    cores = os.cpu_count() or 1
+    P = oracle.params(n=grid.n, L=grid.L, scheme=1 if cg else 0, nonlinear=1, mu0=mu,
+                      threads=cores)
     for _ in range(args.warmup):
         oracle.run(P, Q, G if cg else None, nsteps=1)
     t0 = time.perf_counter()
@@ -221,10 +243,10 @@ def reference_arm(args, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"taylor_green_{n}^3_{args.scheme}_fp64_nonlinear",
-                   "note": "bounded CPU sample of the TGV workload"},
+        "config": {"workload": f"{name}_{n}^3_{args.scheme}_fp64_nonlinear",
+                   "note": f"bounded CPU sample of the {name} workload"},
         "cpu_baseline": {"value": val, "unit": "cell-stage/s", "cores": cores, "kind": "oracle",
-                         "sample": f"TGV {n}^3 {args.scheme} FP64, {args.steps} steps"},
+                         "sample": f"{name} {n}^3 {args.scheme} FP64, {args.steps} steps"},
         "e2e": {"value": val, "unit": "cell-stage/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -315,193 +337,244 @@ def time_kernel(torch, fn, reps, stream):
     return e0.elapsed_time(e1) / reps  # ms per launch
 
 
+def make_workload(args):
+    """Initial cell averages and gradients of the benchmark workload (host,
+    numpy; setup only) with its physics and a description."""
+    from paper_2508_19911_gb300 import workloads as wl
+    n = args.n
+    if args.workload == "tgv":
+        Qh, Gh, grid = wl.taylor_green(n)
+        return dict(Q=Qh, G=Gh, grid=grid, phys=dict(mu=1.0 / 1600), name="taylor_green",
+                    data="synthetic (Taylor-Green cell averages)",
+                    cfg={"Ma": 0.1, "Re": 1600})
+    k0 = 8.0 if args.proxy_of is None else 8.0 * n / args.proxy_of
+    mu = 1e-3 if args.proxy_of is None else 1e-3 * args.proxy_of / n
+    Qh, Gh, grid, info = wl.isotropic_turbulence(n, Mt=0.5, k0=k0, seed=103)
+    cfg = {"Mt": 0.5, "k0": k0, "seed": 103, "mu": mu,
+           "taylor_lambda": float(info["taylor_lambda"])}
+    if args.proxy_of is not None:
+        cfg["proxy_of"] = f"{args.proxy_of}^3 (same cells per wavelength and dt/tau)"
+    return dict(Q=Qh, G=Gh, grid=grid, phys=dict(mu=mu), name="isotropic_turbulence",
+                data="synthetic (seeded isotropic turbulence, E(k) ~ k^4 exp(-2 (k/k0)^2))",
+                cfg=cfg)
+
+
+def timed_steps(torch, solver, Q, G, warmup, steps, stream, clock_index):
+    """W untimed steps, then K steps timed with CUDA events on the solver's
+    stream, with the per-kernel launch times recorded inside the timed
+    region and the SM clocks sampled during it."""
+    for _ in range(warmup):
+        solver.step(Q, G, nsteps=1, sync=False)
+    torch.cuda.synchronize()
+    barrier_ranks()
+    solver.kernel_timing(True)
+    with ClockSampler(clock_index) as clk:
+        ms = time_steps(torch, solver, Q, G, steps, stream)
+    solver.kernel_timing(False)
+    kt = solver.kernel_times()
+    return ms, kt, clk.summary()
+
+
+def alu_peaks(torch, stream):
+    """Measured FMA throughput of this GPU (TFLOP/s), FP64 and FP32."""
+    from paper_2508_19911_gb300 import gks
+    f64, _ = gks.fma_rate("fp64", stream)
+    f32, _ = gks.fma_rate("fp32", stream)
+    return f64 / 1e12, f32 / 1e12
+
+
+def kernel_roofline(kind, ops, kt, units_total, peaks, hbm_peak, hbm_src, clocks):
+    """Roofline of one kernel from the launches recorded in the timed
+    region: achieved = work per unit x units processed / summed launch
+    time (the average launch's work over its average duration)."""
+    ms, launches = kt[kind]
+    sec = ms / 1e3
+    p64, p32 = peaks
+    a64 = ops["fp64"] * units_total / sec / 1e12
+    a32 = ops["fp32"] * units_total / sec / 1e12
+    hbm = ops["bytes"] * units_total / sec / 1e9
+    f64, f32 = a64 / p64, a32 / p32
+    r = {"kernel": ops["name"], "launches": launches, "ms_per_launch": ms / launches,
+         "units_per_launch": units_total / launches}
+    if f64 >= f32:  # the binding unit: the FP64 pipe unless the FP32 one is busier
+        r.update({"bound": "alu", "achieved": a64, "peak": p64, "unit": "TFLOP/s (FP64)",
+                  "frac": f64})
+    else:
+        r.update({"bound": "alu", "achieved": a32, "peak": p32, "unit": "TFLOP/s (FP32)",
+                  "frac": f32})
+    r.update({
+        "traffic": ops["dram"] * units_total / launches if ops.get("dram") else None,
+        "traffic_note": ops.get("dram_note"),
+        "fp64": {"achieved_tflops": a64, "peak_tflops": p64, "frac": f64},
+        "fp32": {"achieved_tflops": a32, "peak_tflops": p32, "frac": f32},
+        "hbm": {"achieved_gbs": hbm, "peak_gbs": hbm_peak, "frac": hbm / hbm_peak,
+                "peak_source": hbm_src},
+        "peak_note": "ALU peaks of measured: gks_fma_rate (independent FMA chains on every SM) "
+                     f"during this run, SM clock {clocks.get('sm_mhz')} MHz; HBM peak of measured "
+                     "copy bandwidth (MEASURED_PEAKS.json)"})
+    return r
+
+
+def path_rooflines(kt, scheme, prec, cells, nxy, slab, stages, steps, peaks, clocks):
+    """Rooflines of the reconstruction and flux kernels of one path and the
+    dominant one of the two (the larger share of the recorded time)."""
+    pk = measured_peaks()
+    hbm_peak = pk.get("hbm_gbs") or HBM_FALLBACK_GBS
+    hbm_src = "MEASURED_PEAKS.json" if pk.get("hbm_gbs") else "fallback"
+    cg = scheme == "cgks5"
+    K = 4 if cg else 1
+    sfx = {"fp64": "", "mixed": "_mixed", "learned": "_learned"}[prec]
+    out = {}
+    # flux: every stage computes the faces of every cell (3 axes x K points)
+    # reconstruction: every stage reconstructs every cell, and each z-slab
+    # also the plane below it
+    nslabs = 0 if not slab else -(-(cells // nxy) // slab)
+    units = {"flux": 3 * K * cells * stages * steps,
+             "recon": (cells + nslabs * nxy) * stages * steps}
+    names = {"flux": ("flux_cgks5" if cg else "flux_gks2") + sfx,
+             "recon": ("recon5" if cg else "recon2") + sfx}
+    for kind in ("recon", "flux"):
+        ops = KERNEL_OPS.get(names[kind])
+        if ops is None or kt[kind][1] == 0:
+            continue
+        out[kind] = kernel_roofline(kind, dict(ops, name=names[kind]), kt, units[kind], peaks,
+                                    hbm_peak, hbm_src, clocks)
+    dom = max(("recon", "flux"), key=lambda k: kt[k][0])
+    total = sum(v[0] for v in kt.values())
+    share = {k: kt[k][0] / total for k in kt}
+    return out.get(dom), out, share
+
+
+def launches_in(kt, cg, prec, stages, steps):
+    """Kernels of this library launched in a timed region: the recorded
+    reconstruction, flux and update launches, two per time step (reduction
+    + finalisation), and the mixed path's views of the state (the float-float
+    split of Q, and for CGKS-5th the FP32 gradient copy) once per stage."""
+    n = kt["recon"][1] + kt["flux"][1] + kt["update"][1] + 2 * kt["dt"][1]
+    if prec != "fp64":
+        n += (2 if cg else 1) * stages * steps
+    return n
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
     from paper_2508_19911_gb300 import gks
-    from paper_2508_19911_gb300 import workloads as wl
 
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
+    t0 = time.time()
+    wk = make_workload(args)
+    Qh, Gh, grid = wk["Q"], wk["G"], wk["grid"]
     n = args.n
     scheme = args.scheme
     cg = scheme == "cgks5"
     stages = 2 if cg else 1
-    if args.workload == "tgv":
-        Qh, Gh, grid = wl.taylor_green(n)
-        phys = dict(mu=1.0 / 1600)
-        wname, wdata = "taylor_green", "synthetic (Taylor-Green cell averages)"
-        wcfg = {"Ma": 0.1, "Re": 1600}
-    else:
-        Qh, Gh, grid, hit_info = wl.isotropic_turbulence(n, Mt=0.5, k0=8.0, seed=103)
-        phys = dict(mu=1e-3)
-        wname, wdata = "isotropic_turbulence", "synthetic (seeded isotropic turbulence)"
-        wcfg = {"Mt": 0.5, "k0": 8, "seed": 103, "mu": 1e-3}
-    cells = n ** 3
+    cells, nxy = n ** 3, n * n
     prec = "mixed" if args.indicator else args.precision
+    tag = "learned" if args.indicator else prec
     if args.indicator and not cg:
         raise SystemExit("--indicator needs --scheme cgks5")
-    params, ind_info = (None, None)
-    if args.indicator or (cg and not args.no_variants and rank == 0):
-        params, ind_info = trained_indicator(torch, dev)
-    solver = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=scheme, nonlinear=True,
-                                   precision=prec, indicator=args.indicator,
-                                   slab_planes=args.slab_planes, **phys), stream)
-    slab = solver.slab_planes
+    want_variants = cg and not args.no_variants and rank == 0
+    params, ind_info = None, None
     if args.indicator:
-        solver.set_indicator(params, theta=ind_info["theta"])
+        params, ind_info = trained_indicator(torch, dev)
+    setup_s = time.time() - t0
+
+    def new_solver(p, learned):
+        s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=scheme, nonlinear=True,
+                                  precision="mixed" if learned else p, indicator=learned,
+                                  slab_planes=args.slab_planes, **wk["phys"]), stream)
+        if learned:
+            s.set_indicator(params, theta=ind_info["theta"])
+        return s
+
+    solver = new_solver(prec, args.indicator)
+    slab = solver.slab_planes
     Q = torch.tensor(Qh, device=dev)
     G = torch.tensor(Gh, device=dev) if cg else None
-    for _ in range(args.warmup):
-        solver.step(Q, G, nsteps=1, sync=False)
-    torch.cuda.synchronize()
-    barrier_ranks()
-    with ClockSampler(local_rank) as clk:
-        ms = time_steps(torch, solver, Q, G, args.steps, stream)
+    ms, kt, clocks = timed_steps(torch, solver, Q, G, args.warmup, args.steps, stream, local_rank)
     ms = max_over_ranks(torch, ms)
-    # per-cell kinetic energy after the warm-up and timed steps: the FP64
-    # reference for the mixed variants' error (same initial state and steps)
-    ke_ref = {}
-    if prec == "fp64" and not args.indicator:
-        ke_ref[scheme] = kinetic_energy(Q)
-    st = solver.status()
-    if st:
-        raise RuntimeError(f"non-physical state during the benchmark (status {st})")
-    value = replica_throughput(world, cells, stages, args.steps, ms)
     if args.indicator:
         ind_info["skip_fraction"] = solver.indicator_skips() / (
-            5 * cells * stages * (args.steps + args.warmup))
-
-    if slab == 0:
-        # dominant kernel: reconstruction or flux launch timed alone (same inputs)
-        fs = solver.reconstruct(Q, G)
-        dtd = solver.compute_dt(Q)
-        reps = 3
-        t_recon = time_kernel(torch, lambda: solver.reconstruct(Q, G, out=fs), reps, stream)
-        frec = solver.flux(fs, dtd, Q=Q)
-        t_flux = time_kernel(torch, lambda: solver.flux(fs, dtd, out=frec, Q=Q), reps, stream)
-        K = 4 if cg else 1
-        sfx = ("_learned" if args.indicator else "_mixed") if prec == "mixed" else ""
-        if t_flux >= t_recon:
-            kname, t_k = ("flux_cgks5" if cg else "flux_gks2") + sfx, t_flux
-            units = 3 * cells * K
-        else:
-            kname, t_k = ("recon5" if cg else "recon2") + sfx, t_recon
-            units = cells
-        clocks = clk.summary()
-        f_mhz = clocks["sm_max_mhz"] or SM_MAX_MHZ_NOMINAL
-        peak64 = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * f_mhz * 1e6 / 1e12
-        peak32 = SM_COUNT * FP32_FLOP_PER_CLK_PER_SM * f_mhz * 1e6 / 1e12
-        peaks = measured_peaks()
-        hbm_peak = peaks.get("hbm_gbs") or HBM_FALLBACK_GBS
-        ops = KERNEL_OPS.get(kname)
-        roofline = {"kernel": kname, "ms_per_launch": t_k, "units_per_launch": units,
-                    "other_kernel_ms": {"recon": t_recon, "flux": t_flux}}
-        if ops:
-            sec = t_k / 1e3
-            a64 = ops["fp64"] * units / sec / 1e12
-            a32 = ops["fp32"] * units / sec / 1e12
-            hbm = ops["bytes"] * units / sec / 1e9
-            f64, f32 = a64 / peak64, a32 / peak32
-            # the binding unit: the FP64 pipe unless the FP32 one is busier
-            if f64 >= f32:
-                roofline.update({"bound": "alu", "achieved": a64, "peak": peak64,
-                                 "unit": "TFLOP/s (FP64)", "frac": f64})
-            else:
-                roofline.update({"bound": "alu", "achieved": a32, "peak": peak32,
-                                 "unit": "TFLOP/s (FP32)", "frac": f32})
-            roofline.update({
-                "traffic": ops["dram"] * units,
-                "traffic_note": "ncu dram__bytes_read+write per unit on TGV 64^3, scaled to this launch",
-                "fp64": {"achieved_tflops": a64, "peak_tflops": peak64, "frac": f64},
-                "fp32": {"achieved_tflops": a32, "peak_tflops": peak32, "frac": f32},
-                "hbm": {"achieved_gbs": hbm, "peak_gbs": hbm_peak, "frac": hbm / hbm_peak,
-                        "peak_source": "MEASURED_PEAKS.json" if peaks.get("hbm_gbs") else "fallback"},
-                "peak_note": "ALU peaks from unit counts (152 SMs x 4 FP64 / 256 FP32 FLOP/clk x "
-                             "sm_max clock); HBM peak measured copy bandwidth",
-            })
-        else:
-            roofline.update({"bound": "alu", "achieved": None, "peak": peak64,
-                             "unit": "TFLOP/s (FP64)", "frac": None, "traffic": None})
-    else:
-        # the face-state buffer holds one z-slab: the kernels are not timed
-        # alone here (the whole-grid buffer they would need does not fit)
-        roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-                    "traffic": None, "note": f"z-slabs of {slab} planes; kernels not timed alone"}
-        clocks = clk.summary()
+            5 * (cells + (-(-n // slab) * nxy if slab else 0)) * stages * (args.steps + args.warmup))
+    if solver.status():
+        raise RuntimeError("non-physical state during the benchmark")
+    value = replica_throughput(world, cells, stages, args.steps, ms)
+    peaks = alu_peaks(torch, stream)
+    roofline, rooflines, share = path_rooflines(kt, scheme, tag, cells, nxy, slab, stages,
+                                                args.steps, peaks, clocks)
+    # per-cell kinetic energy after the warm-up and timed steps: the FP64
+    # reference for the mixed variants' error (same initial state and steps)
+    ke_ref = kinetic_energy(Q) if prec == "fp64" else None
+    del Q, G
+    torch.cuda.empty_cache()
 
     e2e = None
     if not args.no_e2e:
         # end to end through the C-ABI with host buffers (gks_step_host):
         # every step the library copies the state from pinned host memory
-        # to the device, advances it one step and copies it back
+        # to the device, advances it one step and copies it back; all the
+        # timed steps of the device leg, from the same initial state
         Qp = torch.from_numpy(Qh).pin_memory()
         Gp = torch.from_numpy(Gh).pin_memory() if cg else None
-        e2e_steps = max(1, min(args.steps, 3))
-        solver.step_host(Qp, Gp, nsteps=1)  # first call allocates the device copy
+        solver.step_host(Qp, Gp, nsteps=0)  # first call allocates the device copy
         torch.cuda.synchronize()
         barrier_ranks()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(e2e_steps):
+        for _ in range(args.steps):
             solver.step_host(Qp, Gp, nsteps=1)
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = max_over_ranks(torch, e0.elapsed_time(e1) / e2e_steps)
+        e2e_ms = max_over_ranks(torch, e0.elapsed_time(e1))
         state_bytes = Qh.nbytes + (Gh.nbytes if cg else 0)
-        e2e = {"value": replica_throughput(world, cells, stages, 1, e2e_ms), "unit": "cell-stage/s",
-               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
-               "ms_per_step": e2e_ms}
-
+        e2e = {"value": replica_throughput(world, cells, stages, args.steps, e2e_ms),
+               "unit": "cell-stage/s", "h2d_bytes_per_step": state_bytes,
+               "d2h_bytes_per_step": state_bytes, "ms_per_step": e2e_ms / args.steps,
+               "steps": args.steps}
+        del Qp, Gp
     solver.close()
-    fs = frec = None  # release the whole-grid buffers before the variants
     torch.cuda.empty_cache()
+
     variants = {}
-    if not args.no_variants and rank == 0:
-        main_tag = (scheme, "learned" if args.indicator else prec)
-        for other in ("cgks5", "gks2"):
-            for oprec in ("fp64", "mixed", "learned"):
-                if (other, oprec) == main_tag or (other == "gks2" and oprec == "learned"):
-                    continue
-                s2 = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=other, nonlinear=True,
-                                           precision="mixed" if oprec == "learned" else oprec,
-                                           indicator=oprec == "learned"), stream)
-                if oprec == "learned":
-                    s2.set_indicator(params, theta=ind_info["theta"])
-                Q2 = torch.tensor(Qh, device=dev)
-                G2 = torch.tensor(Gh, device=dev) if other == "cgks5" else None
-                # the main run's warm-up and timed step counts, so that the
-                # final state is comparable with the FP64 one
-                w2, k2 = args.warmup, args.steps
-                for _ in range(w2):
-                    s2.step(Q2, G2, nsteps=1, sync=False)
-                ms2 = time_steps(torch, s2, Q2, G2, k2, stream)
-                st2 = 2 if other == "cgks5" else 1
-                ke2 = kinetic_energy(Q2)
-                fs2 = s2.reconstruct(Q2, G2)
-                d2 = s2.compute_dt(Q2)
-                tr = time_kernel(torch, lambda: s2.reconstruct(Q2, G2, out=fs2), 2, stream)
-                fr2 = s2.flux(fs2, d2, Q=Q2)
-                tf = time_kernel(torch, lambda: s2.flux(fs2, d2, out=fr2, Q=Q2), 2, stream)
-                vk = f"{other}_{oprec}_{n}^3"
-                variants[vk] = {
-                    "value": cells * st2 * k2 / (ms2 / 1e3), "unit": "cell-stage/s",
-                    "ms_per_step": ms2 / k2, "recon_ms": tr, "flux_ms": tf}
-                if oprec == "fp64":
-                    ke_ref[other] = ke2
-                elif other in ke_ref:
-                    # the stated error: per-cell KE against FP64 after the same steps
-                    variants[vk]["ke_rel_l2_vs_fp64"] = rel_l2(ke2, ke_ref[other])
-                    variants[vk]["ke_steps"] = w2 + k2
-                if oprec == "learned":
-                    variants[vk]["skip_fraction"] = s2.indicator_skips() / (
-                        5 * cells * st2 * (w2 + k2) + 5 * cells * 3)
-                del ke2
-                s2.close()
-                del Q2, G2, fs2, fr2
-                torch.cuda.empty_cache()
+    if want_variants:
+        # the learned indicator is not among them: its gain is bounded by
+        # GENO's share of the mixed reconstruction (a few percent of the
+        # step) and the network costs about what it skips (--indicator runs
+        # it as the main path)
+        for vtag in ("fp64", "mixed"):
+            if vtag == tag:
+                continue
+            s2 = new_solver("fp64" if vtag == "fp64" else "mixed", vtag == "learned")
+            Q2 = torch.tensor(Qh, device=dev)
+            G2 = torch.tensor(Gh, device=dev)
+            ms2, kt2, clk2 = timed_steps(torch, s2, Q2, G2, args.warmup, args.steps, stream, 0)
+            v = {"value": cells * stages * args.steps / (ms2 / 1e3), "unit": "cell-stage/s",
+                 "ms_per_step": ms2 / args.steps, "slab_planes": s2.slab_planes,
+                 "steps": args.steps, "warmup": args.warmup}
+            if vtag == "learned":
+                sl = s2.slab_planes
+                v["skip_fraction"] = s2.indicator_skips() / (
+                    5 * (cells + (-(-n // sl) * nxy if sl else 0)) * stages *
+                    (args.steps + args.warmup))
+            if s2.status():
+                raise RuntimeError(f"non-physical state in the {vtag} variant")
+            r2, rs2, sh2 = path_rooflines(kt2, scheme, vtag, cells, nxy, s2.slab_planes, stages,
+                                          args.steps, peaks, clk2)
+            v.update({"roofline": r2, "rooflines": rs2, "time_share": sh2,
+                      "gpu_launches": launches_in(kt2, cg, vtag, stages, args.steps),
+                      "clocks": clk2})
+            if ke_ref is not None and vtag != "fp64":
+                # the stated error: per-cell KE against FP64 after the same steps
+                v["ke_rel_l2_vs_fp64"] = rel_l2(kinetic_energy(Q2), ke_ref)
+                v["ke_steps"] = args.warmup + args.steps
+            variants[f"{scheme}_{vtag}_{n}^3"] = v
+            s2.close()
+            del Q2, G2
+            torch.cuda.empty_cache()
 
     line = {
         "metric": METRIC, "value": value, "unit": "cell-stage/s", "n_gpus": world,
@@ -510,17 +583,18 @@ def run_ours(args, rank, world, local_rank):
         "cell_steps_per_s": value / stages,
         "dtype": "f64" if prec == "fp64" else "f32+f64",
         "indicator": ind_info if args.indicator else None,
-        "data": wdata,
-        "config": dict({"workload": f"{wname}_{n}^3_{scheme}_{'learned' if args.indicator else prec}"
-                                   "_nonlinear", "cells": cells,
-                        "scheme": scheme, "stages_per_step": stages,
+        "data": wk["data"],
+        "config": dict({"workload": f"{wk['name']}_{n}^3_{scheme}_{tag}_nonlinear",
+                        "cells": cells, "scheme": scheme, "stages_per_step": stages,
                         "gamma": 1.4, "Pr": 0.72, "cfl": 0.3, "parallelism": f"replicas{world}",
                         "slab_planes": slab,
                         "l2": "working set larger than L2 (state + face buffers > 129 MB)"},
-                       **wcfg),
-        "roofline": roofline, "e2e": e2e,
-        "gpu_launches": LAUNCHES_PER_STEP[(scheme, prec)] * args.steps, "clocks": clocks,
-        "variants": variants,
+                       **wk["cfg"]),
+        "roofline": roofline, "rooflines": rooflines, "time_share": share,
+        "measured_peaks": {"fp64_tflops": peaks[0], "fp32_tflops": peaks[1],
+                           "how": "gks_fma_rate, after the timed steps"},
+        "e2e": e2e, "gpu_launches": launches_in(kt, cg, prec, stages, args.steps),
+        "clocks": clocks, "setup_s": setup_s, "variants": variants,
     }
     return line
 
@@ -885,7 +959,7 @@ def main():
     line = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_cpu:
-            line["cpu_baseline"] = cpu_baseline(args.scheme)
+            line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line))
     if world > 1:
         import torch
