@@ -97,7 +97,22 @@ __device__ __forceinline__ ff ff_div(ff a, ff b) {
     return ff_add_f(q, __fmul_rn(r.hi, rb));
 }
 
-__device__ __forceinline__ ff ff_recip(ff b) { return ff_div(ff_make(1.0f, 0.0f), b); }
+// 1/b: the FP32 reciprocal r and one Newton step r + r (1 - b r), the
+// residual 1 - b.hi r formed exactly by an FMA (quadratic convergence: the
+// relative error ~2^-24 of r becomes ~2^-46)
+__device__ __forceinline__ ff ff_recip(ff b) {
+    const float r = __frcp_rn(b.hi);
+    const float e = __fmaf_rn(-b.lo, r, __fmaf_rn(-b.hi, r, 1.0f));
+    return fast_two_sum(r, __fmul_rn(r, e));
+}
+
+// a + b with the two lo parts added in FP32: about 2^-46 (|a| + |b|), not
+// relative to |a + b| where the two cancel (for sums of like terms)
+__device__ __forceinline__ ff ff_add_like(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, s.lo);
+}
 
 // sqrt(a), a > 0: FP32 root, one Newton correction with the exact residual
 __device__ __forceinline__ ff ff_sqrt(ff a) {

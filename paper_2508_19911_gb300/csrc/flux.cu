@@ -531,8 +531,9 @@ __device__ __forceinline__ PrimFF to_prim_ff(const ff s[5], ff gm1) {
     P.W = ff_mul(s[3], ir);
     const ff q2 = ff_add(ff_add(ff_mul(P.U, P.U), ff_mul(P.V, P.V)), ff_mul(P.W, P.W));
     P.p = ff_mul(gm1, ff_sub(s[4], ff_half(ff_mul(P.rho, q2))));
-    P.lam = ff_div(ff_half(P.rho), P.p);
     P.il = ff_mul(P.p, ir);
+    // lam only feeds the FP32 core (the half-line start uses il)
+    P.lam = ff_make(__fdividef(0.5f * P.rho.hi, P.p.hi), 0.0f);
     return P;
 }
 
@@ -570,8 +571,8 @@ __constant__ ffc cSeriesInvOdd[kSeriesTerms + 1] = {
     ff_const(1.0 / 65)};
 
 __device__ __forceinline__ void half_start_ff(const PrimFF &S, int sgn, ff &m0, ff &m1) {
-    const ff sl = ff_sqrt(S.lam);
-    const ff y = ff_mul(sl, S.U);
+    const ff isl = ff_sqrt(ff_make(2.0f * S.il.hi, 2.0f * S.il.lo));  // 1/sqrt(lam), exact doubling
+    const ff y = ff_mul(S.U, ff_recip(isl));
     if (fabsf(y.hi) <= 2.0f) {
         const ff w = ff_neg(ff_mul(y, y));
         ff t = ff_make(1.0f, 0.0f), se = t, sf = t;
@@ -586,11 +587,11 @@ __device__ __forceinline__ void half_start_ff(const PrimFF &S, int sgn, ff &m0, 
         constexpr ffc krpi = ff_const(0.56418958354775628695);   // 1/sqrt(pi)
         const ff erf = ff_mul(ff_mul(y, ff_of(k2rpi)), sf);
         m0 = ff_half(sgn > 0 ? ff_add_f(erf, 1.0f) : ff_sub(ff_make(1.0f, 0.0f), erf));
-        const ff edge = ff_half(ff_div(ff_mul(se, ff_of(krpi)), sl));
+        const ff edge = ff_half(ff_mul(ff_mul(se, ff_of(krpi)), isl));
         m1 = sgn > 0 ? ff_add(ff_mul(S.U, m0), edge) : ff_sub(ff_mul(S.U, m0), edge);
     } else {
         double d0, d1;
-        half_start(ff_to_double(S.U), ff_to_double(S.lam), (double)sgn, d0, d1);
+        half_start(ff_to_double(S.U), 0.5 / ff_to_double(S.il), (double)sgn, d0, d1);
         m0 = ff_from_double(d0);
         m1 = ff_from_double(d1);
     }
@@ -867,14 +868,23 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S
         }
         flux_point_mixed<kCGKS>(P, Ql, ol, dl, Qr, orr, dr, dt, out, valid ? status : nullptr);
         if (kCGKS) {
-            // Gauss-point average in float-float (the FP32 entries have lo = 0)
+            // Gauss-point average: the time derivatives (blocks 1, 3, 5) are
+            // FP32 values (lo = 0), summed in FP32; F^n and the interface
+            // values in float-float. Both butterflies give every lane of a
+            // face the same bits (the sums are commutative at each step).
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
-                ff s = ff_add(out[q], ff_make(__shfl_xor_sync(0xffffffffu, out[q].hi, 1),
-                                              __shfl_xor_sync(0xffffffffu, out[q].lo, 1)));
-                s = ff_add(s, ff_make(__shfl_xor_sync(0xffffffffu, s.hi, 2),
-                                      __shfl_xor_sync(0xffffffffu, s.lo, 2)));
-                out[q] = ff_make(0.25f * s.hi, 0.25f * s.lo);  // exact
+                if ((q / 5) & 1) {
+                    float s = out[q].hi + __shfl_xor_sync(0xffffffffu, out[q].hi, 1);
+                    s = s + __shfl_xor_sync(0xffffffffu, s, 2);
+                    out[q] = ff_make(0.25f * s, 0.0f);
+                } else {
+                    ff s = ff_add_like(out[q], ff_make(__shfl_xor_sync(0xffffffffu, out[q].hi, 1),
+                                                       __shfl_xor_sync(0xffffffffu, out[q].lo, 1)));
+                    s = ff_add_like(s, ff_make(__shfl_xor_sync(0xffffffffu, s.hi, 2),
+                                               __shfl_xor_sync(0xffffffffu, s.lo, 2)));
+                    out[q] = ff_make(0.25f * s.hi, 0.25f * s.lo);  // exact
+                }
             }
         }
         if (!valid) return;
