@@ -8,8 +8,10 @@
 //   <u^n> on the full line by <u^{n+2}> = U <u^{n+1}> + (n+1)/(2 lam) <u^n>,
 //   on the half lines from erfc/exp starting values and the same recursion,
 //   <xi^2> = N/(2 lam), <xi^4> = (N^2 + 2N)/(4 lam^2),
-// composed into <(a.psi) u^A v^B w^D psi> with compile-time exponents; the
-// Maxwellian slopes a (<(a.psi) psi> = dW/rho) are solved in closed form.
+// composed into the symmetric moment matrices <u^A v^B w^D psi psi^T> with
+// compile-time exponents, each built once per weight and applied to every
+// slope vector that meets it; the Maxwellian slopes a (<(a.psi) psi> =
+// dW/rho) are solved in closed form.
 // One thread evaluates one Gauss point; the four Gauss points of a CGKS-5th
 // face are four adjacent lanes reduced with a butterfly of shuffles.
 #include <cmath>
@@ -59,55 +61,56 @@ __device__ __forceinline__ void psi_m(const T *u, const T *v, const T *w, T x2, 
     o[4] = T(0.5) * (u[A + 2] * vw + u[A] * (v[B + 2] * w[D] + v[B] * w[D + 2]) + b * x2);
 }
 
-// <xi^2 u^A v^B w^D psi>
+// The symmetric moment matrix G[i][k] = <u^A v^B w^D psi_i psi_k> of one
+// Maxwellian (u, v, w its 1D moments, x2 = <xi^2>, x4 = <xi^4>), packed
+// (00 01 02 03 04 11 12 13 14 22 23 24 33 34 44). Built once and applied to
+// every slope vector that meets the same weight u^A v^B w^D (the three
+// directional slopes and A of one side share several), instead of
+// re-deriving its entries in every contraction.
+template <typename T>
+struct Sym5 {
+    T g[15];
+};
+
 template <int A, int B, int D, typename T>
-__device__ __forceinline__ void psixi_m(const T *u, const T *v, const T *w, T x2, T x4, T o[5]) {
-    const T vw = v[B] * w[D];
-    const T b = u[A] * vw;
-    o[0] = x2 * b;
-    o[1] = x2 * u[A + 1] * vw;
-    o[2] = x2 * u[A] * v[B + 1] * w[D];
-    o[3] = x2 * u[A] * v[B] * w[D + 1];
-    o[4] = T(0.5) * (x2 * (u[A + 2] * vw + u[A] * (v[B + 2] * w[D] + v[B] * w[D + 2])) + x4 * b);
+__device__ __forceinline__ Sym5<T> mom_matrix(const T *u, const T *v, const T *w, T x2, T x4) {
+    auto m = [&](int a, int b, int d) { return u[A + a] * (v[B + b] * w[D + d]); };
+    Sym5<T> M;
+    const T m000 = m(0, 0, 0), m200 = m(2, 0, 0), m020 = m(0, 2, 0), m002 = m(0, 0, 2);
+    M.g[0] = m000;
+    M.g[1] = m(1, 0, 0);
+    M.g[2] = m(0, 1, 0);
+    M.g[3] = m(0, 0, 1);
+    M.g[4] = T(0.5) * (m200 + m020 + m002 + x2 * m000);
+    M.g[5] = m200;
+    M.g[6] = m(1, 1, 0);
+    M.g[7] = m(1, 0, 1);
+    M.g[8] = T(0.5) * (m(3, 0, 0) + m(1, 2, 0) + m(1, 0, 2) + x2 * M.g[1]);
+    M.g[9] = m020;
+    M.g[10] = m(0, 1, 1);
+    M.g[11] = T(0.5) * (m(2, 1, 0) + m(0, 3, 0) + m(0, 1, 2) + x2 * M.g[2]);
+    M.g[12] = m002;
+    M.g[13] = T(0.5) * (m(2, 0, 1) + m(0, 2, 1) + m(0, 0, 3) + x2 * M.g[3]);
+    M.g[14] = T(0.25) * (m(4, 0, 0) + m(0, 4, 0) + m(0, 0, 4) +
+                         T(2) * (m(2, 2, 0) + m(2, 0, 2) + m(0, 2, 2)) +
+                         T(2) * x2 * (m200 + m020 + m002) + x4 * m000);
+    return M;
 }
 
-// acc += s * <(a.psi) u^A v^B w^D psi>
-template <int A, int B, int D, typename T>
-__device__ __forceinline__ void apsi_acc(const T a[5], const T *u, const T *v, const T *w, T x2,
-                                         T x4, T s, T acc[5]) {
-    T t[5], o[5], e[5];
-    psi_m<A, B, D>(u, v, w, x2, o);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) t[i] = a[0] * o[i];
-    psi_m<A + 1, B, D>(u, v, w, x2, o);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) t[i] += a[1] * o[i];
-    psi_m<A, B + 1, D>(u, v, w, x2, o);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) t[i] += a[2] * o[i];
-    psi_m<A, B, D + 1>(u, v, w, x2, o);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) t[i] += a[3] * o[i];
-    psi_m<A + 2, B, D>(u, v, w, x2, e);
-    psi_m<A, B + 2, D>(u, v, w, x2, o);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) e[i] += o[i];
-    psi_m<A, B, D + 2>(u, v, w, x2, o);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) e[i] += o[i];
-    psixi_m<A, B, D>(u, v, w, x2, x4, o);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) acc[i] += s * (t[i] + T(0.5) * a[4] * (e[i] + o[i]));
-}
-
-// acc += s * sum_j <(a_j.psi) c_j u^E psi>, c = (u, v, w): the directional
-// slope terms of Eq. flux (E = 1 for fluxes, 0 for conserved moments)
-template <int E, typename T>
-__device__ __forceinline__ void dir_acc(const T a[3][5], const T *u, const T *v, const T *w,
-                                        T x2, T x4, T s, T acc[5]) {
-    apsi_acc<1 + E, 0, 0>(a[0], u, v, w, x2, x4, s, acc);
-    apsi_acc<E, 1, 0>(a[1], u, v, w, x2, x4, s, acc);
-    apsi_acc<E, 0, 1>(a[2], u, v, w, x2, x4, s, acc);
+// acc += s * G a
+template <typename T>
+__device__ __forceinline__ void sym_acc(const Sym5<T> &M, const T a[5], T s, T acc[5]) {
+    const T *g = M.g;
+    const T r0 = g[0] * a[0] + g[1] * a[1] + g[2] * a[2] + g[3] * a[3] + g[4] * a[4];
+    const T r1 = g[1] * a[0] + g[5] * a[1] + g[6] * a[2] + g[7] * a[3] + g[8] * a[4];
+    const T r2 = g[2] * a[0] + g[6] * a[1] + g[9] * a[2] + g[10] * a[3] + g[11] * a[4];
+    const T r3 = g[3] * a[0] + g[7] * a[1] + g[10] * a[2] + g[12] * a[3] + g[13] * a[4];
+    const T r4 = g[4] * a[0] + g[8] * a[1] + g[11] * a[2] + g[13] * a[3] + g[14] * a[4];
+    acc[0] += s * r0;
+    acc[1] += s * r1;
+    acc[2] += s * r2;
+    acc[3] += s * r3;
+    acc[4] += s * r4;
 }
 
 // Slope of a Maxwellian (U, V, W, lam; il = 1/(2 lam)) with N internal
@@ -281,7 +284,7 @@ __device__ __forceinline__ Prim to_prim(const double *s, double gamma) {
 // ds: the 15 derivatives d/dn, d/dt1, d/dt2 of the 5 conserved variables.
 template <int SGN, typename T>
 __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, T c4, T uh0, T uh1,
-                                           T U0, T V0, T W0, T dW0[3][5], T X4[5], T X5[5],
+                                           T U0, T V0, T W0, T dW0[3][5], T X4[5], T X5acc[5],
                                            T X6[5], T q[3], T dtW[5]) {
     const T ir = T(1) / S.rho;
     const T inv2l = S.p * ir;  // 1/(2 lam)
@@ -301,8 +304,11 @@ __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, 
         maxwell_slope(d, S.U, S.V, S.W, S.lam, inv2l, N, c4, a[j]);
     }
     // A from the compatibility condition: <(A.psi) psi> = -<(a.u) psi>
+    // (full line); the moment matrices of the weights u, v, w
     T Tv[5] = {0, 0, 0, 0, 0}, A[5];
-    dir_acc<0>(a, uf, v, w, x2, x4, T(1), Tv);
+    sym_acc(mom_matrix<1, 0, 0>(uf, v, w, x2, x4), a[0], T(1), Tv);
+    sym_acc(mom_matrix<0, 1, 0>(uf, v, w, x2, x4), a[1], T(1), Tv);
+    sym_acc(mom_matrix<0, 0, 1>(uf, v, w, x2, x4), a[2], T(1), Tv);
     {
         T mT[5];
 #pragma unroll
@@ -312,32 +318,45 @@ __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, 
         }
         maxwell_slope(mT, S.U, S.V, S.W, S.lam, inv2l, N, c4, A);
     }
-    // slopes of the interface equilibrium, collected from both sides
+    // half line, weight 1: the slopes of the interface equilibrium (collected
+    // from both sides), term 4 (g_s: rows 1 and 0 of its matrix are
+    // <u psi>, <psi>) and term 6's conserved moments <(A.psi) psi>
+    T X[5], Y[5], X5[5] = {0, 0, 0, 0, 0}, Y5[5] = {0, 0, 0, 0, 0}, Y6[5] = {0, 0, 0, 0, 0};
+    {
+        const Sym5<T> H = mom_matrix<0, 0, 0>(uh, v, w, x2, x4);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) apsi_acc<0, 0, 0>(a[j], uh, v, w, x2, x4, S.rho, dW0[j]);
-    T X[5], Y[5];
-    // term 4: g_s on its half line
-    psi_m<1, 0, 0>(uh, v, w, x2, X);
-    psi_m<0, 0, 0>(uh, v, w, x2, Y);
+        for (int j = 0; j < 3; ++j) sym_acc(H, a[j], S.rho, dW0[j]);
+        sym_acc(H, A, S.rho, Y6);
+        const T r1[5] = {H.g[1], H.g[5], H.g[6], H.g[7], H.g[8]};
 #pragma unroll
-    for (int i = 0; i < 5; ++i) { X[i] *= S.rho; Y[i] *= S.rho; X4[i] += X[i]; }
-    q[0] += heat(X, Y, U0, V0, W0);
-    // term 5: (a.u) g_s
+        for (int i = 0; i < 5; ++i) {
+            X[i] = S.rho * r1[i];
+            Y[i] = S.rho * H.g[i];
+            X4[i] += X[i];
+        }
+        q[0] += heat(X, Y, U0, V0, W0);
+    }
+    // weight u: term 6's flux moments <(A.psi) u psi> and the first
+    // directional part of term 5's conserved moments
 #pragma unroll
-    for (int i = 0; i < 5; ++i) { X[i] = T(0); Y[i] = T(0); }
-    dir_acc<1>(a, uh, v, w, x2, x4, S.rho, X);
-    dir_acc<0>(a, uh, v, w, x2, x4, S.rho, Y);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) X5[i] += X[i];
-    q[1] += heat(X, Y, U0, V0, W0);
-    // term 6: A g_s
-#pragma unroll
-    for (int i = 0; i < 5; ++i) { X[i] = T(0); Y[i] = T(0); }
-    apsi_acc<1, 0, 0>(A, uh, v, w, x2, x4, S.rho, X);
-    apsi_acc<0, 0, 0>(A, uh, v, w, x2, x4, S.rho, Y);
+    for (int i = 0; i < 5; ++i) X[i] = T(0);
+    {
+        const Sym5<T> H = mom_matrix<1, 0, 0>(uh, v, w, x2, x4);
+        sym_acc(H, A, S.rho, X);
+        sym_acc(H, a[0], S.rho, Y5);
+    }
 #pragma unroll
     for (int i = 0; i < 5; ++i) X6[i] += X[i];
-    q[2] += heat(X, Y, U0, V0, W0);
+    q[2] += heat(X, Y6, U0, V0, W0);
+    // term 5: (a.u) g_s = sum_j (a_j.psi) c_j g_s
+    sym_acc(mom_matrix<0, 1, 0>(uh, v, w, x2, x4), a[1], S.rho, Y5);
+    sym_acc(mom_matrix<0, 0, 1>(uh, v, w, x2, x4), a[2], S.rho, Y5);
+    sym_acc(mom_matrix<2, 0, 0>(uh, v, w, x2, x4), a[0], S.rho, X5);
+    sym_acc(mom_matrix<1, 1, 0>(uh, v, w, x2, x4), a[1], S.rho, X5);
+    sym_acc(mom_matrix<1, 0, 1>(uh, v, w, x2, x4), a[2], S.rho, X5);
+    q[1] += heat(X5, Y5, U0, V0, W0);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) X5acc[i] += X5[i];
 }
 
 // Equilibrium part: abar from the collided slopes dW0, Abar by
@@ -361,7 +380,10 @@ __device__ __forceinline__ void equilibrium_terms(const PrimT<T> &Z, T N, T c4, 
         maxwell_slope(d, Z.U, Z.V, Z.W, Z.lam, inv2l, N, c4, ab[j]);
     }
     T T0[5] = {0, 0, 0, 0, 0}, Ab[5];
-    dir_acc<0>(ab, u, v, w, x2, x4, T(1), T0);
+    const Sym5<T> Fu = mom_matrix<1, 0, 0>(u, v, w, x2, x4);
+    sym_acc(Fu, ab[0], T(1), T0);
+    sym_acc(mom_matrix<0, 1, 0>(u, v, w, x2, x4), ab[1], T(1), T0);
+    sym_acc(mom_matrix<0, 0, 1>(u, v, w, x2, x4), ab[2], T(1), T0);
     {
         T mT[5];
 #pragma unroll
@@ -370,20 +392,22 @@ __device__ __forceinline__ void equilibrium_terms(const PrimT<T> &Z, T N, T c4, 
     }
     T Y[5];
     if (kTerm1) {
-        // term 1: g0
-        psi_m<1, 0, 0>(u, v, w, x2, X[0]);
-        psi_m<0, 0, 0>(u, v, w, x2, Y);
+        // term 1: g0 (rows 1 and 0 of its moment matrix: <u psi>, <psi>)
+        const Sym5<T> F0 = mom_matrix<0, 0, 0>(u, v, w, x2, x4);
+        const T r1[5] = {F0.g[1], F0.g[5], F0.g[6], F0.g[7], F0.g[8]};
 #pragma unroll
-        for (int i = 0; i < 5; ++i) { X[0][i] *= Z.rho; Y[i] *= Z.rho; }
+        for (int i = 0; i < 5; ++i) { X[0][i] = Z.rho * r1[i]; Y[i] = Z.rho * F0.g[i]; }
         q[0] = heat(X[0], Y, Z.U, Z.V, Z.W);
     }
     // term 2: (abar.u) g0; its conserved moments are rho0 T0
-    dir_acc<1>(ab, u, v, w, x2, x4, Z.rho, X[1]);
+    sym_acc(mom_matrix<2, 0, 0>(u, v, w, x2, x4), ab[0], Z.rho, X[1]);
+    sym_acc(mom_matrix<1, 1, 0>(u, v, w, x2, x4), ab[1], Z.rho, X[1]);
+    sym_acc(mom_matrix<1, 0, 1>(u, v, w, x2, x4), ab[2], Z.rho, X[1]);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Y[i] = Z.rho * T0[i];
     q[1] = heat(X[1], Y, Z.U, Z.V, Z.W);
     // term 3: Abar g0; its conserved moments are -rho0 T0 (compatibility)
-    apsi_acc<1, 0, 0>(Ab, u, v, w, x2, x4, Z.rho, X[2]);
+    sym_acc(Fu, Ab, Z.rho, X[2]);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         Y[i] = -Z.rho * T0[i];
