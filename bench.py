@@ -50,14 +50,14 @@ _DRAM_NOTE = ("ncu dram__bytes_read+write per unit of one launch on a 64^3 grid,
               "this launch's units (the traffic grows with the units: one pass over state "
               "and face buffers that exceed L2)")
 KERNEL_OPS = {
-    "recon5": {"fp64": 17062.0, "fp32": 130.0, "bytes": 160 + 3840, "dram": 3824.7,
+    "recon5": {"fp64": 17062.0, "fp32": 130.0, "bytes": 160 + 3840, "dram": 3830.4,
                "dram_note": _DRAM_NOTE},
-    "flux_cgks5": {"fp64": 5575.5, "fp32": 58.0, "bytes": (3840 + 720) / 12, "dram": 386.3,
+    "flux_cgks5": {"fp64": 4695.5, "fp32": 16.0, "bytes": (3840 + 720) / 12, "dram": 385.4,
                    "dram_note": _DRAM_NOTE},
-    "recon5_mixed": {"fp64": 0.0, "fp32": 16181.2, "bytes": 40 + 60 + 1920, "dram": 1788.1,
+    "recon5_mixed": {"fp64": 0.0, "fp32": 16181.2, "bytes": 40 + 60 + 1920, "dram": 1787.4,
                      "dram_note": _DRAM_NOTE},
-    "flux_cgks5_mixed": {"fp64": 21.5, "fp32": 9628.4, "bytes": (1920 + 40 + 720) / 12,
-                         "dram": 225.4, "dram_note": _DRAM_NOTE},
+    "flux_cgks5_mixed": {"fp64": 21.5, "fp32": 7843.1, "bytes": (1920 + 40 + 720) / 12,
+                         "dram": 226.0, "dram_note": _DRAM_NOTE},
 }
 KERNEL_OPS["recon5_learned"] = KERNEL_OPS["recon5_mixed"]
 KERNEL_OPS["flux_cgks5_learned"] = KERNEL_OPS["flux_cgks5_mixed"]
@@ -104,6 +104,9 @@ def parse():
     ap.add_argument("--precisions", default="fp64,mixed",
                     help="--c2: paths to run (fp64, mixed, fp64p: FP64 from the initial "
                          "state perturbed by 1e-14 relative, the FP64 path's own sensitivity)")
+    ap.add_argument("--ma2", action="store_true",
+                    help="--c2: the supersonic Taylor-Green vortex of Sec. 4.2 (Ma 2, Re 1600, "
+                         "Pr 0.7, Sutherland viscosity) instead of the Ma 0.1 one")
     ap.add_argument("--linear", action="store_true",
                     help="--c2: the linear scheme (chi = 1 / no limiter), as the paper runs the "
                          "subsonic Taylor-Green vortex")
@@ -699,14 +702,16 @@ def _dump_history(path, obj):
 
 
 def run_c2(args):
-    """Taylor-Green vortex (Ma 0.1, Re 1600, U0 = L = 1), CGKS-5th or
-    GKS-2nd nonlinear, from t = 0 to t_end: the kinetic energy E_k and the
-    solenoidal and dilatational dissipation eps_S, eps_D sampled every
-    `every` time units on each path (FP64, mixed); -dE_k/dt from centred
-    differences of the samples; the mixed history's largest deviation from
-    FP64 and the relative L2 difference of the per-cell kinetic energy at
-    t_end. Each sample time is hit exactly (the last step before it is
-    clamped on the device); steps past it are no-ops."""
+    """Taylor-Green vortex (Ma 0.1, Re 1600, U0 = L = 1; with --ma2 the
+    supersonic one of Sec. 4.2: Ma 2, U0 = sqrt(gamma) Ma, Pr 0.7,
+    Sutherland viscosity mu0 = U0/1600), CGKS-5th or GKS-2nd nonlinear, from
+    t = 0 to t_end: the kinetic energy E_k and the solenoidal and
+    dilatational dissipation eps_S, eps_D sampled every `every` time units
+    on each path (FP64, mixed); -dE_k/dt from centred differences of the
+    samples; the mixed history's largest deviation from FP64 and the
+    relative L2 difference of the per-cell kinetic energy at t_end. Each
+    sample time is hit exactly (the last step before it is clamped on the
+    device); steps past it are no-ops."""
     import torch
 
     from paper_2508_19911_gb300 import gks
@@ -718,14 +723,20 @@ def run_c2(args):
     scheme = args.scheme
     cg = scheme == "cgks5"
     stages = 2 if cg else 1
-    Qh, Gh, grid = wl.taylor_green(n)
+    if args.ma2:
+        Qh, Gh, grid = wl.taylor_green_supersonic(n)
+        U0 = math.sqrt(1.4) * 2.0
+        phys = dict(mu=U0 / 1600, mu_law=1, Pr=0.7)
+    else:
+        Qh, Gh, grid = wl.taylor_green(n)
+        phys = dict(mu=1.0 / 1600)
     nsamp = int(round(args.t_end / args.every))
     times = [args.every * j for j in range(nsamp + 1)]
     hist, paths, kes = {"times": times}, {}, {}
     for prec in args.precisions.split(","):
         s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme=scheme,
                                   precision="fp64" if prec == "fp64p" else prec,
-                                  nonlinear=not args.linear), stream)
+                                  nonlinear=not args.linear, **phys), stream)
         Q0 = Qh
         if prec == "fp64p":
             rng = np.random.default_rng(2024)
@@ -790,10 +801,10 @@ def run_c2(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if "fp64" in paths else "f32+f64",
         "data": "synthetic (Taylor-Green cell averages)",
-        "config": {"workload": f"taylor_green_{n}^3_{scheme}_"
+        "config": {"workload": f"taylor_green{'_supersonic' if args.ma2 else ''}_{n}^3_{scheme}_"
                                f"{'linear' if args.linear else 'nonlinear'}_to_t{args.t_end:g}",
                    "cells": n ** 3,
-                   "Ma": 0.1, "Re": 1600, "sample_every": args.every},
+                   "Ma": 2.0 if args.ma2 else 0.1, "Re": 1600, "sample_every": args.every},
         "paths": paths,
     }
 
