@@ -39,16 +39,37 @@ class Params(ctypes.Structure):
         ("scheme", ctypes.c_int), ("nonlinear", ctypes.c_int),
         ("mu_law", ctypes.c_int), ("inviscid", ctypes.c_int),
         ("threads", ctypes.c_int),
+        ("bc", ctypes.c_int * 3), ("pad_", ctypes.c_int),
+        ("hx", ctypes.POINTER(ctypes.c_double)), ("hy", ctypes.POINTER(ctypes.c_double)),
+        ("hz", ctypes.POINTER(ctypes.c_double)),
     ]
+
+
+BC_PERIODIC, BC_SYMMETRY, BC_OUTFLOW = 0, 1, 2
 
 
 def params(*, gamma=1.4, Pr=0.72, mu0=1.0 / 1600, cfl=0.3, C_tau=10.0,
            eps_tau=0.05, T_ref=1.0, L=(2 * np.pi,) * 3, n=(16, 16, 16),
-           scheme=1, nonlinear=1, mu_law=0, inviscid=0, threads=None):
+           scheme=1, nonlinear=1, mu_law=0, inviscid=0, threads=None,
+           bc=(0, 0, 0), spacing=(None, None, None)):
+    """bc[a]: BC_PERIODIC, BC_SYMMETRY (mirror, normal momentum negated) or
+    BC_OUTFLOW (mirror) on axis a; spacing[a]: the n[a] cell sizes of axis a
+    (None: uniform L[a]/n[a])."""
     if threads is None:
         threads = os.cpu_count() or 1
-    return Params(gamma, Pr, mu0, cfl, C_tau, eps_tau, T_ref, L[0], L[1], L[2],
-                  n[0], n[1], n[2], scheme, nonlinear, mu_law, inviscid, threads)
+    P = Params(gamma, Pr, mu0, cfl, C_tau, eps_tau, T_ref, L[0], L[1], L[2],
+               n[0], n[1], n[2], scheme, nonlinear, mu_law, inviscid, threads)
+    for a in range(3):
+        P.bc[a] = int(bc[a])
+    keep = []
+    for a, name in enumerate(("hx", "hy", "hz")):
+        if spacing[a] is not None:
+            h = np.ascontiguousarray(spacing[a], dtype=np.float64)
+            assert h.shape == (n[a],) and np.all(h > 0)
+            keep.append(h)
+            setattr(P, name, h.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    P._keep = keep  # the spacing arrays live as long as the parameters
+    return P
 
 
 def _sources():
@@ -95,7 +116,7 @@ def lib():
                                     ctypes.c_double, ctypes.c_int, _D, _D],
                 "orc_dt": [_P, _D, _D],
                 "orc_run": [_P, _D, _D, ctypes.c_int, ctypes.c_double, _D, _D],
-                "orc_stage": [_P, _D, _D, ctypes.c_double, _D, _D, _D],
+                "orc_stage": [_P, _D, _D, ctypes.c_double, _D, _D, _D, _D],
                 "orc_face_states": [_P, _D, _D, _D],
                 "orc_face_states_at": [_P, _D, _D, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.c_longlong, _D],
@@ -208,14 +229,22 @@ def run(P, Q, G=None, nsteps=1, t_stop=np.inf, t=0.0):
     return float(tt[0]), float(dl[0])
 
 
-def stage(P, Q, G, dt_):
+def n_plane(P):
+    """Size of the boundary-face planes: max(ny nz, nx nz, nx ny)."""
+    return max(P.ny * P.nz, P.nx * P.nz, P.nx * P.ny)
+
+
+def stage(P, Q, G, dt_, boundary=False):
+    """L, Lt [5][cells] and the face records [3][30][cells]; with
+    boundary=True also the high-boundary records [3][30][n_plane]."""
     n = P.nx * P.ny * P.nz
     L = np.zeros((5, n))
     Lt = np.zeros((5, n))
     faces = np.zeros((3, 30, n))
+    fhi = np.zeros((3, 30, n_plane(P)))
     _check(lib().orc_stage(ctypes.byref(P), _ptr(Q), _ptr(G), dt_, _ptr(L), _ptr(Lt),
-                           _ptr(faces)), "stage")
-    return L, Lt, faces
+                           _ptr(faces), _ptr(fhi)), "stage")
+    return (L, Lt, faces, fhi) if boundary else (L, Lt, faces)
 
 
 def face_states(P, Q, G):

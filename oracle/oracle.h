@@ -62,6 +62,17 @@ typedef struct {
     int mu_law;              /* 0 constant mu, 1 Sutherland (Sec. 4.2)      */
     int inviscid;            /* 1: tau = eps dt + C|dp/sp| dt               */
     int threads;             /* OpenMP threads, <= 0: leave runtime default */
+    /* Non-periodic boundaries and stretched meshes (Sec. 3.2, last
+     * paragraph: each cell mapped to one reference cell). bc[a] for axis a:
+     * 0 periodic; 1 symmetry plane (a mirror ghost cell whose normal
+     * momentum and its tangential derivatives change sign: a free-slip,
+     * adiabatic wall); 2 outflow (a mirror ghost cell, no sign change of
+     * the normal momentum: zero normal derivative at the boundary).
+     * hx[nx], hy[ny], hz[nz]: cell sizes along each axis (NULL: the
+     * uniform L/n of that axis).                                          */
+    int bc[3];
+    int pad_;
+    const double *hx, *hy, *hz;
 } orc_params;
 
 /* --- Maxwellian moments (Sec. 2) ------------------------------------- */
@@ -109,9 +120,12 @@ int orc_dt(const orc_params *P, const double *Q, double *dt);
 int orc_run(const orc_params *P, double *Q, double *G, int nsteps,
             double t_stop, double *t, double *dt_last);
 /* One stage of the spatial operator, for parity of the pieces:
- * L, Lt [5][cells]; face records [3][30][cells] (see scheme.cpp).        */
+ * L, Lt [5][cells]; face records [3][30][cells] (see scheme.cpp);
+ * faces_hi (may be NULL) [3][30][np]: the records of the faces on the high
+ * boundary of each non-periodic axis d, at plane position j + ny k (d = 0),
+ * i + nx k (d = 1), i + nx j (d = 2); np = max(ny nz, nx nz, nx ny).     */
 int orc_stage(const orc_params *P, const double *Q, const double *G,
-              double dt, double *L, double *Lt, double *faces);
+              double dt, double *L, double *Lt, double *faces, double *faces_hi);
 /* GENO's chi of every (variable, cell) of a CGKS-5th state: chi[5][cells]. */
 int orc_chi_field(const orc_params *P, const double *Q, const double *G, double *chi);
 /* Reconstructed face states of all cells: [6][4][20][cells] (CGKS-5th) or

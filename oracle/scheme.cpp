@@ -1,13 +1,29 @@
 /*
- * Oracle: finite-volume scheme on a periodic uniform Cartesian grid
- * (Sec. 2 Eq. semi, Sec. 3.1, Sec. 3.4, Sec. 4).
+ * Oracle: finite-volume scheme on a Cartesian grid (Sec. 2 Eq. semi,
+ * Sec. 3.1, Sec. 3.4, Sec. 4), periodic or with mirror boundaries, uniform
+ * or stretched along each axis.
  * Test infrastructure only (see oracle.h).
  *
  * State layout: Q[v][k][j][i] (v = rho, rho U, rho V, rho W, rho E; x
  * fastest), G[v][axis][k][j][i] the cell-averaged gradients (CGKS-5th).
  * Face records (per axis d, per cell c, for the face on c's low-d side):
  * [F(5), F_t(5), Q^l(5), dQ^l/dt(5), Q^r(5), dQ^r/dt(5)], global frame,
- * each averaged over the face's Gauss points.
+ * each averaged over the face's Gauss points; on a non-periodic axis the
+ * faces of the high boundary have records of their own (faces_hi).
+ *
+ * Boundaries (reading R15): a ghost cell beyond a non-periodic boundary is
+ * the mirror image of the cell inside it. The mirrored field is
+ * F_g(x) = s F(M x), M the reflection in the boundary plane and s = -1 for
+ * the normal momentum of a symmetry plane (bc 1), +1 otherwise (bc 2,
+ * outflow); so its average is s Q, its derivative along the normal -s dQ/dn
+ * and along the plane s dQ/dt.
+ * Stretched meshes (reading R16, Sec. 3.2 last paragraph): every cell is
+ * mapped to one reference cell by x = x_0 + h_a delta_a per axis, and the
+ * stencil is taken in the index coordinates of that map: neighbours are
+ * unit cells there, their averages are used as they are and their
+ * gradients as h_a dQ/dx_a with each neighbour's own h_a; the quartic is
+ * the reference-cell quartic of the uniform grid and its derivatives are
+ * mapped back with the target cell's 1/h_a.
  */
 #include "oracle_internal.h"
 
@@ -21,17 +37,61 @@ namespace {
 struct Grid {
     int nx, ny, nz;
     long n;
-    double h[3];
+    int bc[3];
+    bool uniform;             /* no spacing arrays: h = L/n on every axis */
+    std::vector<double> hs[3];
+    int len(int a) const { return a == 0 ? nx : (a == 1 ? ny : nz); }
+    double h(int a, int i) const { return hs[a][i]; }
+    long cell(int i, int j, int k) const { return ((long)k * ny + j) * nx + i; }
+    /* neighbour of (i, j, k) at offset o: its cell, its coordinates and the
+     * axes across whose boundary it was mirrored (bit a of flip) */
+    long nbr(int i, int j, int k, int o0, int o1, int o2, int c3[3], int &flip) const {
+        const int c0[3] = {i + o0, j + o1, k + o2};
+        flip = 0;
+        for (int a = 0; a < 3; ++a) {
+            const int m = len(a);
+            int x = c0[a];
+            if (bc[a] == 0) {
+                x = (x % m + m) % m;
+            } else if (x < 0) {
+                x = -1 - x;
+                flip |= 1 << a;
+            } else if (x >= m) {
+                x = 2 * m - 1 - x;
+                flip |= 1 << a;
+            }
+            c3[a] = x;
+        }
+        return cell(c3[0], c3[1], c3[2]);
+    }
     long idx(int i, int j, int k) const {
-        i = (i % nx + nx) % nx;
-        j = (j % ny + ny) % ny;
-        k = (k % nz + nz) % nz;
-        return ((long)k * ny + j) * nx + i;
+        int c3[3], f;
+        return nbr(i, j, k, 0, 0, 0, c3, f);
     }
     void ijk(long c, int &i, int &j, int &k) const {
         i = (int)(c % nx);
         j = (int)((c / nx) % ny);
         k = (int)(c / ((long)nx * ny));
+    }
+    /* sign of variable v's average in a ghost mirrored across the axes of flip */
+    double sval(int v, int flip) const {
+        double s = 1.0;
+        for (int a = 0; a < 3; ++a)
+            if ((flip >> a & 1) && bc[a] == 1 && v == 1 + a) s = -s;
+        return s;
+    }
+    /* sign of its derivative along axis q */
+    double sder(int v, int q, int flip) const {
+        return (flip >> q & 1) ? -sval(v, flip) : sval(v, flip);
+    }
+    /* position of a cell in the boundary plane normal to axis d */
+    long plane(int d, int i, int j, int k) const {
+        return d == 0 ? (long)j + (long)ny * k : (d == 1 ? (long)i + (long)nx * k
+                                                         : (long)i + (long)nx * j);
+    }
+    long nplane() const {
+        long a = (long)ny * nz, b = (long)nx * nz, c = (long)nx * ny;
+        return a > b ? (a > c ? a : c) : (b > c ? b : c);
     }
 };
 
@@ -39,8 +99,32 @@ Grid make_grid(const orc_params &P) {
     Grid g;
     g.nx = P.nx; g.ny = P.ny; g.nz = P.nz;
     g.n = (long)P.nx * P.ny * P.nz;
-    g.h[0] = P.Lx / P.nx; g.h[1] = P.Ly / P.ny; g.h[2] = P.Lz / P.nz;
+    const double L[3] = {P.Lx, P.Ly, P.Lz};
+    const double *hs[3] = {P.hx, P.hy, P.hz};
+    g.uniform = true;
+    for (int a = 0; a < 3; ++a) {
+        g.bc[a] = P.bc[a];
+        const int m = g.len(a);
+        g.hs[a].resize(m);
+        for (int i = 0; i < m; ++i) g.hs[a][i] = hs[a] ? hs[a][i] : L[a] / m;
+        if (hs[a]) g.uniform = false;
+    }
     return g;
+}
+
+/* Ghost face states: the mirror image of a cell's own face states across
+ * its face of normal axis d (face frame: [0..4] values, [5..9] d/dn,
+ * [10..19] d/dt1, d/dt2; component 1 is the normal momentum). */
+void mirror_face(const Grid &g, int d, const double *s, double *m, int ngp) {
+    const double sn = g.bc[d] == 1 ? -1.0 : 1.0;
+    for (int p = 0; p < ngp; ++p)
+        for (int v = 0; v < 5; ++v) {
+            const double sv = v == 1 ? sn : 1.0;
+            m[20 * p + v] = sv * s[20 * p + v];
+            m[20 * p + 5 + v] = -sv * s[20 * p + 5 + v];
+            m[20 * p + 10 + v] = sv * s[20 * p + 10 + v];
+            m[20 * p + 15 + v] = sv * s[20 * p + 15 + v];
+        }
 }
 
 const int kFaceOff[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0},
@@ -57,42 +141,46 @@ void cell_face_states(const orc_params &P, const Grid &g, const double *Q,
     const long n = g.n;
     int i, j, k;
     g.ijk(c, i, j, k);
+    const double h0[3] = {g.h(0, i), g.h(1, j), g.h(2, k)};
     if (P.scheme) {
         double q0[5], d[5 * 63];
         for (int v = 0; v < 5; ++v) {
             q0[v] = Q[v * n + c];
             double *dv = d + 63 * v;
             for (int m = 0; m < 6; ++m) {
-                const long nb = g.idx(i + kFaceOff[m][0], j + kFaceOff[m][1], k + kFaceOff[m][2]);
-                dv[m] = Q[v * n + nb] - q0[v];
+                int c3[3], fl;
+                const long nb = g.nbr(i, j, k, kFaceOff[m][0], kFaceOff[m][1], kFaceOff[m][2], c3, fl);
+                dv[m] = g.sval(v, fl) * Q[v * n + nb] - q0[v];
                 for (int a = 0; a < 3; ++a)
-                    dv[18 + 3 * m + a] = g.h[a] * G[(v * 3 + a) * n + nb];
+                    dv[18 + 3 * m + a] = g.h(a, c3[a]) * g.sder(v, a, fl) * G[(v * 3 + a) * n + nb];
             }
             for (int e = 0; e < 12; ++e) {
-                const long nb = g.idx(i + kEdgeOff[e][0], j + kEdgeOff[e][1], k + kEdgeOff[e][2]);
-                dv[6 + e] = Q[v * n + nb] - q0[v];
+                int c3[3], fl;
+                const long nb = g.nbr(i, j, k, kEdgeOff[e][0], kEdgeOff[e][1], kEdgeOff[e][2], c3, fl);
+                dv[6 + e] = g.sval(v, fl) * Q[v * n + nb] - q0[v];
                 /* tangential derivatives of the edge neighbour (R2) */
                 const int *o = kEdgeOff[e];
                 int ax[2], na = 0, ez = 0;
                 for (int a = 0; a < 3; ++a) {
                     if (o[a] != 0) ax[na++] = a; else ez = a;
                 }
-                const double da = g.h[ax[0]] * G[(v * 3 + ax[0]) * n + nb];
-                const double db = g.h[ax[1]] * G[(v * 3 + ax[1]) * n + nb];
+                const double da = g.h(ax[0], c3[ax[0]]) * g.sder(v, ax[0], fl) * G[(v * 3 + ax[0]) * n + nb];
+                const double db = g.h(ax[1], c3[ax[1]]) * g.sder(v, ax[1], fl) * G[(v * 3 + ax[1]) * n + nb];
                 dv[36 + 2 * e] = (o[ax[0]] * da - o[ax[1]] * db) / std::sqrt(2.0);
-                dv[36 + 2 * e + 1] = g.h[ez] * G[(v * 3 + ez) * n + nb];
+                dv[36 + 2 * e + 1] = g.h(ez, c3[ez]) * g.sder(v, ez, fl) * G[(v * 3 + ez) * n + nb];
             }
-            for (int a = 0; a < 3; ++a) dv[60 + a] = g.h[a] * G[(v * 3 + a) * n + c];
+            for (int a = 0; a < 3; ++a) dv[60 + a] = h0[a] * G[(v * 3 + a) * n + c];
         }
-        recon5_cell(q0, d, g.h[0], g.h[1], g.h[2], P.nonlinear, o, chi5);
+        recon5_cell(q0, d, h0[0], h0[1], h0[2], P.nonlinear, o, chi5);
     } else {
         double q7[35];
         for (int v = 0; v < 5; ++v) q7[v] = Q[v * n + c];
         for (int m = 0; m < 6; ++m) {
-            const long nb = g.idx(i + kFaceOff[m][0], j + kFaceOff[m][1], k + kFaceOff[m][2]);
-            for (int v = 0; v < 5; ++v) q7[5 * (m + 1) + v] = Q[v * n + nb];
+            int c3[3], fl;
+            const long nb = g.nbr(i, j, k, kFaceOff[m][0], kFaceOff[m][1], kFaceOff[m][2], c3, fl);
+            for (int v = 0; v < 5; ++v) q7[5 * (m + 1) + v] = g.sval(v, fl) * Q[v * n + nb];
         }
-        recon2_cell(q7, g.h[0], g.h[1], g.h[2], P.nonlinear, o, nullptr);
+        recon2_cell(q7, h0[0], h0[1], h0[2], P.nonlinear, o, nullptr);
     }
 }
 
@@ -134,42 +222,72 @@ int face_record(const orc_params &P, int d, const double *sl_all, const double *
     return err;
 }
 
+/* Records of every face: rec [3][30][cells] for the faces on each cell's
+ * low side, rec_hi [3][30][np] for the high boundary of a non-periodic
+ * axis. A boundary face sees the cell inside and its mirror ghost. */
 int face_fluxes(const orc_params &P, const Grid &g, const std::vector<double> &fs,
-                double dt, double *rec) {
+                double dt, double *rec, double *rec_hi) {
     const int ngp = P.scheme ? 4 : 1;
-    const long n = g.n;
+    const long n = g.n, np = g.nplane();
     int err = 0;
     for (int d = 0; d < 3; ++d) {
 #pragma omp parallel for num_threads(nthreads(P)) schedule(static)
         for (long c = 0; c < n; ++c) {
             int i, j, k;
             g.ijk(c, i, j, k);
-            const long left = g.idx(i - (d == 0), j - (d == 1), k - (d == 2));
-            double r30[30];
-            const int rc = face_record(P, d, &fs[((size_t)left * 6 + 2 * d + 1) * ngp * 20],
-                                       &fs[((size_t)c * 6 + 2 * d) * ngp * 20], dt, r30);
+            const int cd = d == 0 ? i : (d == 1 ? j : k);
+            double r30[30], ghost[4 * 20];
+            const double *sr = &fs[((size_t)c * 6 + 2 * d) * ngp * 20];
+            const double *sl;
+            if (g.bc[d] != 0 && cd == 0) {
+                mirror_face(g, d, sr, ghost, ngp);
+                sl = ghost;
+            } else {
+                const long left = g.idx(i - (d == 0), j - (d == 1), k - (d == 2));
+                sl = &fs[((size_t)left * 6 + 2 * d + 1) * ngp * 20];
+            }
+            int rc = face_record(P, d, sl, sr, dt, r30);
+            for (int q = 0; q < 30; ++q) rec[((size_t)d * 30 + q) * n + c] = r30[q];
+            if (g.bc[d] != 0 && cd == g.len(d) - 1) {
+                const double *sh = &fs[((size_t)c * 6 + 2 * d + 1) * ngp * 20];
+                mirror_face(g, d, sh, ghost, ngp);
+                const int rc2 = face_record(P, d, sh, ghost, dt, r30);
+                if (rc2) rc = rc2;
+                for (int q = 0; q < 30; ++q)
+                    rec_hi[((size_t)d * 30 + q) * np + g.plane(d, i, j, k)] = r30[q];
+            }
             if (rc) {
 #pragma omp atomic write
                 err = rc;
             }
-            for (int q = 0; q < 30; ++q) rec[((size_t)d * 30 + q) * n + c] = r30[q];
         }
     }
     return err;
 }
 
+/* record value q of the face on cell c's high side along d */
+double high_rec(const Grid &g, const double *rec, const double *rec_hi, int d, int q, long c) {
+    int i, j, k;
+    g.ijk(c, i, j, k);
+    const int cd = d == 0 ? i : (d == 1 ? j : k);
+    if (g.bc[d] != 0 && cd == g.len(d) - 1)
+        return rec_hi[((size_t)d * 30 + q) * g.nplane() + g.plane(d, i, j, k)];
+    const long hi = g.idx(i + (d == 0), j + (d == 1), k + (d == 2));
+    return rec[((size_t)d * 30 + q) * g.n + hi];
+}
+
 /* L = -(1/|Omega|) sum_faces F.n S (Eq. semi), and its time derivative. */
-void operator_L(const Grid &g, const double *rec, double *L, double *Lt) {
+void operator_L(const Grid &g, const double *rec, const double *rec_hi, double *L, double *Lt) {
     const long n = g.n;
     for (long c = 0; c < n; ++c) {
         int i, j, k;
         g.ijk(c, i, j, k);
+        const double h0[3] = {g.h(0, i), g.h(1, j), g.h(2, k)};
         for (int v = 0; v < 5; ++v) {
             double s = 0.0, st = 0.0;
             for (int d = 0; d < 3; ++d) {
-                const long hi = g.idx(i + (d == 0), j + (d == 1), k + (d == 2));
-                s += (rec[((size_t)d * 30 + v) * n + hi] - rec[((size_t)d * 30 + v) * n + c]) / g.h[d];
-                st += (rec[((size_t)d * 30 + 5 + v) * n + hi] - rec[((size_t)d * 30 + 5 + v) * n + c]) / g.h[d];
+                s += (high_rec(g, rec, rec_hi, d, v, c) - rec[((size_t)d * 30 + v) * n + c]) / h0[d];
+                st += (high_rec(g, rec, rec_hi, d, 5 + v, c) - rec[((size_t)d * 30 + 5 + v) * n + c]) / h0[d];
             }
             L[v * n + c] = -s;
             Lt[v * n + c] = -st;
@@ -193,8 +311,11 @@ double time_step(const orc_params &P, const Grid &g, const double *Q) {
         const Prim p = primitive(W, P.gamma);
         const double cs = std::sqrt(P.gamma * p.p / p.rho);
         const double vel[3] = {p.U, p.V, p.W};
+        int i, j, k;
+        g.ijk(c, i, j, k);
+        const double h0[3] = {g.h(0, i), g.h(1, j), g.h(2, k)};
         for (int d = 0; d < 3; ++d) {
-            const double r = (std::fabs(vel[d]) + cs) / g.h[d];
+            const double r = (std::fabs(vel[d]) + cs) / h0[d];
             if (r > rate) rate = r;
         }
         const double nu = viscosity(P, p.rho, p.p) / p.rho;
@@ -202,7 +323,9 @@ double time_step(const orc_params &P, const Grid &g, const double *Q) {
     }
     double dt = P.cfl / rate;
     if (!P.inviscid && numax > 0.0) {
-        const double hmin = std::fmin(g.h[0], std::fmin(g.h[1], g.h[2]));
+        double hmin = INFINITY;  /* the smallest cell size of the grid */
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < g.len(a); ++i) hmin = std::fmin(hmin, g.h(a, i));
         const double dv = P.cfl * hmin * hmin / (3.0 * numax);
         if (dv < dt) dt = dv;
     }
@@ -262,14 +385,15 @@ extern "C" int orc_face_record(const orc_params *P, int d, const double *sl, con
 }
 
 extern "C" int orc_stage(const orc_params *P, const double *Q, const double *G,
-                         double dt, double *L, double *Lt, double *faces) {
+                         double dt, double *L, double *Lt, double *faces, double *faces_hi) {
     const Grid g = make_grid(*P);
     std::vector<double> fs;
     face_states(*P, g, Q, G, fs);
-    std::vector<double> rec((size_t)3 * 30 * g.n);
-    const int rc = face_fluxes(*P, g, fs, dt, rec.data());
-    operator_L(g, rec.data(), L, Lt);
+    std::vector<double> rec((size_t)3 * 30 * g.n), rec_hi((size_t)3 * 30 * g.nplane(), 0.0);
+    const int rc = face_fluxes(*P, g, fs, dt, rec.data(), rec_hi.data());
+    operator_L(g, rec.data(), rec_hi.data(), L, Lt);
     if (faces) std::memcpy(faces, rec.data(), sizeof(double) * rec.size());
+    if (faces_hi) std::memcpy(faces_hi, rec_hi.data(), sizeof(double) * rec_hi.size());
     return rc;
 }
 
@@ -283,6 +407,7 @@ extern "C" int orc_run(const orc_params *P, double *Q, double *G, int nsteps,
     const Grid g = make_grid(*P);
     const long n = g.n;
     std::vector<double> fs, rec((size_t)3 * 30 * n), L(5 * n), Lt(5 * n);
+    std::vector<double> rec_hi((size_t)3 * 30 * g.nplane(), 0.0);
     std::vector<double> Qs, Gs, L1, Lt1, S1;
     for (int step = 0; step < nsteps; ++step) {
         double dt = time_step(*P, g, Q);
@@ -291,18 +416,18 @@ extern "C" int orc_run(const orc_params *P, double *Q, double *G, int nsteps,
         if (P->scheme == 0) {
             /* GKS-2nd: Q^{n+1} = Q^n + dt L + dt^2/2 dL/dt (Sec. 3.4) */
             face_states(*P, g, Q, nullptr, fs);
-            const int rc = face_fluxes(*P, g, fs, dt, rec.data());
+            const int rc = face_fluxes(*P, g, fs, dt, rec.data(), rec_hi.data());
             if (rc) return rc;
-            operator_L(g, rec.data(), L.data(), Lt.data());
+            operator_L(g, rec.data(), rec_hi.data(), L.data(), Lt.data());
             for (long q = 0; q < 5 * n; ++q) Q[q] += dt * L[q] + 0.5 * dt * dt * Lt[q];
         } else {
             /* CGKS-5th: two-stage fourth-order update (Sec. 3.4) */
             face_states(*P, g, Q, G, fs);
-            int rc = face_fluxes(*P, g, fs, dt, rec.data());
+            int rc = face_fluxes(*P, g, fs, dt, rec.data(), rec_hi.data());
             if (rc) return rc;
             L1.resize(5 * n);
             Lt1.resize(5 * n);
-            operator_L(g, rec.data(), L1.data(), Lt1.data());
+            operator_L(g, rec.data(), rec_hi.data(), L1.data(), Lt1.data());
             Qs.resize(5 * n);
             Gs.resize(15 * n);
             S1.resize(15 * n);
@@ -313,34 +438,34 @@ extern "C" int orc_run(const orc_params *P, double *Q, double *G, int nsteps,
             for (long c = 0; c < n; ++c) {
                 int i, j, k;
                 g.ijk(c, i, j, k);
+                const double h0[3] = {g.h(0, i), g.h(1, j), g.h(2, k)};
                 for (int d = 0; d < 3; ++d) {
-                    const long hi = g.idx(i + (d == 0), j + (d == 1), k + (d == 2));
                     for (int v = 0; v < 5; ++v) {
-                        const double ql = rec[((size_t)d * 30 + 10 + v) * n + hi];
-                        const double qlt = rec[((size_t)d * 30 + 15 + v) * n + hi];
+                        const double ql = high_rec(g, rec.data(), rec_hi.data(), d, 10 + v, c);
+                        const double qlt = high_rec(g, rec.data(), rec_hi.data(), d, 15 + v, c);
                         const double qr = rec[((size_t)d * 30 + 20 + v) * n + c];
                         const double qrt = rec[((size_t)d * 30 + 25 + v) * n + c];
-                        Gs[(v * 3 + d) * n + c] = ((ql + 0.5 * dt * qlt) - (qr + 0.5 * dt * qrt)) / g.h[d];
-                        S1[(v * 3 + d) * n + c] = (ql - qr) / g.h[d];
+                        Gs[(v * 3 + d) * n + c] = ((ql + 0.5 * dt * qlt) - (qr + 0.5 * dt * qrt)) / h0[d];
+                        S1[(v * 3 + d) * n + c] = (ql - qr) / h0[d];
                     }
                 }
             }
             face_states(*P, g, Qs.data(), Gs.data(), fs);
-            rc = face_fluxes(*P, g, fs, dt, rec.data());
+            rc = face_fluxes(*P, g, fs, dt, rec.data(), rec_hi.data());
             if (rc) return rc;
-            operator_L(g, rec.data(), L.data(), Lt.data());
+            operator_L(g, rec.data(), rec_hi.data(), L.data(), Lt.data());
             for (long q = 0; q < 5 * n; ++q)
                 Q[q] = Q[q] + dt * L1[q] + dt * dt / 6.0 * (Lt1[q] + 2.0 * Lt[q]);
             /* Q_G^{n+1} = Q_G^n + dt (dQ_G/dt at the second stage) */
             for (long c = 0; c < n; ++c) {
                 int i, j, k;
                 g.ijk(c, i, j, k);
+                const double h0[3] = {g.h(0, i), g.h(1, j), g.h(2, k)};
                 for (int d = 0; d < 3; ++d) {
-                    const long hi = g.idx(i + (d == 0), j + (d == 1), k + (d == 2));
                     for (int v = 0; v < 5; ++v) {
-                        const double qlt = rec[((size_t)d * 30 + 15 + v) * n + hi];
+                        const double qlt = high_rec(g, rec.data(), rec_hi.data(), d, 15 + v, c);
                         const double qrt = rec[((size_t)d * 30 + 25 + v) * n + c];
-                        G[(v * 3 + d) * n + c] = S1[(v * 3 + d) * n + c] + dt * (qlt - qrt) / g.h[d];
+                        G[(v * 3 + d) * n + c] = S1[(v * 3 + d) * n + c] + dt * (qlt - qrt) / h0[d];
                     }
                 }
             }
@@ -355,13 +480,23 @@ extern "C" int orc_diagnostics(const orc_params *P, const double *Q,
                                const double *G, double *out) {
     const Grid g = make_grid(*P);
     const long n = g.n;
-    const double vol = g.h[0] * g.h[1] * g.h[2];
-    const double Omega = vol * n;
+    /* the domain's volume: cells of one size (uniform grid), or the sum of
+     * the cell volumes (stretched) */
+    double Omega = g.h(0, 0) * g.h(1, 0) * g.h(2, 0) * n;
+    if (!g.uniform) {
+        Omega = 0.0;
+        for (long c = 0; c < n; ++c) {
+            int i, j, k;
+            g.ijk(c, i, j, k);
+            Omega += g.h(0, i) * g.h(1, j) * g.h(2, k);
+        }
+    }
     double ek = 0, es = 0, ed = 0, rmin = INFINITY, pmin = INFINITY, bad = 0, smax = 0;
     double sums[5] = {0, 0, 0, 0, 0};
     for (long c = 0; c < n; ++c) {
         int i, j, k;
         g.ijk(c, i, j, k);
+        const double vol = g.h(0, i) * g.h(1, j) * g.h(2, k);
         double W[5];
         for (int v = 0; v < 5; ++v) {
             W[v] = Q[v * n + c];
@@ -385,9 +520,14 @@ extern "C" int orc_diagnostics(const orc_params *P, const double *Q,
                 if (G) {
                     dQ[v][d] = G[(v * 3 + d) * n + c];
                 } else {
-                    const long hi = g.idx(i + (d == 0), j + (d == 1), k + (d == 2));
-                    const long lo = g.idx(i - (d == 0), j - (d == 1), k - (d == 2));
-                    dQ[v][d] = (Q[v * n + hi] - Q[v * n + lo]) / (2.0 * g.h[d]);
+                    /* centres of the two neighbours: h_c + (h_hi + h_lo)/2 apart */
+                    int chi[3], clo[3], fhi, flo;
+                    const long hi = g.nbr(i, j, k, d == 0, d == 1, d == 2, chi, fhi);
+                    const long lo = g.nbr(i, j, k, -(d == 0), -(d == 1), -(d == 2), clo, flo);
+                    const int cd = d == 0 ? i : (d == 1 ? j : k);
+                    const double dist = g.uniform ? 2.0 * g.h(d, 0)
+                                                  : g.h(d, cd) + 0.5 * (g.h(d, chi[d]) + g.h(d, clo[d]));
+                    dQ[v][d] = (g.sval(v, fhi) * Q[v * n + hi] - g.sval(v, flo) * Q[v * n + lo]) / dist;
                 }
             }
         double du[3][3];  /* du[a][d] = d U_a / dx_d */

@@ -42,13 +42,46 @@ class Grid:
     n: tuple[int, int, int]
     L: tuple[float, float, float]
     origin: tuple[float, float, float] = (0.0, 0.0, 0.0)
+    # stretched mesh: the n[d] + 1 face coordinates of each axis (None:
+    # uniform cells of size L/n)
+    edges: tuple | None = None
 
     @property
     def h(self):
         return tuple(self.L[d] / self.n[d] for d in range(3))
 
     def faces(self, d):
+        if self.edges is not None:
+            return np.asarray(self.edges[d], dtype=float)
         return self.origin[d] + self.h[d] * np.arange(self.n[d] + 1)
+
+    def widths(self, d):
+        """Cell sizes along axis d."""
+        if self.edges is not None:
+            return np.diff(self.faces(d))
+        return np.full(self.n[d], self.h[d])
+
+    @property
+    def spacing(self):
+        """Per-axis cell sizes for a stretched mesh, else (None, None, None)."""
+        if self.edges is None:
+            return (None, None, None)
+        return tuple(self.widths(d) for d in range(3))
+
+
+def stretched_edges(n, length, amp, x0=0.0):
+    """Face coordinates x(s) = x0 + length (s + amp sin(2 pi s)/(2 pi)),
+    s = 0, 1/n, ..., 1: a smooth periodic stretching (|amp| < 1), cells
+    (1 - amp)..(1 + amp) times the mean, mirror-symmetric about the middle."""
+    s = np.arange(n + 1) / n
+    return x0 + length * (s + amp * np.sin(2 * np.pi * s) / (2 * np.pi))
+
+
+def grid_from_edges(edges):
+    edges = tuple(np.asarray(e, dtype=float) for e in edges)
+    n = tuple(len(e) - 1 for e in edges)
+    L = tuple(float(e[-1] - e[0]) for e in edges)
+    return Grid(n, L, tuple(float(e[0]) for e in edges), edges)
 
 
 def _avg1(f, grid: Grid, d: int):
@@ -61,10 +94,12 @@ def _avg1(f, grid: Grid, d: int):
 
 
 def _dif1(f, grid: Grid, d: int):
-    """(f(x_{i+1/2}) - f(x_{i-1/2}))/h along axis d."""
+    """(f(x_{i+1/2}) - f(x_{i-1/2}))/h_i along axis d."""
     xf = grid.faces(d)
     v = f(xf)
-    return (v[1:] - v[:-1]) / grid.h[d]
+    if grid.edges is None:
+        return (v[1:] - v[:-1]) / grid.h[d]
+    return (v[1:] - v[:-1]) / grid.widths(d)
 
 
 # A separable field is a list of (coef, fx, fy, fz) with fi callables.
@@ -119,14 +154,17 @@ def _conserved(grid, rho, u, v, w, p, gamma):
 
 
 def taylor_green(n=16, *, Ma=0.1, gamma=1.4, rho0=1.0, U0=1.0, L=1.0,
-                 rho_form="uniform"):
+                 rho_form="uniform", edges=None):
     """Subsonic Taylor-Green vortex (Sec. 4.1) on [0, 2 pi L]^3.
 
     rho_form = "uniform": rho = rho0, p = p0 + rho0 U0^2/16 (...)(...);
     rho_form = "paper":   rho and p both scaled by 1 + gamma Ma^2/16 (...)(...).
+    edges: face coordinates per axis (a stretched mesh or a sub-box such as
+    the octant [0, pi L]^3 bounded by the vortex's symmetry planes); n is
+    then ignored.
     """
     nn = (n, n, n) if np.isscalar(n) else tuple(n)
-    grid = Grid(nn, (2 * np.pi * L,) * 3)
+    grid = Grid(nn, (2 * np.pi * L,) * 3) if edges is None else grid_from_edges(edges)
     p0 = rho0 * U0 * U0 / (gamma * Ma * Ma)
     s, c = (lambda x: np.sin(x / L)), (lambda x: np.cos(x / L))
     c2 = lambda x: np.cos(2 * x / L)
@@ -163,13 +201,14 @@ def taylor_green_supersonic(n=16, *, Ma=2.0, gamma=1.4, rho0=1.0, p0=1.0, L=1.0)
 
 
 def advection(n=16, *, amp=0.2, gamma=1.4, vel=(1.0, 1.0, 1.0), p=1.0,
-              dims=3, t=0.0):
+              dims=3, t=0.0, edges=None):
     """rho = 1 + amp sin(x + y + z - (U + V + W) t) (dims = 3) or
     rho = 1 + amp sin(x + y - (U + V) t) on an n x n x 1 grid (dims = 2,
     W = 0, the z extent one cell of size 2 pi/n), uniform velocity and
     pressure; t > 0 gives the exact translated solution."""
     if dims == 2:
-        grid = Grid((n, n, 1), (2 * np.pi, 2 * np.pi, 2 * np.pi / n))
+        grid = (Grid((n, n, 1), (2 * np.pi, 2 * np.pi, 2 * np.pi / n)) if edges is None
+                else grid_from_edges(edges))
         vel = (vel[0], vel[1], 0.0)
         ph = -(vel[0] + vel[1]) * t
         s = lambda x: np.sin(x + ph)
@@ -177,7 +216,7 @@ def advection(n=16, *, amp=0.2, gamma=1.4, vel=(1.0, 1.0, 1.0), p=1.0,
         sxyz = [(1.0, s, np.cos, _one), (1.0, c, np.sin, _one)]
     else:
         nn = (n, n, n) if np.isscalar(n) else tuple(n)
-        grid = Grid(nn, (2 * np.pi,) * 3)
+        grid = Grid(nn, (2 * np.pi,) * 3) if edges is None else grid_from_edges(edges)
         ph = -(vel[0] + vel[1] + vel[2]) * t
         s = lambda x: np.sin(x + ph)
         c = lambda x: np.cos(x + ph)
