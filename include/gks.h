@@ -2,7 +2,8 @@
  * gks.h -- C-ABI of the GB300 (sm_103a) CGKS-5th / GKS-2nd hot path.
  *
  * The library advances the compressible Navier-Stokes equations on a
- * periodic uniform Cartesian grid with the gas-kinetic schemes compared in
+ * Cartesian grid (periodic or with symmetry / outflow boundaries, uniform
+ * or stretched along each axis) with the gas-kinetic schemes compared in
  * Yang, Zhao & Xu, "Performance evaluation of high-order compact and
  * second-order gas-kinetic schemes in compressible flow simulations":
  * CGKS-5th (Sec. 3.2: compact fifth-order reconstruction with GENO weights,
@@ -50,6 +51,12 @@ enum {
 
 enum { GKS_SCHEME_GKS2 = 0, GKS_SCHEME_CGKS5 = 1 };
 enum { GKS_PREC_FP64 = 0, GKS_PREC_MIXED = 1 };
+/* Boundary of one axis. A ghost cell beyond a non-periodic boundary is the
+ * mirror image of the cell inside it: average s Q, derivative along the
+ * normal -s dQ/dn, along the boundary s dQ/dt, with s = -1 for the normal
+ * momentum of a symmetry plane (a free-slip, adiabatic wall) and s = +1
+ * otherwise (outflow: zero normal derivative at the boundary). */
+enum { GKS_BC_PERIODIC = 0, GKS_BC_SYMMETRY = 1, GKS_BC_OUTFLOW = 2 };
 
 typedef struct gks_ctx gks_ctx; /* opaque; created by gks_init */
 
@@ -75,6 +82,18 @@ typedef struct {
                         also reconstructs the plane below it); the results
                         equal the whole-grid ones bit for bit.           */
     int reserved;    /* set to 0                                            */
+    int bc[3];       /* GKS_BC_* per axis (x, y, z); default periodic        */
+    int reserved2;   /* set to 0                                            */
+    const double *h[3]; /* stretched mesh (Sec. 3.2, last paragraph): HOST
+                        arrays of the nx, ny, nz cell sizes of each axis
+                        (copied by gks_init; NULL: uniform L/n, and Lx, Ly,
+                        Lz are then the box; an axis with sizes ignores its
+                        L). Each cell is mapped to the one reference cell:
+                        its stencil is taken in index coordinates, the
+                        neighbours' gradients scaled by their own sizes,
+                        and the derivatives mapped back with 1/h.
+                        Non-periodic or stretched grids run the general
+                        kernels and have no learned indicator.             */
 } gks_options;
 
 /* Fill *opt with the defaults: CGKS-5th, nonlinear, FP64, no indicator,
@@ -105,7 +124,9 @@ const char *gks_strerror(int code);
  * 6 faces x K Gauss points x 20 components x nx*ny*nz cells, K = 4
  * (CGKS-5th) or 1 (GKS-2nd), 8 bytes each (FP64) or 4 (mixed). */
 size_t gks_face_state_bytes(const gks_ctx *ctx);
-/* Bytes of the face-flux records written by gks_flux: 3 x 30 x cells x 8. */
+/* Bytes of the face-flux records written by gks_flux: 3 x 30 x cells x 8,
+ * plus, on a grid with a non-periodic or stretched axis, 3 x 30 x np x 8
+ * for the faces on the high boundary (np = max(ny nz, nx nz, nx ny)). */
 size_t gks_face_flux_bytes(const gks_ctx *ctx);
 /* z-planes per slab of gks_step's reconstruction + flux (see slab_planes in
  * gks_options): 0 when the context's face-state buffer holds the whole grid,
@@ -150,7 +171,11 @@ int gks_reconstruct(gks_ctx *ctx, const double *Q, const double *gradQ,
  * the face on the low-d side of cell c, element (d*30 + q)*cells + c:
  *   F^n(5), F_t^n(5), Q^l(5), dQ^l/dt(5), Q^r(5), dQ^r/dt(5)
  * in the global frame (the interface values only for CGKS-5th; GKS-2nd
- * leaves q 10..29 untouched). */
+ * leaves q 10..29 untouched). On a non-periodic axis d the face on the low
+ * boundary pairs the cell with its mirror ghost, and the faces on the high
+ * boundary follow the 90 x cells records: element
+ * 90*cells + (d*30 + q)*np + p, p = j + ny k (d = 0), i + nx k (d = 1),
+ * i + nx j (d = 2). */
 int gks_flux(gks_ctx *ctx, const double *Q, const void *face_states,
              const double *dt_dev, double *face_flux);
 

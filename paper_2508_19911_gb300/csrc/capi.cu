@@ -3,6 +3,7 @@
 // recon.cu, flux.cu and update.cu on the caller's stream.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -34,6 +35,7 @@ struct gks_ctx {
     double *partials;
     int diag_blocks;
     double *hQ, *hG, *hT;  // device state of gks_step_host (allocated on its first call)
+    double *hsz;           // stretched mesh: the nx + ny + nz cell sizes (device)
     int timing;            // gks_kernel_timing: record events around the step's launches
     cudaEvent_t t_open;    // event before the launch being timed
     std::vector<struct KernelRec> *t_recs;  // (kind, start, end) of the timed launches
@@ -152,6 +154,7 @@ void gks_destroy(gks_ctx *c) {
     cudaFree(c->hQ);
     cudaFree(c->hG);
     cudaFree(c->hT);
+    cudaFree(c->hsz);
     time_clear(c);
     delete c->t_recs;
     if (prev >= 0) cudaSetDevice(prev);
@@ -175,6 +178,16 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
     if (o.mu_law < 0 || o.mu_law > 1 || !(o.C_tau >= 0.0) || !(o.eps_tau >= 0.0) ||
         !(o.T_ref > 0.0) || o.slab_planes < 0)
         return GKS_ERR_ARG;
+    const int len[3] = {nx, ny, nz};
+    bool general = false;
+    for (int a = 0; a < 3; ++a) {
+        if (o.bc[a] < GKS_BC_PERIODIC || o.bc[a] > GKS_BC_OUTFLOW) return GKS_ERR_ARG;
+        if (o.bc[a] != GKS_BC_PERIODIC || o.h[a]) general = true;
+        if (o.h[a])
+            for (int i = 0; i < len[a]; ++i)
+                if (!(o.h[a][i] > 0.0) || !std::isfinite(o.h[a][i])) return GKS_ERR_ARG;
+    }
+    if (general && o.indicator) return GKS_ERR_ARG;
     const long long n = (long long)nx * ny * nz;
     if (n > (1LL << 31)) return GKS_ERR_ARG;
 
@@ -186,6 +199,24 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
     c->opt = o;
     c->g.nx = nx; c->g.ny = ny; c->g.nz = nz; c->g.n = n;
     c->g.h[0] = Lx / nx; c->g.h[1] = Ly / ny; c->g.h[2] = Lz / nz;
+    if (general) {
+        c->g.general = 1;
+        c->g.np = std::max((long long)ny * nz, std::max((long long)nx * nz, (long long)nx * ny));
+        double hmin = INFINITY, ext[3];
+        for (int a = 0; a < 3; ++a) {
+            c->g.bc[a] = o.bc[a];
+            ext[a] = 0.0;
+            for (int i = 0; i < len[a]; ++i) {
+                const double hh = o.h[a] ? o.h[a][i] : c->g.h[a];
+                hmin = std::min(hmin, hh);
+                ext[a] += hh;
+            }
+        }
+        c->g.hmin = hmin;
+        const bool stretched = o.h[0] || o.h[1] || o.h[2];
+        c->g.volume = stretched ? ext[0] * ext[1] * ext[2]
+                                : c->g.h[0] * c->g.h[1] * c->g.h[2] * (double)n;
+    }
     c->P.gamma = gamma; c->P.Pr = Pr; c->P.mu0 = mu; c->P.cfl = cfl;
     c->P.C_tau = o.C_tau; c->P.eps_tau = o.eps_tau; c->P.T_ref = o.T_ref;
     c->P.Nint = (5.0 - 3.0 * gamma) / (gamma - 1.0);
@@ -215,8 +246,9 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
     }
     c->slab_planes = planes >= nz ? 0 : (int)planes;
     const long long fs_cells = c->slab_planes ? nxy * (c->slab_planes + 1) : n;
+    const size_t nrec = (size_t)90 * n + (c->g.general ? (size_t)90 * c->g.np : 0);
     if ((rc = dalloc((char **)&c->fs, fs_per_cell * fs_cells)) ||
-        (rc = dalloc(&c->frec, (size_t)90 * n)) ||
+        (rc = dalloc(&c->frec, nrec)) ||
         (rc = dalloc(&c->scal, (size_t)3 + 12)) ||
         (rc = dalloc(&c->status, 1)) ||
         (rc = dalloc(&c->skips, 1)) ||
@@ -236,9 +268,28 @@ int gks_init(gks_ctx **out, double gamma, double Pr, double mu, double cfl, int 
     if (cudaMemsetAsync(c->scal, 0, sizeof(double) * 15, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->status, 0, sizeof(int), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->skips, 0, sizeof(unsigned long long), c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->frec, 0, sizeof(double) * 90 * n, c->stream) != cudaSuccess) {
+        cudaMemsetAsync(c->frec, 0, sizeof(double) * nrec, c->stream) != cudaSuccess) {
         gks_destroy(c);
         return GKS_ERR_CUDA;
+    }
+    if (o.h[0] || o.h[1] || o.h[2]) {
+        // the cell sizes, copied synchronously (the host arrays need not
+        // outlive this call)
+        std::vector<double> hh;
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < len[a]; ++i) hh.push_back(o.h[a] ? o.h[a][i] : c->g.h[a]);
+        if ((rc = dalloc(&c->hsz, hh.size()))) {
+            gks_destroy(c);
+            return rc;
+        }
+        if (cudaMemcpy(c->hsz, hh.data(), sizeof(double) * hh.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+            gks_destroy(c);
+            return GKS_ERR_CUDA;
+        }
+        c->g.hs[0] = c->hsz;
+        c->g.hs[1] = c->hsz + nx;
+        c->g.hs[2] = c->hsz + nx + ny;
     }
     *out = c;
     return GKS_OK;
@@ -251,7 +302,8 @@ size_t gks_face_state_bytes(const gks_ctx *c) {
 int gks_slab_planes(const gks_ctx *c) { return c ? c->slab_planes : -1; }
 
 size_t gks_face_flux_bytes(const gks_ctx *c) {
-    return c ? (size_t)90 * c->g.n * sizeof(double) : 0;
+    if (!c) return 0;
+    return ((size_t)90 * c->g.n + (c->g.general ? (size_t)90 * c->g.np : 0)) * sizeof(double);
 }
 
 int gks_compute_dt(gks_ctx *c, const double *Q, double *dt_dev) {

@@ -13,7 +13,21 @@ constexpr int kStatusNonfinite = 2;
 struct GridDesc {
     int nx, ny, nz;
     long long n;     // cells
-    double h[3];     // cell sizes
+    double h[3];     // cell sizes of a uniform grid
+    // General grids (general = 1; the ensemble and uniform periodic grids
+    // leave it 0): per-axis cell sizes on the device (nullptr: the uniform
+    // h[a]), boundary kind per axis (0 periodic, 1 symmetry plane, 2
+    // outflow: a mirror ghost cell, the normal momentum negated for 1),
+    // the smallest cell size, the domain's volume and the size of the
+    // boundary-face planes np = max(ny nz, nx nz, nx ny). The records of
+    // the faces on the high boundary of a non-periodic axis d follow the
+    // [3][30][n] face records as [3][30][np], at plane position j + ny k
+    // (d = 0), i + nx k (d = 1), i + nx j (d = 2).
+    const double *hs[3];
+    double hmin, volume;
+    long long np;
+    int bc[3];
+    int general;
 };
 
 struct PhysParams {
@@ -45,6 +59,53 @@ __host__ __device__ __forceinline__ long long cell_index(const GridDesc &g, int 
 
 __device__ __forceinline__ int wrap(int i, int n) {
     return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+__host__ __device__ __forceinline__ int axis_len(const GridDesc &g, int a) {
+    return a == 0 ? g.nx : (a == 1 ? g.ny : g.nz);
+}
+
+// cell size along axis a at coordinate i
+__device__ __forceinline__ double cell_h(const GridDesc &g, int a, int i) {
+    return g.hs[a] ? __ldg(g.hs[a] + i) : g.h[a];
+}
+
+// Coordinate along axis a of the neighbour at x = i + offset: wrapped on a
+// periodic axis, mirrored into the grid across a boundary (bit a of flip
+// set: the neighbour is the ghost image of that cell).
+__device__ __forceinline__ int nb_coord(const GridDesc &g, int a, int x, int &flip) {
+    const int m = axis_len(g, a);
+    if (g.bc[a] == 0) return wrap(x, m);
+    if (x < 0) {
+        flip |= 1 << a;
+        return -1 - x;
+    }
+    if (x >= m) {
+        flip |= 1 << a;
+        return 2 * m - 1 - x;
+    }
+    return x;
+}
+
+// Does the average of conserved variable v change sign in a ghost mirrored
+// across the axes of flip? (the momentum normal to a symmetry plane)
+__device__ __forceinline__ bool ghost_neg(const GridDesc &g, int v, int flip) {
+    if (v < 1 || v > 3) return false;
+    return ((flip >> (v - 1)) & 1) && g.bc[v - 1] == 1;
+}
+
+// position of a cell in the boundary plane normal to axis d
+__device__ __forceinline__ long long plane_pos(const GridDesc &g, int d, int i, int j, int k) {
+    return d == 0 ? (long long)j + (long long)g.ny * k
+                  : (d == 1 ? (long long)i + (long long)g.nx * k : (long long)i + (long long)g.nx * j);
+}
+
+// Mirror of face-frame component q (0..19: values, d/dn, d/dt1, d/dt2 of
+// rho, rho u_n, rho u_t1, rho u_t2, rho E) across the face itself, for a
+// boundary of kind bc: negated or not.
+__host__ __device__ __forceinline__ bool mirror_neg(int q, int bc) {
+    const bool normal_mom = (q % 5) == 1 && bc == 1;
+    return (q / 5 == 1) != normal_mom;
 }
 
 // The face-state buffer holds nzb z-planes starting at the global plane zb

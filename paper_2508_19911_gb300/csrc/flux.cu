@@ -811,6 +811,10 @@ __device__ __forceinline__ int global_var(int c, int d) {
 // S.nb), the averages Q and the records at global cells (stride g.n).
 // mixed: the averages as float-float pairs Qhi, Qlo ([5][n] each, written
 // once per stage by q_to_ff_kernel)
+// bmode (general grids): 0 an interior face; 1 the low boundary face of a
+// non-periodic axis (the cell's own low face state and its mirror ghost);
+// 2 the high boundary face of cell l (its high face state and its mirror),
+// written to the boundary records after the [3][30][n] records.
 template <bool kCGKS, bool MIXED>
 __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S,
                                                 const PhysParams &P,
@@ -818,7 +822,7 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S
                                                 const float *__restrict__ Qhi,
                                                 const float *__restrict__ Qlo, double dt,
                                                 double *__restrict__ frec, int *status, int d,
-                                                long long l, int k, bool valid) {
+                                                long long l, int k, bool valid, int bmode = 0) {
     constexpr int K = kCGKS ? 4 : 1;
     const long long n = g.n, nb = S.nb;
     const long long nxy = (long long)g.nx * g.ny;
@@ -841,6 +845,10 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S
         left = (long long)wrap(gz - 1, g.nz) * nxy + ij;
     }
     constexpr int NV = kCGKS ? 30 : 10;
+    // the record's position: the right cell's low face, or a high boundary face
+    const long long rec_base = bmode == 2 ? 90 * n + plane_pos(g, d, i, j, gz) : c;
+    const long long rec_stride = bmode == 2 ? g.np : n;
+    if (bmode == 2) ll = l;  // the face state on the cell's high side
     if (!MIXED) {
         double out[30];
         const double *fs = (const double *)fsv;
@@ -851,6 +859,13 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S
         for (int q = 0; q < 20; ++q) {
             sl[q] = __ldg(pl + (long long)q * nb);
             sr[q] = __ldg(pr + (long long)q * nb);
+        }
+        if (bmode == 1) {
+#pragma unroll
+            for (int q = 0; q < 20; ++q) sl[q] = mirror_neg(q, g.bc[d]) ? -sr[q] : sr[q];
+        } else if (bmode == 2) {
+#pragma unroll
+            for (int q = 0; q < 20; ++q) sr[q] = mirror_neg(q, g.bc[d]) ? -sl[q] : sl[q];
         }
         flux_point<kCGKS>(P, sl, sr, dt, out, valid ? status : nullptr);
         if (kCGKS) {
@@ -868,7 +883,7 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S
         for (int q = 0; q < NV; ++q) {
             if (q % K != k) continue;
             const int blk = q / 5, cmp = q % 5;
-            frec[((long long)d * 30 + blk * 5 + global_var(cmp, d)) * n + c] = out[q];
+            frec[((long long)d * 30 + blk * 5 + global_var(cmp, d)) * rec_stride + rec_base] = out[q];
         }
     } else {
         ff out[30];
@@ -889,6 +904,30 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S
         for (int q = 0; q < 15; ++q) {
             dl[q] = __ldg(pl + (long long)(5 + q) * nb);
             dr[q] = __ldg(pr + (long long)(5 + q) * nb);
+        }
+        if (bmode == 2) {
+            // the high face state belongs to the cell itself (global c)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) Ql[q] = Qr[q];
+        }
+        if (bmode == 1) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const bool ng = mirror_neg(q, g.bc[d]);
+                Ql[q] = ng ? ff_neg(Qr[q]) : Qr[q];
+                ol[q] = ng ? -orr[q] : orr[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 15; ++q) dl[q] = mirror_neg(5 + q, g.bc[d]) ? -dr[q] : dr[q];
+        } else if (bmode == 2) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const bool ng = mirror_neg(q, g.bc[d]);
+                Qr[q] = ng ? ff_neg(Ql[q]) : Ql[q];
+                orr[q] = ng ? -ol[q] : ol[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 15; ++q) dr[q] = mirror_neg(5 + q, g.bc[d]) ? -dl[q] : dl[q];
         }
         flux_point_mixed<kCGKS>(P, Ql, ol, dl, Qr, orr, dr, dt, out, valid ? status : nullptr);
         if (kCGKS) {
@@ -927,15 +966,19 @@ __device__ __forceinline__ void flux_face_point(const GridDesc &g, const Slab &S
             }
             if (q < NV && (K == 1 || q % K == k)) {
                 const int blk = q / 5, cmp = q % 5;
-                frec[((long long)d * 30 + blk * 5 + global_var(cmp, d)) * n + c] = ff_to_double(x);
+                frec[((long long)d * 30 + blk * 5 + global_var(cmp, d)) * rec_stride + rec_base] =
+                    ff_to_double(x);
             }
         }
     }
 }
 
 // mixed: at most 168 registers for 3 blocks per SM (a few spills; 20%
-// faster at 128^3 than 2 blocks with 255 registers and none)
-template <bool kCGKS, bool MIXED>
+// faster at 128^3 than 2 blocks with 255 registers and none).
+// GEN (general grids): the faces of cells on the low boundary of a
+// non-periodic axis pair the cell with its mirror ghost, and the high
+// boundary faces of this buffer's cells follow the 3 x cells faces.
+template <bool kCGKS, bool MIXED, bool GEN>
 __global__ void __launch_bounds__(128, MIXED ? 3 : 1) flux_faces_kernel(GridDesc g, Slab S, PhysParams P,
                                                          const void *__restrict__ fs,
                                                          const float *__restrict__ Qhi,
@@ -947,16 +990,52 @@ __global__ void __launch_bounds__(128, MIXED ? 3 : 1) flux_faces_kernel(GridDesc
     constexpr int K = kCGKS ? 4 : 1;
     const long long nxy = (long long)g.nx * g.ny;
     const long long cnt = (long long)(S.nzb - S.p0) * nxy;  // cells whose faces are computed
-    const long long total = 3 * cnt * K;
+    long long total = 3 * cnt * K;
+    long long nbx = 0, nby = 0;
+    if constexpr (GEN) {
+        const long long planes = S.nzb - S.p0;
+        nbx = g.bc[0] ? (long long)g.ny * planes : 0;
+        nby = g.bc[1] ? (long long)g.nx * planes : 0;
+        const long long nbz = (g.bc[2] && (S.zb + S.nzb - 1) % g.nz == g.nz - 1) ? nxy : 0;
+        total += K * (nbx + nby + nbz);
+    }
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = gid < total;
     if (!valid) gid = total - 1;  // groups of K lanes are entirely in or out
     const int k = (int)(gid % K);
     const long long fc = gid / K;
-    const int d = (int)(fc / cnt);
-    const long long t = fc - (long long)d * cnt;
-    flux_face_point<kCGKS, MIXED>(g, S, P, fs, Qhi, Qlo, dt, frec, status, d, S.p0 * nxy + t, k,
-                                  valid);
+    if (!GEN || fc < 3 * cnt) {
+        const int d = (int)(fc / cnt);
+        const long long t = fc - (long long)d * cnt;
+        const long long l = S.p0 * nxy + t;
+        int bmode = 0;
+        if constexpr (GEN) {
+            if (g.bc[d]) {
+                const long long ij = l % nxy;
+                const int cd = d == 0 ? (int)(ij % g.nx)
+                                      : (d == 1 ? (int)(ij / g.nx) : (int)((S.zb + l / nxy) % g.nz));
+                if (cd == 0) bmode = 1;
+            }
+        }
+        flux_face_point<kCGKS, MIXED>(g, S, P, fs, Qhi, Qlo, dt, frec, status, d, l, k, valid,
+                                      bmode);
+    } else {
+        long long e = fc - 3 * cnt, l;
+        int d;
+        if (e < nbx) {
+            d = 0;
+            l = (S.p0 + e / g.ny) * nxy + (e % g.ny) * g.nx + (g.nx - 1);
+        } else if (e < nbx + nby) {
+            d = 1;
+            e -= nbx;
+            l = (S.p0 + e / g.nx) * nxy + (long long)(g.ny - 1) * g.nx + e % g.nx;
+        } else {
+            d = 2;
+            e -= nbx + nby;
+            l = (long long)(S.nzb - 1) * nxy + e;
+        }
+        flux_face_point<kCGKS, MIXED>(g, S, P, fs, Qhi, Qlo, dt, frec, status, d, l, k, valid, 2);
+    }
 }
 
 // Persistent ensemble flux (CGKS-5th): blocks stride over the work items
@@ -1031,36 +1110,46 @@ int launch_q_to_ff(long long m, const double *x, float *hi, float *lo, cudaStrea
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
+// threads of one flux launch: K per face, 3 faces per cell of the slab's
+// planes p0..nzb-1, and on a general grid the high boundary faces
+static long long flux_threads(const GridDesc &g, const Slab &S, int K) {
+    const long long planes = S.nzb - S.p0, nxy = (long long)g.nx * g.ny;
+    long long faces = 3 * planes * nxy;
+    if (g.general) {
+        if (g.bc[0]) faces += (long long)g.ny * planes;
+        if (g.bc[1]) faces += (long long)g.nx * planes;
+        if (g.bc[2] && (S.zb + S.nzb - 1) % g.nz == g.nz - 1) faces += nxy;
+    }
+    return faces * K;
+}
+
+template <bool MIXED, bool GEN>
+static void launch_flux_t(const GridDesc &g, const Slab &S, const PhysParams &P, const void *fs,
+                          const float *Qhi, const float *Qlo, const double *dt_dev, double *frec,
+                          int *status, cudaStream_t s) {
+    const long long total = flux_threads(g, S, P.scheme ? 4 : 1);
+    const int block = 128;
+    const unsigned grid = (unsigned)((total + block - 1) / block);
+    if (P.scheme)
+        flux_faces_kernel<true, MIXED, GEN><<<grid, block, 0, s>>>(g, S, P, fs, Qhi, Qlo, dt_dev,
+                                                                   frec, status);
+    else
+        flux_faces_kernel<false, MIXED, GEN><<<grid, block, 0, s>>>(g, S, P, fs, Qhi, Qlo, dt_dev,
+                                                                    frec, status);
+}
+
 int launch_flux_faces_mixed(const GridDesc &g, const Slab &S, const PhysParams &P,
                             const float *fs, const float *Qhi, const float *Qlo,
                             const double *dt_dev, double *frec, int *status, cudaStream_t s) {
-    const int K = P.scheme ? 4 : 1;
-    const long long total = 3 * (long long)(S.nzb - S.p0) * g.nx * g.ny * K;
-    const int block = 128;
-    const long long grid = (total + block - 1) / block;
-    if (P.scheme)
-        flux_faces_kernel<true, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Qhi, Qlo,
-                                                                        dt_dev, frec, status);
-    else
-        flux_faces_kernel<false, true><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, Qhi, Qlo,
-                                                                         dt_dev, frec, status);
+    if (g.general) launch_flux_t<true, true>(g, S, P, fs, Qhi, Qlo, dt_dev, frec, status, s);
+    else launch_flux_t<true, false>(g, S, P, fs, Qhi, Qlo, dt_dev, frec, status, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 int launch_flux_faces(const GridDesc &g, const Slab &S, const PhysParams &P, const double *fs,
                       const double *dt_dev, double *frec, int *status, cudaStream_t s) {
-    const int K = P.scheme ? 4 : 1;
-    const long long total = 3 * (long long)(S.nzb - S.p0) * g.nx * g.ny * K;
-    const int block = 128;
-    const long long grid = (total + block - 1) / block;
-    if (P.scheme)
-        flux_faces_kernel<true, false><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, nullptr,
-                                                                         nullptr, dt_dev, frec,
-                                                                         status);
-    else
-        flux_faces_kernel<false, false><<<(unsigned)grid, block, 0, s>>>(g, S, P, fs, nullptr,
-                                                                          nullptr, dt_dev, frec,
-                                                                          status);
+    if (g.general) launch_flux_t<false, true>(g, S, P, fs, nullptr, nullptr, dt_dev, frec, status, s);
+    else launch_flux_t<false, false>(g, S, P, fs, nullptr, nullptr, dt_dev, frec, status, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -66,7 +66,7 @@ extern "C" int gks_diagnostics_noalloc(const double *Q, const double *gradQ, int
     double *scratch = nullptr;
     const int rc = na_scratch(dev, &scratch);
     if (rc) return rc;
-    GridDesc g;
+    GridDesc g = {};  // uniform, periodic: the general-grid fields stay zero
     g.nx = nx; g.ny = ny; g.nz = nz; g.n = n;
     g.h[0] = Lx / nx; g.h[1] = Ly / ny; g.h[2] = Lz / nz;
     PhysParams P = {};

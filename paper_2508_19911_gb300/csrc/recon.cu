@@ -107,7 +107,8 @@ __device__ __forceinline__ float gval(const double *__restrict__ Gv, const float
     else return (float)__ldg(Gv + idx);
 }
 
-template <int K, bool VIEW>
+// GEN: a general grid (mirror ghosts, per-cell sizes; see recon_fp64.cu)
+template <int K, bool VIEW, bool GEN>
 __device__ __forceinline__ float data_col_f(const double *__restrict__ Qv,
                                             const double *__restrict__ Gv,
                                             const float *__restrict__ qh,
@@ -115,28 +116,45 @@ __device__ __forceinline__ float data_col_f(const double *__restrict__ Qv,
                                             const float *__restrict__ Gfv, long long n,
                                             long long c, const long long nbF[6],
                                             const long long nbE[12], double q0, float h0,
-                                            float l0, const float hf[3]) {
+                                            float l0, const float hf[3], const NbGeo &geo) {
     if constexpr (K < kColFaceGrad) {
         const long long nb = K < kColEdge ? nbF[K] : nbE[K - kColEdge];
+        bool neg = false;
+        if constexpr (GEN) neg = ((K < kColEdge ? geo.fF[K] : geo.fE[K - kColEdge]) >> 3) & 1;
         if constexpr (VIEW)
-            return __fadd_rn(__fsub_rn(__ldg(qh + nb), h0), __fsub_rn(__ldg(ql + nb), l0));
+            return __fadd_rn(__fsub_rn(neg_if(__ldg(qh + nb), neg), h0),
+                             __fsub_rn(neg_if(__ldg(ql + nb), neg), l0));
         else
-            return (float)(__ldg(Qv + nb) - q0);
+            return (float)(neg_if(__ldg(Qv + nb), neg) - q0);
     } else if constexpr (K < kColEdgeGrad) {
         constexpr int m = (K - kColFaceGrad) / 3, j = (K - kColFaceGrad) % 3;
-        return __fmul_rn(hf[j], gval<VIEW>(Gv, Gfv, j * n + nbF[m]));
+        if constexpr (GEN)
+            return __fmul_rn((float)geo.hm[j][face_off(m, j) + 1],
+                             neg_if(gval<VIEW>(Gv, Gfv, j * n + nbF[m]), der_neg(geo.fF[m], j)));
+        else return __fmul_rn(hf[j], gval<VIEW>(Gv, Gfv, j * n + nbF[m]));
     } else if constexpr (K < kColCentreGrad) {
         constexpr int e = (K - kColEdgeGrad) / 2;
         constexpr int ea = edge_axis_a(e), eb = edge_axis_b(e), ee = edge_axis_e(e);
         if constexpr ((K - kColEdgeGrad) % 2 == 0) {
-            const float da = __fmul_rn(hf[ea], gval<VIEW>(Gv, Gfv, ea * n + nbE[e]));
-            const float db = __fmul_rn(hf[eb], gval<VIEW>(Gv, Gfv, eb * n + nbE[e]));
+            float da, db;
+            if constexpr (GEN) {
+                da = __fmul_rn((float)geo.hm[ea][edge_off(e, ea) + 1],
+                               neg_if(gval<VIEW>(Gv, Gfv, ea * n + nbE[e]), der_neg(geo.fE[e], ea)));
+                db = __fmul_rn((float)geo.hm[eb][edge_off(e, eb) + 1],
+                               neg_if(gval<VIEW>(Gv, Gfv, eb * n + nbE[e]), der_neg(geo.fE[e], eb)));
+            } else {
+                da = __fmul_rn(hf[ea], gval<VIEW>(Gv, Gfv, ea * n + nbE[e]));
+                db = __fmul_rn(hf[eb], gval<VIEW>(Gv, Gfv, eb * n + nbE[e]));
+            }
             // o_a d_a - o_b d_b with o = +-1
             constexpr bool same = edge_off(e, ea) == edge_off(e, eb);
             const float t = same ? __fsub_rn(da, db) : __fadd_rn(da, db);
             return __fmul_rn(edge_off(e, ea) > 0 ? t : -t, (float)kRs2);
         } else {
-            return __fmul_rn(hf[ee], gval<VIEW>(Gv, Gfv, ee * n + nbE[e]));
+            if constexpr (GEN)
+                return __fmul_rn((float)geo.hm[ee][1],
+                                 neg_if(gval<VIEW>(Gv, Gfv, ee * n + nbE[e]), der_neg(geo.fE[e], ee)));
+            else return __fmul_rn(hf[ee], gval<VIEW>(Gv, Gfv, ee * n + nbE[e]));
         }
     } else {
         constexpr int j = K - kColCentreGrad;
@@ -215,7 +233,7 @@ __device__ __forceinline__ void eval_faces_f(const float *T, float *__restrict__
         }
 }
 
-template <int MODE, bool VIEW>
+template <int MODE, bool VIEW, bool GEN = false>
 __device__ __forceinline__ void recon5_mixed_cell(const float *T,
                                                   const GridDesc &g, int nonlinear,
                                                   const double *__restrict__ Q,
@@ -234,17 +252,16 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
     const int j = (int)((c / g.nx) % g.ny);
     const int k = (int)(c / ((long long)g.nx * g.ny));
     long long nbF[6], nbE[12];
-#pragma unroll
-    for (int m = 0; m < 6; ++m)
-        nbF[m] = cell_index(g, wrap(i + face_off(m, 0), g.nx), wrap(j + face_off(m, 1), g.ny),
-                            wrap(k + face_off(m, 2), g.nz));
-#pragma unroll
-    for (int e = 0; e < 12; ++e)
-        nbE[e] = cell_index(g, wrap(i + edge_off(e, 0), g.nx), wrap(j + edge_off(e, 1), g.ny),
-                            wrap(k + edge_off(e, 2), g.nz));
+    NbGeo geo;
+    stencil<GEN>(g, i, j, k, v, nbF, nbE, geo);
     // h and 1/h in FP32: the gradient entries h G are rounded to FP32 anyway
     // (only the differences of averages need FP64, for their cancellation)
-    const float hf[3] = {(float)g.h[0], (float)g.h[1], (float)g.h[2]};
+    float hf[3] = {(float)g.h[0], (float)g.h[1], (float)g.h[2]};
+    if constexpr (GEN) {
+        hf[0] = (float)geo.hm[0][1];
+        hf[1] = (float)geo.hm[1][1];
+        hf[2] = (float)geo.hm[2][1];
+    }
     const float ih[3] = {1.0f / hf[0], 1.0f / hf[1], 1.0f / hf[2]};
 
 {
@@ -273,8 +290,8 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
                 static_for<nm>([&](auto Qq) {
                     constexpr int q = decltype(Qq)::value;
                     constexpr int col = kSym.mem[r][q];
-                    ov[q] = data_col_f<col, VIEW>(Qv, Gv, qh, ql, Gfv, n, c, nbF, nbE, q0, h0, l0,
-                                                  hf);
+                    ov[q] = data_col_f<col, VIEW, GEN>(Qv, Gv, qh, ql, Gfv, n, c, nbF, nbE, q0,
+                                                       h0, l0, hf, geo);
                     constexpr float wc = (float)(col_weight(col) * col_weight(col));
                     norm2 = fmaf(wc * ov[q], ov[q], norm2);
                     if constexpr (col < kColEdge) dface[col] = ov[q];
@@ -370,8 +387,8 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
                         static_for<nm>([&](auto Qq) {
                             constexpr int q = decltype(Qq)::value;
                             constexpr int col = kSym.mem[r][q];
-                            ov[q] = data_col_f<col, VIEW>(Qv, Gv, qh, ql, Gfv, n, c, nbF, nbE, q0,
-                                                          h0, l0, hf);
+                            ov[q] = data_col_f<col, VIEW, GEN>(Qv, Gv, qh, ql, Gfv, n, c, nbF,
+                                                               nbE, q0, h0, l0, hf, geo);
                         });
                     }
                     float ds = kSym.sgn[r][0] > 0 ? ov[0] : -ov[0];
@@ -427,7 +444,7 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
 // block are adjacent tiles). The empty asm with a memory clobber at the top
 // of each tile keeps the compiler from hoisting table loads out of the tile
 // loop into registers (which spills).
-template <int MODE, bool VIEW>
+template <int MODE, bool VIEW, bool GEN = false>
 __global__ void __launch_bounds__(128) recon5_mixed_kernel(GridDesc g, Slab S, int nonlinear,
                                                            const double *__restrict__ Q,
                                                            const double *__restrict__ G,
@@ -445,9 +462,9 @@ __global__ void __launch_bounds__(128) recon5_mixed_kernel(GridDesc g, Slab S, i
         asm volatile("" ::: "memory");
         const long long l = (t / 5) * 128 + threadIdx.x;
         if (l < S.nb)
-            recon5_mixed_cell<MODE, VIEW>(sT, g, nonlinear, Q, G, Gf, Qhi, Qlo, fs, dump_x,
-                                          dump_chi, skips, slab_global(g, S, l), 5 * g.n, 0,
-                                          (int)(t % 5), S.nb, l);
+            recon5_mixed_cell<MODE, VIEW, GEN>(sT, g, nonlinear, Q, G, Gf, Qhi, Qlo, fs, dump_x,
+                                               dump_chi, skips, slab_global(g, S, l), 5 * g.n,
+                                               0, (int)(t % 5), S.nb, l);
     }
 }
 
@@ -481,6 +498,7 @@ __global__ void __launch_bounds__(128) recon5_ens_kernel(const EnsInst *__restri
     }
 }
 
+template <bool GEN>
 __global__ void __launch_bounds__(128) recon2_mixed_kernel(GridDesc g, Slab S, int nonlinear,
                                                            float eps2, const double *__restrict__ Q,
                                                            float *__restrict__ fs) {
@@ -492,18 +510,43 @@ __global__ void __launch_bounds__(128) recon2_mixed_kernel(GridDesc g, Slab S, i
     const int j = (int)((c / g.nx) % g.ny);
     const int k = (int)(c / ((long long)g.nx * g.ny));
     long long nb[6];
+    int fl[6];
+    float ih[3] = {(float)(1.0 / g.h[0]), (float)(1.0 / g.h[1]), (float)(1.0 / g.h[2])};
+    if constexpr (!GEN) {
 #pragma unroll
-    for (int m = 0; m < 6; ++m)
-        nb[m] = cell_index(g, wrap(i + face_off(m, 0), g.nx), wrap(j + face_off(m, 1), g.ny),
-                           wrap(k + face_off(m, 2), g.nz));
-    const float ih[3] = {(float)(1.0 / g.h[0]), (float)(1.0 / g.h[1]), (float)(1.0 / g.h[2])};
+        for (int m = 0; m < 6; ++m)
+            nb[m] = cell_index(g, wrap(i + face_off(m, 0), g.nx), wrap(j + face_off(m, 1), g.ny),
+                               wrap(k + face_off(m, 2), g.nz));
+    } else {
+        const int c0[3] = {i, j, k};
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            int cc[3];
+            fl[m] = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cc[a] = nb_coord(g, a, c0[a] + face_off(m, a), fl[m]);
+            nb[m] = cell_index(g, cc[0], cc[1], cc[2]);
+        }
+        double h[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            h[a] = cell_h(g, a, c0[a]);
+            ih[a] = (float)(1.0 / h[a]);
+        }
+        const double hv = cbrt(h[0] * h[1] * h[2]);
+        eps2 = (float)(hv * hv * hv);
+    }
 #pragma unroll 1
     for (int v = 0; v < 5; ++v) {
         const double *Qv = Q + (long long)v * n;
         const double q0 = __ldg(Qv + c);
         float dn[6];  // neighbour minus own average, FP64 difference
 #pragma unroll
-        for (int m = 0; m < 6; ++m) dn[m] = (float)(__ldg(Qv + nb[m]) - q0);
+        for (int m = 0; m < 6; ++m) {
+            double x = __ldg(Qv + nb[m]);
+            if constexpr (GEN) x = neg_if(x, ghost_neg(g, v, fl[m]));
+            dn[m] = (float)(x - q0);
+        }
         float b[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) b[d] = 0.5f * (dn[2 * d + 1] - dn[2 * d]);
@@ -608,7 +651,13 @@ int launch_recon5_mixed(const GridDesc &g, const Slab &S, const PhysParams &P, c
                         int indicator, unsigned long long *skips) {
     if (!Gf || !Qhi || !Qlo) return -1;
     const long long tiles = 5 * ((S.nb + 127) / 128);
-    if (indicator)
+    if (g.general) {
+        // general grids: the plain reconstruction only (no indicator)
+        if (indicator) return -1;
+        recon5_mixed_kernel<kModePlain, true, true>
+            <<<persistent_blocks(recon5_mixed_kernel<kModePlain, true, true>, tiles), 128, 0, s>>>(
+                g, S, P.nonlinear, nullptr, nullptr, Gf, Qhi, Qlo, fs, nullptr, nullptr, nullptr);
+    } else if (indicator)
         recon5_mixed_kernel<kModeIndicator, true>
             <<<persistent_blocks(recon5_mixed_kernel<kModeIndicator, true>, tiles), 128, 0, s>>>(
                 g, S, P.nonlinear, nullptr, nullptr, Gf, Qhi, Qlo, fs, nullptr, nullptr, skips);
@@ -622,6 +671,7 @@ int launch_recon5_mixed(const GridDesc &g, const Slab &S, const PhysParams &P, c
 int launch_indicator_dump(const GridDesc &g, const double *Q, const double *G, const float *Gf,
                           const float *Qhi, const float *Qlo, float *x, float *chi,
                           cudaStream_t s) {
+    if (g.general) return -1;  // training dumps come from periodic uniform grids
     const long long tiles = 5 * ((g.n + 127) / 128);
     const Slab S = whole_grid(g);
     if (Gf && Qhi && Qlo) {
@@ -683,7 +733,10 @@ int launch_recon2_mixed(const GridDesc &g, const Slab &S, const PhysParams &P, c
     const float eps2 = (float)(hv * hv * hv);
     const int block = 128;
     const long long grid = (S.nb + block - 1) / block;
-    recon2_mixed_kernel<<<(unsigned)grid, block, 0, s>>>(g, S, P.nonlinear, eps2, Q, fs);
+    if (g.general)
+        recon2_mixed_kernel<true><<<(unsigned)grid, block, 0, s>>>(g, S, P.nonlinear, eps2, Q, fs);
+    else
+        recon2_mixed_kernel<false><<<(unsigned)grid, block, 0, s>>>(g, S, P.nonlinear, eps2, Q, fs);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -18,29 +18,48 @@ __constant__ double cBs[kNumData][kMaxClass];  // weighted derivative rows, same
 __constant__ double cMean[kNumBasis];
 __constant__ double cMval[3][kNumBasis];
 __constant__ double cMder[3][3][kNumBasis];
-// Value of data column K for one (cell, variable) (layout in basis.h)
-template <int K>
+// Value of data column K for one (cell, variable) (layout in basis.h); on a
+// general grid (GEN) the neighbours' gradients are scaled by their own cell
+// sizes and a mirror ghost's averages and derivatives carry their signs
+template <int K, bool GEN>
 __device__ __forceinline__ double data_col(const double *__restrict__ Qv,
                                            const double *__restrict__ Gv, long long n, long long c,
                                            const long long nbF[6], const long long nbE[12],
-                                           double q0, const double h[3]) {
+                                           double q0, const double h[3], const NbGeo &geo) {
     if constexpr (K < kColEdge) {
-        return __ldg(Qv + nbF[K]) - q0;
+        const double x = __ldg(Qv + nbF[K]);
+        if constexpr (GEN) return neg_if(x, (geo.fF[K] >> 3) & 1) - q0;
+        else return x - q0;
     } else if constexpr (K < kColFaceGrad) {
-        return __ldg(Qv + nbE[K - kColEdge]) - q0;
+        const double x = __ldg(Qv + nbE[K - kColEdge]);
+        if constexpr (GEN) return neg_if(x, (geo.fE[K - kColEdge] >> 3) & 1) - q0;
+        else return x - q0;
     } else if constexpr (K < kColEdgeGrad) {
         constexpr int m = (K - kColFaceGrad) / 3, j = (K - kColFaceGrad) % 3;
-        return h[j] * __ldg(Gv + j * n + nbF[m]);
+        if constexpr (GEN)
+            return geo.hm[j][face_off(m, j) + 1] *
+                   neg_if(__ldg(Gv + j * n + nbF[m]), der_neg(geo.fF[m], j));
+        else return h[j] * __ldg(Gv + j * n + nbF[m]);
     } else if constexpr (K < kColCentreGrad) {
         constexpr int e = (K - kColEdgeGrad) / 2;
         constexpr int ea = edge_axis_a(e), eb = edge_axis_b(e), ee = edge_axis_e(e);
         if constexpr ((K - kColEdgeGrad) % 2 == 0) {
             constexpr double oa = edge_off(e, ea), ob = edge_off(e, eb);
-            const double da = h[ea] * __ldg(Gv + ea * n + nbE[e]);
-            const double db = h[eb] * __ldg(Gv + eb * n + nbE[e]);
+            double da, db;
+            if constexpr (GEN) {
+                da = geo.hm[ea][edge_off(e, ea) + 1] *
+                     neg_if(__ldg(Gv + ea * n + nbE[e]), der_neg(geo.fE[e], ea));
+                db = geo.hm[eb][edge_off(e, eb) + 1] *
+                     neg_if(__ldg(Gv + eb * n + nbE[e]), der_neg(geo.fE[e], eb));
+            } else {
+                da = h[ea] * __ldg(Gv + ea * n + nbE[e]);
+                db = h[eb] * __ldg(Gv + eb * n + nbE[e]);
+            }
             return (oa * da - ob * db) * kRs2;
         } else {
-            return h[ee] * __ldg(Gv + ee * n + nbE[e]);
+            if constexpr (GEN)
+                return geo.hm[ee][1] * neg_if(__ldg(Gv + ee * n + nbE[e]), der_neg(geo.fE[e], ee));
+            else return h[ee] * __ldg(Gv + ee * n + nbE[e]);
         }
     } else {
         constexpr int j = K - kColCentreGrad;
@@ -104,6 +123,7 @@ __device__ __forceinline__ void eval_faces(double *__restrict__ fs, long long n,
 }
 
 // cell c (global), variable v; face states to buffer position l (stride nb)
+template <bool GEN>
 __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
                                             const double *__restrict__ Q,
                                             const double *__restrict__ G,
@@ -114,15 +134,14 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
     const int j = (int)((c / g.nx) % g.ny);
     const int k = (int)(c / ((long long)g.nx * g.ny));
     long long nbF[6], nbE[12];
-#pragma unroll
-    for (int m = 0; m < 6; ++m)
-        nbF[m] = cell_index(g, wrap(i + face_off(m, 0), g.nx), wrap(j + face_off(m, 1), g.ny),
-                            wrap(k + face_off(m, 2), g.nz));
-#pragma unroll
-    for (int e = 0; e < 12; ++e)
-        nbE[e] = cell_index(g, wrap(i + edge_off(e, 0), g.nx), wrap(j + edge_off(e, 1), g.ny),
-                            wrap(k + edge_off(e, 2), g.nz));
-    const double h[3] = {g.h[0], g.h[1], g.h[2]};
+    NbGeo geo;
+    stencil<GEN>(g, i, j, k, v, nbF, nbE, geo);
+    double h[3] = {g.h[0], g.h[1], g.h[2]};
+    if constexpr (GEN) {
+        h[0] = geo.hm[0][1];
+        h[1] = geo.hm[1][1];
+        h[2] = geo.hm[2][1];
+    }
     const double ih[3] = {1.0 / h[0], 1.0 / h[1], 1.0 / h[2]};
 
     const double *Qv = Q + (long long)v * n;
@@ -143,7 +162,7 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
             static_for<nm>([&](auto Qq) {
                 constexpr int q = decltype(Qq)::value;
                 constexpr int col = kSym.mem[r][q];
-                ov[q] = data_col<col>(Qv, Gv, n, c, nbF, nbE, q0, h);
+                ov[q] = data_col<col, GEN>(Qv, Gv, n, c, nbF, nbE, q0, h, geo);
                 constexpr double wc = col_weight(col);
                 norm2 = fma(wc * wc * ov[q], ov[q], norm2);
                 if constexpr (col < kColEdge) dface[col] = ov[q];
@@ -209,7 +228,7 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
                     static_for<nm>([&](auto Qq) {
                         constexpr int q = decltype(Qq)::value;
                         constexpr int col = kSym.mem[r][q];
-                        ov[q] = data_col<col>(Qv, Gv, n, c, nbF, nbE, q0, h);
+                        ov[q] = data_col<col, GEN>(Qv, Gv, n, c, nbF, nbE, q0, h, geo);
                     });
                 }
                 double ds = kSym.sgn[r][0] > 0 ? ov[0] : -ov[0];
@@ -241,15 +260,17 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
     eval_faces<2>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
 }
 
+template <bool GEN>
 __global__ void __launch_bounds__(128) recon5_kernel(GridDesc g, Slab S, int nonlinear,
                                                      const double *__restrict__ Q,
                                                      const double *__restrict__ G,
                                                      double *__restrict__ fs) {
     const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l < S.nb)
-        recon5_cell(g, nonlinear, Q, G, fs, slab_global(g, S, l), (int)blockIdx.y, S.nb, l);
+        recon5_cell<GEN>(g, nonlinear, Q, G, fs, slab_global(g, S, l), (int)blockIdx.y, S.nb, l);
 }
 
+template <bool GEN>
 __global__ void __launch_bounds__(128) recon2_kernel(GridDesc g, Slab S, int nonlinear,
                                                      double eps2, const double *__restrict__ Q,
                                                      double *__restrict__ fs) {
@@ -261,19 +282,43 @@ __global__ void __launch_bounds__(128) recon2_kernel(GridDesc g, Slab S, int non
     const int j = (int)((c / g.nx) % g.ny);
     const int k = (int)(c / ((long long)g.nx * g.ny));
     long long nb[6];
+    int fl[6];
+    double h[3] = {g.h[0], g.h[1], g.h[2]};
+    if constexpr (!GEN) {
 #pragma unroll
-    for (int m = 0; m < 6; ++m)
-        nb[m] = cell_index(g, wrap(i + face_off(m, 0), g.nx), wrap(j + face_off(m, 1), g.ny),
-                           wrap(k + face_off(m, 2), g.nz));
+        for (int m = 0; m < 6; ++m)
+            nb[m] = cell_index(g, wrap(i + face_off(m, 0), g.nx), wrap(j + face_off(m, 1), g.ny),
+                               wrap(k + face_off(m, 2), g.nz));
+    } else {
+        // mirror ghosts across non-periodic axes; this cell's sizes and the
+        // limiter's eps^2 = h^3 from its own volume (reading R9)
+        const int c0[3] = {i, j, k};
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            int cc[3];
+            fl[m] = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cc[a] = nb_coord(g, a, c0[a] + face_off(m, a), fl[m]);
+            nb[m] = cell_index(g, cc[0], cc[1], cc[2]);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) h[a] = cell_h(g, a, c0[a]);
+        const double hv = cbrt(h[0] * h[1] * h[2]);
+        eps2 = hv * hv * hv;
+    }
 #pragma unroll 1
     for (int v = 0; v < 5; ++v) {
         const double *Qv = Q + (long long)v * n;
         const double q0 = __ldg(Qv + c);
         double qn[6];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) qn[m] = __ldg(Qv + nb[m]);
+        for (int m = 0; m < 6; ++m) {
+            qn[m] = __ldg(Qv + nb[m]);
+            if constexpr (GEN) qn[m] = neg_if(qn[m], ghost_neg(g, v, fl[m]));
+        }
         // least-squares gradient of the face-neighbour averages on a uniform
-        // grid: the central difference (normalised units)
+        // grid: the central difference (normalised units; on a stretched
+        // mesh those of the reference cell)
         double b[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) b[d] = 0.5 * (qn[2 * d + 1] - qn[2 * d]);
@@ -305,7 +350,7 @@ __global__ void __launch_bounds__(128) recon2_kernel(GridDesc g, Slab S, int non
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const int jf = (q - d + 3) % 3;
-                o[(long long)(5 + 5 * jf + cmp) * S.nb] = phi * b[q] / g.h[q];
+                o[(long long)(5 + 5 * jf + cmp) * S.nb] = phi * b[q] / h[q];
             }
         }
     }
@@ -324,7 +369,7 @@ __global__ void __launch_bounds__(128) recon5_ens_fp64_kernel(const EnsInst *__r
         const double *G = Ga + 15 * I.off;
         const long long T = it.c1 - it.c0;
         for (long long t = threadIdx.x; t < 5 * T; t += blockDim.x)
-            recon5_cell(I.g, I.P.nonlinear, Q, G, fsa + 480 * I.off, it.c0 + t % T, (int)(t / T),
+            recon5_cell<false>(I.g, I.P.nonlinear, Q, G, fsa + 480 * I.off, it.c0 + t % T, (int)(t / T),
                         I.g.n, it.c0 + t % T);
     }
 }
@@ -351,7 +396,10 @@ int launch_recon5(const GridDesc &g, const Slab &S, const PhysParams &P, const d
                   const double *G, double *fs, cudaStream_t s) {
     const int block = 128;
     const long long grid = (S.nb + block - 1) / block;
-    recon5_kernel<<<dim3((unsigned)grid, 5), block, 0, s>>>(g, S, P.nonlinear, Q, G, fs);
+    if (g.general)
+        recon5_kernel<true><<<dim3((unsigned)grid, 5), block, 0, s>>>(g, S, P.nonlinear, Q, G, fs);
+    else
+        recon5_kernel<false><<<dim3((unsigned)grid, 5), block, 0, s>>>(g, S, P.nonlinear, Q, G, fs);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -361,7 +409,10 @@ int launch_recon2(const GridDesc &g, const Slab &S, const PhysParams &P, const d
     const double eps2 = hv * hv * hv;  // (K h)^3 with K = 1
     const int block = 128;
     const long long grid = (S.nb + block - 1) / block;
-    recon2_kernel<<<(unsigned)grid, block, 0, s>>>(g, S, P.nonlinear, eps2, Q, fs);
+    if (g.general)
+        recon2_kernel<true><<<(unsigned)grid, block, 0, s>>>(g, S, P.nonlinear, eps2, Q, fs);
+    else
+        recon2_kernel<false><<<(unsigned)grid, block, 0, s>>>(g, S, P.nonlinear, eps2, Q, fs);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

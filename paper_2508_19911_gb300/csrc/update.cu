@@ -42,9 +42,16 @@ __device__ __forceinline__ void cell_rates(const GridDesc &g, const PhysParams &
     const double U = Q[n + c] * ir, V = Q[2 * n + c] * ir, W = Q[3 * n + c] * ir;
     const double p = (P.gamma - 1.0) * (Q[4 * n + c] - 0.5 * rho * (U * U + V * V + W * W));
     const double cs = sqrt(P.gamma * p * ir);
-    rate = fmax(rate, (fabs(U) + cs) / g.h[0]);
-    rate = fmax(rate, (fabs(V) + cs) / g.h[1]);
-    rate = fmax(rate, (fabs(W) + cs) / g.h[2]);
+    double h[3] = {g.h[0], g.h[1], g.h[2]};
+    if (g.general) {
+        const long long nxy = (long long)g.nx * g.ny;
+        h[0] = cell_h(g, 0, (int)(c % g.nx));
+        h[1] = cell_h(g, 1, (int)((c % nxy) / g.nx));
+        h[2] = cell_h(g, 2, (int)(c / nxy));
+    }
+    rate = fmax(rate, (fabs(U) + cs) / h[0]);
+    rate = fmax(rate, (fabs(V) + cs) / h[1]);
+    rate = fmax(rate, (fabs(W) + cs) / h[2]);
     numax = fmax(numax, viscosity(P, rho, p) * ir);
 }
 
@@ -74,7 +81,7 @@ __device__ __forceinline__ double dt_from_rates(const GridDesc &g, const PhysPar
                                                 double rate, double numax) {
     double dt = P.cfl / rate;
     if (!P.inviscid && numax > 0.0) {
-        const double hmin = fmin(g.h[0], fmin(g.h[1], g.h[2]));
+        const double hmin = g.general ? g.hmin : fmin(g.h[0], fmin(g.h[1], g.h[2]));
         dt = fmin(dt, P.cfl * hmin * hmin / (3.0 * numax));
     }
     return dt;
@@ -120,12 +127,28 @@ __device__ __forceinline__ void update_cell(const GridDesc &g, const PhysParams 
     const int i = (int)(c % g.nx);
     const int j = (int)((c / g.nx) % g.ny);
     const int k = (int)(c / ((long long)g.nx * g.ny));
-    const long long hi[3] = {cell_index(g, wrap(i + 1, g.nx), j, k),
-                             cell_index(g, i, wrap(j + 1, g.ny), k),
-                             cell_index(g, i, j, wrap(k + 1, g.nz))};
+    long long hi[3] = {cell_index(g, wrap(i + 1, g.nx), j, k),
+                       cell_index(g, i, wrap(j + 1, g.ny), k),
+                       cell_index(g, i, j, wrap(k + 1, g.nz))};
+    // records of the faces on the high side: strides n (the next cell's low
+    // face) or np (a high boundary face of a non-periodic axis)
+    const double *Fh[3] = {fr, fr + 30 * n, fr + 60 * n};
+    long long hs[3] = {n, n, n};
     const double dt2 = dt * dt;
     // 1/h once per thread (FP64 division is a multi-instruction sequence)
-    const double ih[3] = {1.0 / g.h[0], 1.0 / g.h[1], 1.0 / g.h[2]};
+    double ih[3] = {1.0 / g.h[0], 1.0 / g.h[1], 1.0 / g.h[2]};
+    if (g.general) {
+        const int cc[3] = {i, j, k};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ih[d] = 1.0 / cell_h(g, d, cc[d]);
+            if (g.bc[d] && cc[d] == axis_len(g, d) - 1) {
+                Fh[d] = fr + 90 * n + (long long)d * 30 * g.np;
+                hs[d] = g.np;
+                hi[d] = plane_pos(g, d, i, j, k);
+            }
+        }
+    }
     constexpr double kSixth = 1.0 / 6.0, kThird = 1.0 / 3.0;
     double out[5];
 #pragma unroll
@@ -134,8 +157,8 @@ __device__ __forceinline__ void update_cell(const GridDesc &g, const PhysParams 
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double *F = fr + (long long)d * 30 * n;
-            L += (F[(long long)v * n + hi[d]] - F[(long long)v * n + c]) * ih[d];
-            Lt += (F[(long long)(5 + v) * n + hi[d]] - F[(long long)(5 + v) * n + c]) * ih[d];
+            L += (Fh[d][(long long)v * hs[d] + hi[d]] - F[(long long)v * n + c]) * ih[d];
+            Lt += (Fh[d][(long long)(5 + v) * hs[d] + hi[d]] - F[(long long)(5 + v) * n + c]) * ih[d];
         }
         L = -L;
         Lt = -Lt;
@@ -151,8 +174,8 @@ __device__ __forceinline__ void update_cell(const GridDesc &g, const PhysParams 
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const double *F = fr + (long long)d * 30 * n;
-                const double ql = F[(long long)(10 + v) * n + hi[d]];
-                const double qlt = F[(long long)(15 + v) * n + hi[d]];
+                const double ql = Fh[d][(long long)(10 + v) * hs[d] + hi[d]];
+                const double qlt = Fh[d][(long long)(15 + v) * hs[d] + hi[d]];
                 const double qr = F[(long long)(20 + v) * n + c];
                 const double qrt = F[(long long)(25 + v) * n + c];
                 const long long gi = ((long long)v * 3 + d) * n + c;
@@ -165,7 +188,7 @@ __device__ __forceinline__ void update_cell(const GridDesc &g, const PhysParams 
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const double *F = fr + (long long)d * 30 * n;
-                const double qlt = F[(long long)(15 + v) * n + hi[d]];
+                const double qlt = Fh[d][(long long)(15 + v) * hs[d] + hi[d]];
                 const double qrt = F[(long long)(25 + v) * n + c];
                 const long long gi = ((long long)v * 3 + d) * n + c;
                 G[gi] = S1[gi] + dt * (qlt - qrt) * ih[d];
@@ -255,6 +278,10 @@ __global__ void __launch_bounds__(kBlock) update_ens_kernel(const EnsInst *__res
 // 11 max speed; 3, 4 are minima, 11 a maximum, the rest sums
 constexpr int kDiag = kDiagSlots;
 
+__device__ __forceinline__ double neg_val(const GridDesc &g, int v, int flip, double x) {
+    return ghost_neg(g, v, flip) ? -x : x;
+}
+
 __device__ __forceinline__ double combine(int s, double a, double b) {
     if (s == 3 || s == 4) return fmin(a, b);
     if (s == 11) return fmax(a, b);
@@ -298,12 +325,16 @@ __global__ void __launch_bounds__(kBlock) diag_partial_kernel(GridDesc g, PhysPa
                                                               const double *__restrict__ G,
                                                               double *partials) {
     const long long n = g.n;
-    const double vol = g.h[0] * g.h[1] * g.h[2];
+    const double vol_u = g.h[0] * g.h[1] * g.h[2];
     double acc[kDiag];
 #pragma unroll
     for (int s = 0; s < kDiag; ++s) acc[s] = identity_of(s);
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(c % g.nx);
+        const int j = (int)((c / g.nx) % g.ny);
+        const int k = (int)(c / ((long long)g.nx * g.ny));
+        const double vol = g.general ? cell_h(g, 0, i) * cell_h(g, 1, j) * cell_h(g, 2, k) : vol_u;
         double W[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
@@ -327,9 +358,6 @@ __global__ void __launch_bounds__(kBlock) diag_partial_kernel(GridDesc g, PhysPa
 #pragma unroll
         for (int d = 0; d < 3; ++d) acc[11] = fmax(acc[11], fabs(vel[d]) + cs);
         acc[0] += 0.5 * rho * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]) * vol;
-        const int i = (int)(c % g.nx);
-        const int j = (int)((c / g.nx) % g.ny);
-        const int k = (int)(c / ((long long)g.nx * g.ny));
         double dQ[4][3];  // d(rho), d(rho U), d(rho V), d(rho W)
 #pragma unroll
         for (int v = 0; v < 4; ++v)
@@ -337,6 +365,21 @@ __global__ void __launch_bounds__(kBlock) diag_partial_kernel(GridDesc g, PhysPa
             for (int d = 0; d < 3; ++d) {
                 if (G) {
                     dQ[v][d] = G[((long long)v * 3 + d) * n + c];
+                } else if (g.general) {
+                    // the two neighbours (mirror ghosts at a boundary), their
+                    // centres h_c + (h_hi + h_lo)/2 apart
+                    const int cc[3] = {i, j, k};
+                    int fh = 0, fl = 0, ch[3], cl[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        ch[a] = a == d ? nb_coord(g, a, cc[a] + 1, fh) : cc[a];
+                        cl[a] = a == d ? nb_coord(g, a, cc[a] - 1, fl) : cc[a];
+                    }
+                    const double qh = neg_val(g, v, fh, Q[(long long)v * n + cell_index(g, ch[0], ch[1], ch[2])]);
+                    const double ql = neg_val(g, v, fl, Q[(long long)v * n + cell_index(g, cl[0], cl[1], cl[2])]);
+                    const double dist = cell_h(g, d, cc[d]) +
+                                        0.5 * (cell_h(g, d, ch[d]) + cell_h(g, d, cl[d]));
+                    dQ[v][d] = (qh - ql) / dist;
                 } else {
                     const long long hi = cell_index(g, d == 0 ? wrap(i + 1, g.nx) : i,
                                                     d == 1 ? wrap(j + 1, g.ny) : j,
@@ -435,7 +478,7 @@ int diagnostics_blocks(const GridDesc &g) {
 int launch_diagnostics(const GridDesc &g, const PhysParams &P, const double *Q, const double *G,
                        double *partials, int nblocks, double *out_dev, cudaStream_t s) {
     diag_partial_kernel<<<nblocks, kBlock, 0, s>>>(g, P, Q, G, partials);
-    const double volume = g.h[0] * g.h[1] * g.h[2] * (double)g.n;
+    const double volume = g.general ? g.volume : g.h[0] * g.h[1] * g.h[2] * (double)g.n;
     diag_final_kernel<<<1, kBlock, 0, s>>>(partials, nblocks, volume, out_dev);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }

@@ -44,7 +44,12 @@ class Options(ctypes.Structure):
         ("C_tau", ctypes.c_double), ("eps_tau", ctypes.c_double),
         ("T_ref", ctypes.c_double), ("theta", ctypes.c_double),
         ("slab_planes", ctypes.c_int), ("reserved", ctypes.c_int),
+        ("bc", ctypes.c_int * 3), ("reserved2", ctypes.c_int),
+        ("h", ctypes.POINTER(ctypes.c_double) * 3),
     ]
+
+
+BC = {"periodic": 0, "symmetry": 1, "outflow": 2}
 
 
 _LIB = None
@@ -199,10 +204,14 @@ class Config:
     T_ref: float = 1.0
     theta: float = 0.9
     slab_planes: int = 0
+    # boundary per axis ("periodic", "symmetry", "outflow") and, for a
+    # stretched mesh, the cell sizes of each axis (None: uniform L/n)
+    bc: tuple = ("periodic", "periodic", "periodic")
+    spacing: tuple = (None, None, None)
 
 
 class Solver:
-    """One gks_ctx: a periodic grid with its workspace on the current device."""
+    """One gks_ctx: a grid with its workspace on the current device."""
 
     def __init__(self, cfg: Config, stream=None):
         import torch
@@ -219,6 +228,16 @@ class Solver:
         opt.inviscid = int(bool(cfg.inviscid))
         opt.C_tau, opt.eps_tau, opt.T_ref, opt.theta = cfg.C_tau, cfg.eps_tau, cfg.T_ref, cfg.theta
         opt.slab_planes = int(cfg.slab_planes)
+        keep = []
+        for a in range(3):
+            b = cfg.bc[a]
+            opt.bc[a] = BC[b] if isinstance(b, str) else int(b)
+            if cfg.spacing[a] is not None:
+                h = np.ascontiguousarray(cfg.spacing[a], dtype=np.float64)
+                if h.shape != (int(cfg.n[a]),):
+                    raise ValueError(f"spacing[{a}] needs {cfg.n[a]} cell sizes")
+                keep.append(h)
+                opt.h[a] = h.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.device = self.stream.device
         ctx = _VP()
@@ -227,6 +246,7 @@ class Solver:
                               int(cfg.n[0]), int(cfg.n[1]), int(cfg.n[2]),
                               float(cfg.L[0]), float(cfg.L[1]), float(cfg.L[2]),
                               ctypes.byref(opt), _VP(self.stream.cuda_stream)), "gks_init")
+        del keep  # gks_init copied the cell sizes
         self.ctx = ctx
         self.ncells = int(cfg.n[0]) * int(cfg.n[1]) * int(cfg.n[2])
         self.K = 4 if cfg.scheme == "cgks5" else 1
@@ -269,9 +289,17 @@ class Solver:
                "gks_reconstruct")
         return out
 
+    def flux_bytes(self):
+        """Bytes of gks_flux's records (boundary faces included)."""
+        return int(lib().gks_face_flux_bytes(self.ctx))
+
     def flux(self, face_states, dt, out=None, Q=None):
+        """Face records; on a grid with a non-periodic or stretched axis the
+        returned buffer is flat: [3][30][cells] then the high-boundary
+        records [3][30][np]."""
         if out is None:
-            out = self.zeros(3, 30, self.ncells)
+            words = self.flux_bytes() // 8
+            out = self.zeros(words) if words != 90 * self.ncells else self.zeros(3, 30, self.ncells)
         _check(lib().gks_flux(self.ctx, _ptr(Q), _ptr(face_states, self.fs_dtype), _ptr(dt),
                               _ptr(out)), "gks_flux")
         return out
