@@ -114,6 +114,8 @@ __device__ __forceinline__ ff ff_add_like(ff a, ff b) {
     return fast_two_sum(s.hi, s.lo);
 }
 
+__device__ __forceinline__ ff ff_sub_like(ff a, ff b) { return ff_add_like(a, ff_neg(b)); }
+
 // sqrt(a), a > 0: FP32 root, one Newton correction with the exact residual
 __device__ __forceinline__ ff ff_sqrt(ff a) {
     const float h = __fsqrt_rn(a.hi);

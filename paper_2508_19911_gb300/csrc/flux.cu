@@ -97,20 +97,20 @@ __device__ __forceinline__ Sym5<T> mom_matrix(const T *u, const T *v, const T *w
     return M;
 }
 
-// acc += s * G a
+__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+
+// acc += G b, one fused multiply-add per matrix entry (the caller scales b:
+// the density-weighted slopes are formed once and shared by every matrix
+// they meet)
 template <typename T>
-__device__ __forceinline__ void sym_acc(const Sym5<T> &M, const T a[5], T s, T acc[5]) {
+__device__ __forceinline__ void sym_acc(const Sym5<T> &M, const T b[5], T acc[5]) {
     const T *g = M.g;
-    const T r0 = g[0] * a[0] + g[1] * a[1] + g[2] * a[2] + g[3] * a[3] + g[4] * a[4];
-    const T r1 = g[1] * a[0] + g[5] * a[1] + g[6] * a[2] + g[7] * a[3] + g[8] * a[4];
-    const T r2 = g[2] * a[0] + g[6] * a[1] + g[9] * a[2] + g[10] * a[3] + g[11] * a[4];
-    const T r3 = g[3] * a[0] + g[7] * a[1] + g[10] * a[2] + g[12] * a[3] + g[13] * a[4];
-    const T r4 = g[4] * a[0] + g[8] * a[1] + g[11] * a[2] + g[13] * a[3] + g[14] * a[4];
-    acc[0] += s * r0;
-    acc[1] += s * r1;
-    acc[2] += s * r2;
-    acc[3] += s * r3;
-    acc[4] += s * r4;
+    acc[0] = mad(g[4], b[4], mad(g[3], b[3], mad(g[2], b[2], mad(g[1], b[1], mad(g[0], b[0], acc[0])))));
+    acc[1] = mad(g[8], b[4], mad(g[7], b[3], mad(g[6], b[2], mad(g[5], b[1], mad(g[1], b[0], acc[1])))));
+    acc[2] = mad(g[11], b[4], mad(g[10], b[3], mad(g[9], b[2], mad(g[6], b[1], mad(g[2], b[0], acc[2])))));
+    acc[3] = mad(g[13], b[4], mad(g[12], b[3], mad(g[10], b[2], mad(g[7], b[1], mad(g[3], b[0], acc[3])))));
+    acc[4] = mad(g[14], b[4], mad(g[13], b[3], mad(g[11], b[2], mad(g[8], b[1], mad(g[4], b[0], acc[4])))));
 }
 
 // Slope of a Maxwellian (U, V, W, lam; il = 1/(2 lam)) with N internal
@@ -306,9 +306,9 @@ __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, 
     // A from the compatibility condition: <(A.psi) psi> = -<(a.u) psi>
     // (full line); the moment matrices of the weights u, v, w
     T Tv[5] = {0, 0, 0, 0, 0}, A[5];
-    sym_acc(mom_matrix<1, 0, 0>(uf, v, w, x2, x4), a[0], T(1), Tv);
-    sym_acc(mom_matrix<0, 1, 0>(uf, v, w, x2, x4), a[1], T(1), Tv);
-    sym_acc(mom_matrix<0, 0, 1>(uf, v, w, x2, x4), a[2], T(1), Tv);
+    sym_acc(mom_matrix<1, 0, 0>(uf, v, w, x2, x4), a[0], Tv);
+    sym_acc(mom_matrix<0, 1, 0>(uf, v, w, x2, x4), a[1], Tv);
+    sym_acc(mom_matrix<0, 0, 1>(uf, v, w, x2, x4), a[2], Tv);
     {
         T mT[5];
 #pragma unroll
@@ -318,6 +318,14 @@ __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, 
         }
         maxwell_slope(mT, S.U, S.V, S.W, S.lam, inv2l, N, c4, A);
     }
+    // every later contraction weighs the slopes with rho: scale them once
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        a[0][i] *= S.rho;
+        a[1][i] *= S.rho;
+        a[2][i] *= S.rho;
+        A[i] *= S.rho;
+    }
     // half line, weight 1: the slopes of the interface equilibrium (collected
     // from both sides), term 4 (g_s: rows 1 and 0 of its matrix are
     // <u psi>, <psi>) and term 6's conserved moments <(A.psi) psi>
@@ -325,8 +333,8 @@ __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, 
     {
         const Sym5<T> H = mom_matrix<0, 0, 0>(uh, v, w, x2, x4);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) sym_acc(H, a[j], S.rho, dW0[j]);
-        sym_acc(H, A, S.rho, Y6);
+        for (int j = 0; j < 3; ++j) sym_acc(H, a[j], dW0[j]);
+        sym_acc(H, A, Y6);
         const T r1[5] = {H.g[1], H.g[5], H.g[6], H.g[7], H.g[8]};
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
@@ -342,18 +350,18 @@ __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, 
     for (int i = 0; i < 5; ++i) X[i] = T(0);
     {
         const Sym5<T> H = mom_matrix<1, 0, 0>(uh, v, w, x2, x4);
-        sym_acc(H, A, S.rho, X);
-        sym_acc(H, a[0], S.rho, Y5);
+        sym_acc(H, A, X);
+        sym_acc(H, a[0], Y5);
     }
 #pragma unroll
     for (int i = 0; i < 5; ++i) X6[i] += X[i];
     q[2] += heat(X, Y6, U0, V0, W0);
     // term 5: (a.u) g_s = sum_j (a_j.psi) c_j g_s
-    sym_acc(mom_matrix<0, 1, 0>(uh, v, w, x2, x4), a[1], S.rho, Y5);
-    sym_acc(mom_matrix<0, 0, 1>(uh, v, w, x2, x4), a[2], S.rho, Y5);
-    sym_acc(mom_matrix<2, 0, 0>(uh, v, w, x2, x4), a[0], S.rho, X5);
-    sym_acc(mom_matrix<1, 1, 0>(uh, v, w, x2, x4), a[1], S.rho, X5);
-    sym_acc(mom_matrix<1, 0, 1>(uh, v, w, x2, x4), a[2], S.rho, X5);
+    sym_acc(mom_matrix<0, 1, 0>(uh, v, w, x2, x4), a[1], Y5);
+    sym_acc(mom_matrix<0, 0, 1>(uh, v, w, x2, x4), a[2], Y5);
+    sym_acc(mom_matrix<2, 0, 0>(uh, v, w, x2, x4), a[0], X5);
+    sym_acc(mom_matrix<1, 1, 0>(uh, v, w, x2, x4), a[1], X5);
+    sym_acc(mom_matrix<1, 0, 1>(uh, v, w, x2, x4), a[2], X5);
     q[1] += heat(X5, Y5, U0, V0, W0);
 #pragma unroll
     for (int i = 0; i < 5; ++i) X5acc[i] += X5[i];
@@ -381,14 +389,22 @@ __device__ __forceinline__ void equilibrium_terms(const PrimT<T> &Z, T N, T c4, 
     }
     T T0[5] = {0, 0, 0, 0, 0}, Ab[5];
     const Sym5<T> Fu = mom_matrix<1, 0, 0>(u, v, w, x2, x4);
-    sym_acc(Fu, ab[0], T(1), T0);
-    sym_acc(mom_matrix<0, 1, 0>(u, v, w, x2, x4), ab[1], T(1), T0);
-    sym_acc(mom_matrix<0, 0, 1>(u, v, w, x2, x4), ab[2], T(1), T0);
+    sym_acc(Fu, ab[0], T0);
+    sym_acc(mom_matrix<0, 1, 0>(u, v, w, x2, x4), ab[1], T0);
+    sym_acc(mom_matrix<0, 0, 1>(u, v, w, x2, x4), ab[2], T0);
     {
         T mT[5];
 #pragma unroll
         for (int i = 0; i < 5; ++i) mT[i] = -T0[i];
         maxwell_slope(mT, Z.U, Z.V, Z.W, Z.lam, inv2l, N, c4, Ab);
+    }
+    // rho0-weighted slopes for the flux moments of terms 2 and 3
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        ab[0][i] *= Z.rho;
+        ab[1][i] *= Z.rho;
+        ab[2][i] *= Z.rho;
+        Ab[i] *= Z.rho;
     }
     T Y[5];
     if (kTerm1) {
@@ -400,14 +416,14 @@ __device__ __forceinline__ void equilibrium_terms(const PrimT<T> &Z, T N, T c4, 
         q[0] = heat(X[0], Y, Z.U, Z.V, Z.W);
     }
     // term 2: (abar.u) g0; its conserved moments are rho0 T0
-    sym_acc(mom_matrix<2, 0, 0>(u, v, w, x2, x4), ab[0], Z.rho, X[1]);
-    sym_acc(mom_matrix<1, 1, 0>(u, v, w, x2, x4), ab[1], Z.rho, X[1]);
-    sym_acc(mom_matrix<1, 0, 1>(u, v, w, x2, x4), ab[2], Z.rho, X[1]);
+    sym_acc(mom_matrix<2, 0, 0>(u, v, w, x2, x4), ab[0], X[1]);
+    sym_acc(mom_matrix<1, 1, 0>(u, v, w, x2, x4), ab[1], X[1]);
+    sym_acc(mom_matrix<1, 0, 1>(u, v, w, x2, x4), ab[2], X[1]);
 #pragma unroll
     for (int i = 0; i < 5; ++i) Y[i] = Z.rho * T0[i];
     q[1] = heat(X[1], Y, Z.U, Z.V, Z.W);
     // term 3: Abar g0; its conserved moments are -rho0 T0 (compatibility)
-    sym_acc(Fu, Ab, Z.rho, X[2]);
+    sym_acc(Fu, Ab, X[2]);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         Y[i] = -Z.rho * T0[i];
@@ -536,10 +552,15 @@ __device__ void flux_point(const PhysParams &P, const double *sl, const double *
 //   F^n  = X1 - al4 D + sum_{k=2,3,5,6} al_k X_k,
 //   F_t^n =    - be4 D + sum_{k=2,3,5,6} be_k X_k,
 // and D is small where the flow is smooth. These three are computed in
-// float-float arithmetic (ff.cuh) from W = Q0 + offset; the half-line
-// starting values (erfc, exp) and the time integrals stay FP64, their
-// products with moments FP32; the slopes and moments of terms 2, 3, 5, 6
-// are the FP32 core shared with the FP32 part of the previous design.
+// float-float arithmetic (ff.cuh) from W = Q0 + offset, with the half-line
+// starting values erfc and exp from a float-float series (FP64 beyond its
+// range); the slopes and moments of terms 2, 3, 5, 6 are the FP32 core
+// shared with the FP64 kernel's templates. The float-float sums are the
+// like-term form (error 2^-46 of the operands' magnitudes, not of the
+// result): what matters here is the error against each quantity's own
+// scale (rho, rho E, their fluxes), never relative to a small result of
+// a cancellation, except 1 - erf (a half-space weight), which keeps the
+// full float-float subtraction.
 struct PrimFF {
     ff rho, U, V, W, p, lam, il;  // il = 1/(2 lam) = p/rho
 };
@@ -553,8 +574,8 @@ __device__ __forceinline__ PrimFF to_prim_ff(const ff s[5], ff gm1) {
     P.U = ff_mul(s[1], ir);
     P.V = ff_mul(s[2], ir);
     P.W = ff_mul(s[3], ir);
-    const ff q2 = ff_add(ff_add(ff_mul(P.U, P.U), ff_mul(P.V, P.V)), ff_mul(P.W, P.W));
-    P.p = ff_mul(gm1, ff_sub(s[4], ff_half(ff_mul(P.rho, q2))));
+    const ff q2 = ff_add_like(ff_add_like(ff_mul(P.U, P.U), ff_mul(P.V, P.V)), ff_mul(P.W, P.W));
+    P.p = ff_mul(gm1, ff_sub_like(s[4], ff_half(ff_mul(P.rho, q2))));
     P.il = ff_mul(P.p, ir);
     // lam only feeds the FP32 core (the half-line start uses il)
     P.lam = ff_make(__fdividef(0.5f * P.rho.hi, P.p.hi), 0.0f);
@@ -603,8 +624,8 @@ __device__ __forceinline__ void half_start_ff(const PrimFF &S, int sgn, ff &m0, 
 #pragma unroll 1
         for (int n = 1; n <= kSeriesTerms; ++n) {
             t = ff_mul(ff_mul(t, w), ff_of(cSeriesInv[n]));
-            se = ff_add(se, t);
-            sf = ff_add(sf, ff_mul(t, ff_of(cSeriesInvOdd[n])));
+            se = ff_add_like(se, t);
+            sf = ff_add_like(sf, ff_mul(t, ff_of(cSeriesInvOdd[n])));
             if (fabsf(t.hi) < 1e-16f) break;
         }
         constexpr ffc k2rpi = ff_const(1.1283791670955125739);   // 2/sqrt(pi)
@@ -612,7 +633,7 @@ __device__ __forceinline__ void half_start_ff(const PrimFF &S, int sgn, ff &m0, 
         const ff erf = ff_mul(ff_mul(y, ff_of(k2rpi)), sf);
         m0 = ff_half(sgn > 0 ? ff_add_f(erf, 1.0f) : ff_sub(ff_make(1.0f, 0.0f), erf));
         const ff edge = ff_half(ff_mul(ff_mul(se, ff_of(krpi)), isl));
-        m1 = sgn > 0 ? ff_add(ff_mul(S.U, m0), edge) : ff_sub(ff_mul(S.U, m0), edge);
+        m1 = sgn > 0 ? ff_add_like(ff_mul(S.U, m0), edge) : ff_sub_like(ff_mul(S.U, m0), edge);
     } else {
         double d0, d1;
         half_start(ff_to_double(S.U), 0.5 / ff_to_double(S.il), (double)sgn, d0, d1);
@@ -630,10 +651,10 @@ __device__ __forceinline__ void half_side_ff(const PrimFF &S, int sgn, ff N, ff 
     m0f = u[0].hi;
     m1f = u[1].hi;
     const ff inv2l = S.il;
-    u[2] = ff_add(ff_mul(S.U, u[1]), ff_mul(inv2l, u[0]));
-    u[3] = ff_add(ff_mul(S.U, u[2]), ff_mul(ff_add(inv2l, inv2l), u[1]));
+    u[2] = ff_add_like(ff_mul(S.U, u[1]), ff_mul(inv2l, u[0]));
+    u[3] = ff_add_like(ff_mul(S.U, u[2]), ff_mul(ff_add_like(inv2l, inv2l), u[1]));
     // <v^2> + <w^2> + <xi^2> of the full lines
-    const ff s2 = ff_add(ff_add(ff_mul(S.V, S.V), ff_mul(S.W, S.W)),
+    const ff s2 = ff_add_like(ff_add_like(ff_mul(S.V, S.V), ff_mul(S.W, S.W)),
                          ff_mul(ff_add_f(N, 2.0f), inv2l));
 #pragma unroll
     for (int A = 0; A < 2; ++A) {
@@ -642,10 +663,10 @@ __device__ __forceinline__ void half_side_ff(const PrimFF &S, int sgn, ff N, ff 
         o[1] = u[A + 1];
         o[2] = ff_mul(u[A], S.V);
         o[3] = ff_mul(u[A], S.W);
-        o[4] = ff_half(ff_add(u[A + 2], ff_mul(u[A], s2)));
+        o[4] = ff_half(ff_add_like(u[A + 2], ff_mul(u[A], s2)));
         ff *acc = A == 0 ? W0 : X4;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) acc[i] = ff_add(acc[i], ff_mul(S.rho, o[i]));
+        for (int i = 0; i < 5; ++i) acc[i] = ff_add_like(acc[i], ff_mul(S.rho, o[i]));
     }
 }
 
@@ -694,13 +715,13 @@ __device__ void flux_point_mixed(const PhysParams &P, const ff Ql[5], const floa
     // term 1: the Euler flux of W0; D = X1 - X4
     ff X1[5];
     X1[0] = W0[1];
-    X1[1] = ff_add(ff_mul(W0[1], Z.U), Z.p);
+    X1[1] = ff_add_like(ff_mul(W0[1], Z.U), Z.p);
     X1[2] = ff_mul(W0[2], Z.U);
     X1[3] = ff_mul(W0[3], Z.U);
-    X1[4] = ff_mul(ff_add(W0[4], Z.p), Z.U);
+    X1[4] = ff_mul(ff_add_like(W0[4], Z.p), Z.U);
     float D[5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) D[i] = ff_sub(X1[i], X4[i]).hi;
+    for (int i = 0; i < 5; ++i) D[i] = ff_sub_like(X1[i], X4[i]).hi;
 
     // FP32 core: slopes and the moments of terms 2, 3, 5, 6 (and the heat
     // fluxes for the Prandtl fix)
@@ -736,7 +757,7 @@ __device__ void flux_point_mixed(const PhysParams &P, const ff Ql[5], const floa
 
     // collision time (Sec. 4) in FP32; time coefficients in FP32 for
     // dt >= tau/2, else from the FP64 closed forms (dt >= tau/100) or series
-    const float dpr = fabsf(ff_sub(L.p, R.p).hi / ff_add(L.p, R.p).hi);
+    const float dpr = fabsf(ff_sub_like(L.p, R.p).hi / ff_add_like(L.p, R.p).hi);
     const float dtf = (float)dt;
     float tau;
     if (P.inviscid) {
@@ -789,9 +810,9 @@ __device__ void flux_point_mixed(const PhysParams &P, const ff Ql[5], const floa
         const float e = cd > 0.0f ? expf(-1.0f / cd) : 0.0f;
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            out[10 + i] = ff_add_f(W0[i], e * ff_sub(Wl[i], W0[i]).hi);
+            out[10 + i] = ff_add_f(W0[i], e * ff_sub_like(Wl[i], W0[i]).hi);
             out[15 + i] = ff_make((1.0f - e) * dtW0[i] + e * dtWl[i], 0.0f);
-            out[20 + i] = ff_add_f(W0[i], e * ff_sub(Wr[i], W0[i]).hi);
+            out[20 + i] = ff_add_f(W0[i], e * ff_sub_like(Wr[i], W0[i]).hi);
             out[25 + i] = ff_make((1.0f - e) * dtW0[i] + e * dtWr[i], 0.0f);
         }
     }
