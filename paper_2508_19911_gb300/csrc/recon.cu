@@ -162,12 +162,14 @@ __device__ __forceinline__ float data_col_f(const double *__restrict__ Qv,
     }
 }
 
+// the FP32 evaluation at the Gauss points, GENO's blend folded into the
+// class sums as in recon_fp64.cu (a scaled by chi, base = -chi K for the
+// offset from Q0, w = (1 - chi) bbar)
 template <int D>
 __device__ __forceinline__ void eval_faces_f(const float *T, float *__restrict__ fs,
                                              long long n, long long c, int v,
-                                             const float a[kNumBasis], float base, float chi,
-                                             const float bbar[3], bool nonlinear,
-                                             const float ih[3]) {
+                                             const float a[kNumBasis], float base,
+                                             const float w[3], bool blend, const float ih[3]) {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     float S[8], Dq[3][8];
 #pragma unroll
@@ -202,6 +204,17 @@ __device__ __forceinline__ void eval_faces_f(const float *T, float *__restrict__
             }
         });
     });
+    if (blend) {
+        S[1 << D] = fmaf(0.5f, w[D], S[1 << D]);
+        S[1 << T1] = fmaf((float)kG, w[T1], S[1 << T1]);
+        S[1 << T2] = fmaf((float)kG, w[T2], S[1 << T2]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Dq[q][0] += w[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) Dq[q][k] *= ih[q];
     class_to_points(S);
     class_to_points(Dq[0]);
     class_to_points(Dq[1]);
@@ -212,23 +225,12 @@ __device__ __forceinline__ void eval_faces_f(const float *T, float *__restrict__
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
             const int p = (side << D) | ((kk & 1) << T1) | (((kk >> 1) & 1) << T2);
-            float val = base + S[p], der[3] = {Dq[0][p], Dq[1][p], Dq[2][p]};
-            if (nonlinear) {
-                float x[3];
-                x[D] = side ? 0.5f : -0.5f;
-                x[T1] = (kk & 1) ? (float)kG : -(float)kG;
-                x[T2] = (kk & 2) ? (float)kG : -(float)kG;
-                const float p1 = fmaf(bbar[0], x[0], fmaf(bbar[1], x[1], bbar[2] * x[2]));
-                val = fmaf(chi, val - p1, p1);  // chi P4 + (1 - chi) P1
-#pragma unroll
-                for (int q = 0; q < 3; ++q) der[q] = fmaf(chi, der[q] - bbar[q], bbar[q]);
-            }
             float *o = fs + ((long long)((2 * D + side) * 4 + kk) * 20) * n + c;
-            o[(long long)cmp * n] = val;
+            o[(long long)cmp * n] = base + S[p];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const int jf = (q - D + 3) % 3;
-                o[(long long)(5 + 5 * jf + cmp) * n] = der[q] * ih[q];
+                o[(long long)(5 + 5 * jf + cmp) * n] = Dq[q][p];
             }
         }
 }
@@ -433,9 +435,20 @@ __device__ __forceinline__ void recon5_mixed_cell(const float *T,
             dump_chi[dump_base + 5 * c + v] = chi;
             return;
         }
-        eval_faces_f<0>(T, fs, nb, l, v, a, base, chi, bbar, geno, ih);
-        eval_faces_f<1>(T, fs, nb, l, v, a, base, chi, bbar, geno, ih);
-        eval_faces_f<2>(T, fs, nb, l, v, a, base, chi, bbar, geno, ih);
+        float w[3] = {0.0f, 0.0f, 0.0f};
+        float bse = base;
+        if (geno) {
+            // chi P4 + (1 - chi) P1 (Eq. weno-new), folded into the evaluation
+#pragma unroll
+            for (int ii = 0; ii < kNumBasis; ++ii) a[ii] *= chi;
+            bse = -chi * K;
+            const float omc = 1.0f - chi;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) w[q] = omc * bbar[q];
+        }
+        eval_faces_f<0>(T, fs, nb, l, v, a, bse, w, geno, ih);
+        eval_faces_f<1>(T, fs, nb, l, v, a, bse, w, geno, ih);
+        eval_faces_f<2>(T, fs, nb, l, v, a, bse, w, geno, ih);
     }
 }
 

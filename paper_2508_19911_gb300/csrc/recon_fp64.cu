@@ -67,11 +67,17 @@ __device__ __forceinline__ double data_col(const double *__restrict__ Qv,
     }
 }
 
+// P4 (and, blended, P1) at the 8 Gauss points of the two faces normal to
+// axis D. GENO's blend chi P4 + (1 - chi) P1 is applied to the class sums
+// before the transform: the caller scales a by chi (and base to
+// q0 - chi K); P1's slopes w = (1 - chi) bbar each sit in the class of one
+// odd axis (class sum w_j |x_j|, |x_D| = 1/2, |x_T| = g) and, for the
+// derivatives, in class 0. The derivatives are scaled by 1/h before the
+// transform too (it is linear).
 template <int D>
 __device__ __forceinline__ void eval_faces(double *__restrict__ fs, long long n, long long c,
                                            int v, const double a[kNumBasis], double base,
-                                           double chi, const double bbar[3], double q0,
-                                           bool nonlinear, const double ih[3]) {
+                                           const double w[3], bool blend, const double ih[3]) {
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     double S[8], Dq[3][8];
 #pragma unroll
@@ -91,6 +97,17 @@ __device__ __forceinline__ void eval_faces(double *__restrict__ fs, long long n,
             }
         });
     });
+    if (blend) {
+        S[1 << D] = fma(0.5, w[D], S[1 << D]);
+        S[1 << T1] = fma(kG, w[T1], S[1 << T1]);
+        S[1 << T2] = fma(kG, w[T2], S[1 << T2]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Dq[q][0] += w[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) Dq[q][k] *= ih[q];
     class_to_points(S);
     class_to_points(Dq[0]);
     class_to_points(Dq[1]);
@@ -101,23 +118,12 @@ __device__ __forceinline__ void eval_faces(double *__restrict__ fs, long long n,
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
             const int p = (side << D) | ((kk & 1) << T1) | (((kk >> 1) & 1) << T2);
-            double val = base + S[p], der[3] = {Dq[0][p], Dq[1][p], Dq[2][p]};
-            if (nonlinear) {
-                double x[3];
-                x[D] = side ? 0.5 : -0.5;
-                x[T1] = (kk & 1) ? kG : -kG;
-                x[T2] = (kk & 2) ? kG : -kG;
-                const double p1 = fma(bbar[0], x[0], fma(bbar[1], x[1], fma(bbar[2], x[2], q0)));
-                val = fma(chi, val - p1, p1);  // chi P4 + (1 - chi) P1
-#pragma unroll
-                for (int q = 0; q < 3; ++q) der[q] = fma(chi, der[q] - bbar[q], bbar[q]);
-            }
             double *o = fs + ((long long)((2 * D + side) * 4 + kk) * 20) * n + c;
-            o[(long long)cmp * n] = val;
+            o[(long long)cmp * n] = base + S[p];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const int jf = (q - D + 3) % 3;
-                o[(long long)(5 + 5 * jf + cmp) * n] = der[q] * ih[q];
+                o[(long long)(5 + 5 * jf + cmp) * n] = Dq[q][p];
             }
         }
 }
@@ -255,9 +261,20 @@ __device__ __forceinline__ void recon5_cell(const GridDesc &g, int nonlinear,
         const double s = sig * (1.0 / kGenoSigma0);
         chi = 1.0 / (1.0 + s + s * s);
     }
-    eval_faces<0>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
-    eval_faces<1>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
-    eval_faces<2>(fs, nb, l, v, a, base, chi, bbar, q0, nonlinear, ih);
+    double w[3] = {0.0, 0.0, 0.0};
+    double bse = base;
+    if (nonlinear) {
+        // chi P4 + (1 - chi) P1 (Eq. weno-new), folded into the evaluation
+#pragma unroll
+        for (int ii = 0; ii < kNumBasis; ++ii) a[ii] *= chi;
+        bse = fma(-chi, K, q0);
+        const double omc = 1.0 - chi;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) w[q] = omc * bbar[q];
+    }
+    eval_faces<0>(fs, nb, l, v, a, bse, w, nonlinear, ih);
+    eval_faces<1>(fs, nb, l, v, a, bse, w, nonlinear, ih);
+    eval_faces<2>(fs, nb, l, v, a, bse, w, nonlinear, ih);
 }
 
 template <bool GEN>
