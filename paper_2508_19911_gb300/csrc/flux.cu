@@ -73,32 +73,45 @@ struct Sym5 {
 };
 
 template <int A, int B, int D, typename T>
-__device__ __forceinline__ Sym5<T> mom_matrix(const T *u, const T *v, const T *w, T x2, T x4) {
-    auto m = [&](int a, int b, int d) { return u[A + a] * (v[B + b] * w[D + d]); };
-    Sym5<T> M;
-    const T m000 = m(0, 0, 0), m200 = m(2, 0, 0), m020 = m(0, 2, 0), m002 = m(0, 0, 2);
-    M.g[0] = m000;
-    M.g[1] = m(1, 0, 0);
-    M.g[2] = m(0, 1, 0);
-    M.g[3] = m(0, 0, 1);
-    M.g[4] = T(0.5) * (m200 + m020 + m002 + x2 * m000);
-    M.g[5] = m200;
-    M.g[6] = m(1, 1, 0);
-    M.g[7] = m(1, 0, 1);
-    M.g[8] = T(0.5) * (m(3, 0, 0) + m(1, 2, 0) + m(1, 0, 2) + x2 * M.g[1]);
-    M.g[9] = m020;
-    M.g[10] = m(0, 1, 1);
-    M.g[11] = T(0.5) * (m(2, 1, 0) + m(0, 3, 0) + m(0, 1, 2) + x2 * M.g[2]);
-    M.g[12] = m002;
-    M.g[13] = T(0.5) * (m(2, 0, 1) + m(0, 2, 1) + m(0, 0, 3) + x2 * M.g[3]);
-    M.g[14] = T(0.25) * (m(4, 0, 0) + m(0, 4, 0) + m(0, 0, 4) +
-                         T(2) * (m(2, 2, 0) + m(2, 0, 2) + m(0, 2, 2)) +
-                         T(2) * x2 * (m200 + m020 + m002) + x4 * m000);
-    return M;
-}
+__device__ __forceinline__ Sym5<T> mom_matrix(const T *u, const T *v, const T *w, T x2, T x4);
 
 __device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+
+// The entries with psi_4 = (u^2 + s)/2, s = v^2 + w^2 + xi^2, are
+// composed from pieces shared by every matrix of the same Maxwellian (the
+// compiler merges identical subexpressions): <v^b w^d s> = sig(b, d) and
+// <s^2>, and the half and quarter u-moments, so that
+//   <u^a v^b w^d psi_4> = (1/2) u_{a+2} vw_{bd} + (1/2) u_a sig_{bd},
+//   <psi_4^2>           = (1/4) u_4 vw + (1/2) u_2 sig + (1/4) u_0 <s^2>.
+template <int A, int B, int D, typename T>
+__device__ __forceinline__ Sym5<T> mom_matrix(const T *u, const T *v, const T *w, T x2, T x4) {
+    auto vw = [&](int b, int d) { return v[B + b] * w[D + d]; };
+    auto m = [&](int a, int b, int d) { return u[A + a] * vw(b, d); };
+    auto hu = [&](int a) { return T(0.5) * u[A + a]; };
+    auto qu = [&](int a) { return T(0.25) * u[A + a]; };
+    auto sig = [&](int b, int d) { return mad(x2, vw(b, d), vw(b + 2, d) + vw(b, d + 2)); };
+    auto E = [&](int a, int b, int d) { return mad(hu(a + 2), vw(b, d), hu(a) * sig(b, d)); };
+    Sym5<T> M;
+    M.g[0] = m(0, 0, 0);
+    M.g[1] = m(1, 0, 0);
+    M.g[2] = m(0, 1, 0);
+    M.g[3] = m(0, 0, 1);
+    M.g[4] = E(0, 0, 0);
+    M.g[5] = m(2, 0, 0);
+    M.g[6] = m(1, 1, 0);
+    M.g[7] = m(1, 0, 1);
+    M.g[8] = E(1, 0, 0);
+    M.g[9] = m(0, 2, 0);
+    M.g[10] = m(0, 1, 1);
+    M.g[11] = E(0, 1, 0);
+    M.g[12] = m(0, 0, 2);
+    M.g[13] = E(0, 0, 1);
+    const T s2 = mad(x4, vw(0, 0),
+                     mad(T(2) * x2, vw(2, 0) + vw(0, 2), vw(4, 0) + vw(0, 4) + T(2) * vw(2, 2)));
+    M.g[14] = mad(qu(4), vw(0, 0), mad(hu(2), sig(0, 0), qu(0) * s2));
+    return M;
+}
 
 // acc += G b, one fused multiply-add per matrix entry (the caller scales b:
 // the density-weighted slopes are formed once and shared by every matrix
@@ -119,15 +132,16 @@ __device__ __forceinline__ void sym_acc(const Sym5<T> &M, const T b[5], T acc[5]
 template <typename T>
 __device__ __forceinline__ void maxwell_slope(const T d[5], T U, T V, T W, T lam, T il, T N,
                                               T c4, T a[5]) {
-    const T q2 = U * U + V * V + W * W;
-    const T K = (N + T(3)) * il;
+    // the state's own factors (shared by every slope of the same state)
+    const T q2K = U * U + V * V + W * W + (N + T(3)) * il;
+    const T m2U = T(-2) * U, m2V = T(-2) * V, m2W = T(-2) * W;
     const T R1 = d[1] - U * d[0], R2 = d[2] - V * d[0], R3 = d[3] - W * d[0];
-    const T R4 = T(2) * d[4] - (q2 + K) * d[0];
-    a[4] = c4 * lam * lam * (R4 - T(2) * (U * R1 + V * R2 + W * R3));
+    const T R4 = T(2) * d[4] - q2K * d[0];
+    a[4] = c4 * lam * lam * mad(m2U, R1, mad(m2V, R2, mad(m2W, R3, R4)));
     a[1] = T(2) * lam * R1 - U * a[4];
     a[2] = T(2) * lam * R2 - V * a[4];
     a[3] = T(2) * lam * R3 - W * a[4];
-    a[0] = d[0] - U * a[1] - V * a[2] - W * a[3] - T(0.5) * a[4] * (q2 + K);
+    a[0] = d[0] - U * a[1] - V * a[2] - W * a[3] - (T(0.5) * q2K) * a[4];
 }
 
 // heat flux 1/2 <(u-U0)((u-U0)^2+(v-V0)^2+(w-W0)^2+xi^2)> of a term from its
