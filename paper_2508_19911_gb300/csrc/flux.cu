@@ -293,6 +293,36 @@ __device__ __forceinline__ Prim to_prim(const double *s, double gamma) {
     return P;
 }
 
+// sum_j <u_j (a_j.psi) psi> of a Maxwellian whose slopes a_j carry the
+// derivatives dW/dx_j (ds: d/dn, d/dt1, d/dt2 of the five conserved
+// variables): <u_j psi g> is the Euler flux F_j(W), so the sum is
+// (1/rho) sum_j dF_j/dW dW/dx_j, written with the flux Jacobians of the
+// face frame (velocity (U, V, W), total enthalpy H, gm1 = gamma - 1 =
+// 2/(N + 3)) instead of three contractions of full-line moment matrices.
+template <typename T>
+__device__ __forceinline__ void euler_rate(const T *ds, T ir, T U, T V, T W, T H, T gm1,
+                                           T out[5]) {
+    const T vel[3] = {U, V, W};
+    const T k2 = T(0.5) * (U * U + V * V + W * W);
+    T acc[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const T *d = ds + 5 * j;
+        const T c = vel[j];
+        const T dp = gm1 * mad(k2, d[0], d[4] - U * d[1] - V * d[2] - W * d[3]);
+        const T dmj = d[1 + j];
+        acc[0] += dmj;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            acc[1 + i] = mad(vel[i], dmj, mad(c, d[1 + i], mad(-(vel[i] * c), d[0], acc[1 + i])));
+            if (i == j) acc[1 + i] += dp;
+        }
+        acc[4] = mad(c, d[4] + dp, mad(H, mad(-c, d[0], dmj), acc[4]));
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) out[i] = acc[i] * ir;
+}
+
 // Contribution of one side (SGN = +1: left state over u > 0; -1: right
 // state over u < 0) to W0's slopes and to terms 4-6 of Eq. flux.
 // ds: the 15 derivatives d/dn, d/dt1, d/dt2 of the 5 conserved variables.
@@ -302,8 +332,7 @@ __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, 
                                            T X6[5], T q[3], T dtW[5]) {
     const T ir = T(1) / S.rho;
     const T inv2l = S.p * ir;  // 1/(2 lam)
-    T uf[kNU], uh[kNU], v[kNV], w[kNV];
-    full_line<kNU>(S.U, inv2l, uf);
+    T uh[kNU], v[kNV], w[kNV];
     half_line<kNU>(S.U, inv2l, uh0, uh1, uh);
     full_line<kNV>(S.V, inv2l, v);
     full_line<kNV>(S.W, inv2l, w);
@@ -318,11 +347,11 @@ __device__ __forceinline__ void side_terms(const T *ds, const PrimT<T> &S, T N, 
         maxwell_slope(d, S.U, S.V, S.W, S.lam, inv2l, N, c4, a[j]);
     }
     // A from the compatibility condition: <(A.psi) psi> = -<(a.u) psi>
-    // (full line); the moment matrices of the weights u, v, w
-    T Tv[5] = {0, 0, 0, 0, 0}, A[5];
-    sym_acc(mom_matrix<1, 0, 0>(uf, v, w, x2, x4), a[0], Tv);
-    sym_acc(mom_matrix<0, 1, 0>(uf, v, w, x2, x4), a[1], Tv);
-    sym_acc(mom_matrix<0, 0, 1>(uf, v, w, x2, x4), a[2], Tv);
+    // (full line): the Euler flux Jacobians applied to the derivatives
+    T Tv[5], A[5];
+    euler_rate(ds, ir, S.U, S.V, S.W, mad(T(0.5) * (N + T(5)), inv2l,
+                                          T(0.5) * (S.U * S.U + S.V * S.V + S.W * S.W)),
+               T(0.5) * c4, Tv);
     {
         T mT[5];
 #pragma unroll
@@ -401,11 +430,13 @@ __device__ __forceinline__ void equilibrium_terms(const PrimT<T> &Z, T N, T c4, 
         for (int i = 0; i < 5; ++i) d[i] = dW0[j][i] * ir;
         maxwell_slope(d, Z.U, Z.V, Z.W, Z.lam, inv2l, N, c4, ab[j]);
     }
-    T T0[5] = {0, 0, 0, 0, 0}, Ab[5];
+    // T0 = sum_j <u_j (abar_j.psi) psi>: the Euler flux Jacobians of W0
+    // applied to its collided slopes dW0 (see euler_rate)
+    T T0[5], Ab[5];
+    euler_rate(&dW0[0][0], ir, Z.U, Z.V, Z.W,
+               mad(T(0.5) * (N + T(5)), inv2l, T(0.5) * (Z.U * Z.U + Z.V * Z.V + Z.W * Z.W)),
+               T(0.5) * c4, T0);
     const Sym5<T> Fu = mom_matrix<1, 0, 0>(u, v, w, x2, x4);
-    sym_acc(Fu, ab[0], T0);
-    sym_acc(mom_matrix<0, 1, 0>(u, v, w, x2, x4), ab[1], T0);
-    sym_acc(mom_matrix<0, 0, 1>(u, v, w, x2, x4), ab[2], T0);
     {
         T mT[5];
 #pragma unroll
