@@ -299,6 +299,29 @@ __device__ __forceinline__ Prim to_prim(const double *s, double gamma) {
 // (1/rho) sum_j dF_j/dW dW/dx_j, written with the flux Jacobians of the
 // face frame (velocity (U, V, W), total enthalpy H, gm1 = gamma - 1 =
 // 2/(N + 3)) instead of three contractions of full-line moment matrices.
+// acc += dF_j/dW d: the Euler flux Jacobian along face-frame direction j
+// (velocity vel, k2 = |vel|^2/2, total enthalpy H, gm1 = gamma - 1)
+template <typename T>
+__device__ __forceinline__ void euler_jac_acc(const T *d, int j, const T vel[3], T k2, T H, T gm1,
+                                              T acc[5]) {
+    const T c = vel[j];
+    const T dp = gm1 * mad(k2, d[0], d[4] - vel[0] * d[1] - vel[1] * d[2] - vel[2] * d[3]);
+    const T dmj = d[1 + j];
+    acc[0] += dmj;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        acc[1 + i] = mad(vel[i], dmj, mad(c, d[1 + i], mad(-(vel[i] * c), d[0], acc[1 + i])));
+        if (i == j) acc[1 + i] += dp;
+    }
+    acc[4] = mad(c, d[4] + dp, mad(H, mad(-c, d[0], dmj), acc[4]));
+}
+
+// sum_j <u_j (a_j.psi) psi> of a Maxwellian whose slopes a_j carry the
+// derivatives dW/dx_j (ds: d/dn, d/dt1, d/dt2 of the five conserved
+// variables): <u_j psi g> is the Euler flux F_j(W), so the sum is
+// (1/rho) sum_j dF_j/dW dW/dx_j, written with the flux Jacobians of the
+// face frame (gm1 = gamma - 1 = 2/(N + 3)) instead of three contractions
+// of full-line moment matrices.
 template <typename T>
 __device__ __forceinline__ void euler_rate(const T *ds, T ir, T U, T V, T W, T H, T gm1,
                                            T out[5]) {
@@ -306,19 +329,7 @@ __device__ __forceinline__ void euler_rate(const T *ds, T ir, T U, T V, T W, T H
     const T k2 = T(0.5) * (U * U + V * V + W * W);
     T acc[5] = {0, 0, 0, 0, 0};
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const T *d = ds + 5 * j;
-        const T c = vel[j];
-        const T dp = gm1 * mad(k2, d[0], d[4] - U * d[1] - V * d[2] - W * d[3]);
-        const T dmj = d[1 + j];
-        acc[0] += dmj;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            acc[1 + i] = mad(vel[i], dmj, mad(c, d[1 + i], mad(-(vel[i] * c), d[0], acc[1 + i])));
-            if (i == j) acc[1 + i] += dp;
-        }
-        acc[4] = mad(c, d[4] + dp, mad(H, mad(-c, d[0], dmj), acc[4]));
-    }
+    for (int j = 0; j < 3; ++j) euler_jac_acc(ds + 5 * j, j, vel, k2, H, gm1, acc);
 #pragma unroll
     for (int i = 0; i < 5; ++i) out[i] = acc[i] * ir;
 }
@@ -432,24 +443,15 @@ __device__ __forceinline__ void equilibrium_terms(const PrimT<T> &Z, T N, T c4, 
     }
     // T0 = sum_j <u_j (abar_j.psi) psi>: the Euler flux Jacobians of W0
     // applied to its collided slopes dW0 (see euler_rate)
-    T T0[5], Ab[5];
-    euler_rate(&dW0[0][0], ir, Z.U, Z.V, Z.W,
-               mad(T(0.5) * (N + T(5)), inv2l, T(0.5) * (Z.U * Z.U + Z.V * Z.V + Z.W * Z.W)),
-               T(0.5) * c4, T0);
-    const Sym5<T> Fu = mom_matrix<1, 0, 0>(u, v, w, x2, x4);
-    {
-        T mT[5];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) mT[i] = -T0[i];
-        maxwell_slope(mT, Z.U, Z.V, Z.W, Z.lam, inv2l, N, c4, Ab);
-    }
-    // rho0-weighted slopes for the flux moments of terms 2 and 3
+    const T H0 = mad(T(0.5) * (N + T(5)), inv2l, T(0.5) * (Z.U * Z.U + Z.V * Z.V + Z.W * Z.W));
+    T T0[5];
+    euler_rate(&dW0[0][0], ir, Z.U, Z.V, Z.W, H0, T(0.5) * c4, T0);
+    // rho0-weighted slopes for the flux moments of term 2
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         ab[0][i] *= Z.rho;
         ab[1][i] *= Z.rho;
         ab[2][i] *= Z.rho;
-        Ab[i] *= Z.rho;
     }
     T Y[5];
     if (kTerm1) {
@@ -467,12 +469,18 @@ __device__ __forceinline__ void equilibrium_terms(const PrimT<T> &Z, T N, T c4, 
 #pragma unroll
     for (int i = 0; i < 5; ++i) Y[i] = Z.rho * T0[i];
     q[1] = heat(X[1], Y, Z.U, Z.V, Z.W);
-    // term 3: Abar g0; its conserved moments are -rho0 T0 (compatibility)
-    sym_acc(Fu, Ab, X[2]);
+    // term 3: Abar g0 with <(Abar.psi) psi> = -T0 (compatibility): its
+    // conserved moments are dW0/dt = -rho0 T0 and its flux moments
+    // <u (Abar.psi) psi g0> = dF_n/dW dW0/dt (the normal flux Jacobian)
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         Y[i] = -Z.rho * T0[i];
         dtW0[i] = Y[i];
+    }
+    {
+        const T vel[3] = {Z.U, Z.V, Z.W};
+        euler_jac_acc(dtW0, 0, vel, T(0.5) * (Z.U * Z.U + Z.V * Z.V + Z.W * Z.W), H0,
+                      T(0.5) * c4, X[2]);
     }
     q[2] = heat(X[2], Y, Z.U, Z.V, Z.W);
 }
