@@ -50,14 +50,14 @@ _DRAM_NOTE = ("ncu dram__bytes_read+write per unit of one launch on a 64^3 grid,
               "this launch's units (the traffic grows with the units: one pass over state "
               "and face buffers that exceed L2)")
 KERNEL_OPS = {
-    "recon5": {"fp64": 17062.0, "fp32": 130.0, "bytes": 160 + 3840, "dram": 3832.8,
+    "recon5": {"fp64": 15708.5, "fp32": 130.0, "bytes": 160 + 3840, "dram": 3832.4,
                "dram_note": _DRAM_NOTE},
-    "flux_cgks5": {"fp64": 4715.5, "fp32": 16.0, "bytes": (3840 + 720) / 12, "dram": 384.5,
+    "flux_cgks5": {"fp64": 4098.5, "fp32": 16.0, "bytes": (3840 + 720) / 12, "dram": 377.2,
                    "dram_note": _DRAM_NOTE},
-    "recon5_mixed": {"fp64": 0.0, "fp32": 16181.2, "bytes": 40 + 60 + 1920, "dram": 1788.0,
+    "recon5_mixed": {"fp64": 0.0, "fp32": 14676.2, "bytes": 40 + 60 + 1920, "dram": 1787.8,
                      "dram_note": _DRAM_NOTE},
-    "flux_cgks5_mixed": {"fp64": 21.5, "fp32": 7007.4, "bytes": (1920 + 40 + 720) / 12,
-                         "dram": 225.8, "dram_note": _DRAM_NOTE},
+    "flux_cgks5_mixed": {"fp64": 21.5, "fp32": 6380.4, "bytes": (1920 + 40 + 720) / 12,
+                         "dram": 225.2, "dram_note": _DRAM_NOTE},
 }
 KERNEL_OPS["recon5_learned"] = KERNEL_OPS["recon5_mixed"]
 KERNEL_OPS["flux_cgks5_learned"] = KERNEL_OPS["flux_cgks5_mixed"]
