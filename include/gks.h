@@ -298,10 +298,12 @@ int gks_indicator_skips(gks_ctx *ctx, unsigned long long *count);
  * Q_all[5 * total] with instance i's block [5][cells_i] at
  * 5 * gks_ensemble_offset(e, i), and gradQ_all[15 * total] with its block
  * [5][3][cells_i] at 15 * offset. The library splits the instances into
- * work items of `tile` cells; each phase of a step (dt, reconstruction,
- * flux, update) is one persistent launch over the items of all instances;
- * every instance keeps its own dt and time. Work is enqueued on an internal
- * stream ordered after and before cuda_stream. */
+ * work items of `tile` cells; a step is one persistent launch over the
+ * items of all instances whose blocks meet at grid-wide barriers between
+ * the phases (dt, reconstruction, flux, update; mode 1, the default), or
+ * one persistent launch per phase (mode 0, and always with the learned
+ * indicator on); every instance keeps its own dt and time. Work is
+ * enqueued on an internal stream ordered after and before cuda_stream. */
 typedef struct gks_ensemble gks_ensemble;
 int gks_ensemble_create(gks_ensemble **out, int n_instances, const int *dims,
                         const double *lengths, const double *phys,
@@ -318,8 +320,24 @@ int gks_ensemble_set_tile(gks_ensemble *e, int tile_cells);
 int gks_ensemble_step(gks_ensemble *e, double *Q, double *gradQ, int nsteps,
                       double t_stop, int use_graph);
 /* Synchronising: per-instance times (host array of n_instances) and the
- * status word; returns GKS_ERR_NONPHYSICAL if it is set. */
+ * status word; returns GKS_ERR_TIMEOUT if a barrier wait of the
+ * single-launch step ran out (20 s; the launch then returned without
+ * finishing the step), else GKS_ERR_NONPHYSICAL if the word is set. */
 int gks_ensemble_times(gks_ensemble *e, double *t_host, int *status);
+/* Step mode (an implementation choice, no counterpart in the paper): 1 one
+ * launch per step (default), 0 one launch per phase. Synchronises the
+ * ensemble's stream; GKS_ERR_ARG for another value. gks_ensemble_mode
+ * returns the mode (-1 for NULL). */
+int gks_ensemble_set_mode(gks_ensemble *e, int mode);
+int gks_ensemble_mode(const gks_ensemble *e);
+/* Self-check of the single-launch step's bounded barrier wait (no
+ * counterpart in the paper): launches, on cuda_stream, two blocks that
+ * wait for a third that never arrives; their waits must give up after
+ * limit_s seconds (0 < limit_s <= 10) and report it. Returns
+ * GKS_ERR_TIMEOUT when they did (the expected result), GKS_OK if the wait
+ * ended otherwise, GKS_ERR_ARG, GKS_ERR_NOMEM or GKS_ERR_CUDA.
+ * Synchronises cuda_stream; allocates 16 bytes of device memory. */
+int gks_barrier_timeout_check(double limit_s, void *cuda_stream);
 /* Autotuner: times one graph-replayed step for work-item sizes
  * 256 .. 8192 cells on a scratch copy of the state (the state and the
  * instance times are unchanged), keeps the fastest; *tile_out and *best_ms

@@ -19,9 +19,11 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["flux.cu", "recon.cu", "recon_fp64.cu", "update.cu", "capi.cu", "noalloc.cu", "mlp.cu", "ensemble.cu", "peak.cu"]
+CU_SOURCES = ["flux.cu", "recon.cu", "recon_fp64.cu", "update.cu", "capi.cu", "noalloc.cu", "mlp.cu", "ensemble.cu", "peak.cu",
+              "ensemble_step.cu"]
 CPP_SOURCES = ["tables.cpp"]
-HEADERS = ["basis.h", "common.cuh", "ff.cuh", "recon_common.cuh"]
+HEADERS = ["basis.h", "common.cuh", "ff.cuh", "recon_common.cuh", "flux_device.cuh",
+           "recon_fp64_device.cuh", "recon_mixed_device.cuh", "update_device.cuh"]
 # recon.cu (the mixed-precision reconstruction): no implicit multiply-add
 # contraction (only explicit fmaf), so that every kernel inlining the same
 # reconstruction rounds identically (the learned indicator's never-skip

@@ -9,6 +9,14 @@ namespace gks {
 // status word bits (gks_status)
 constexpr int kStatusNonphysical = 1;
 constexpr int kStatusNonfinite = 2;
+constexpr int kStatusTimeout = 4;   // a bounded device wait gave up
+
+// Grid-wide barrier of the ensemble's single-launch step (ensemble_step.cu):
+// arrivals, generation, abort word; zeroed before every launch.
+struct StepSync {
+    unsigned int count, gen;
+    int abort, pad;
+};
 
 struct GridDesc {
     int nx, ny, nz;
@@ -202,6 +210,20 @@ int launch_diagnostics(const GridDesc &g, const PhysParams &P, const double *Q,
                        const double *G, double *partials, int nblocks, double *out_dev,
                        cudaStream_t s);
 int diagnostics_blocks(const GridDesc &g);
+
+// the ensemble's time step as one persistent launch (ensemble_step.cu):
+// its own copy of the reconstruction tables (FP64 tables and the FP32
+// table), the grid it launches, the launch, and a barrier that cannot
+// complete (its bounded wait must report kStatusTimeout)
+int upload_recon_tables_step(const ReconTables &t, const float *tab, size_t tab_bytes);
+int ens_step_grid(int mixed);
+int launch_ens_step(const EnsInst *inst, int ninst, const EnsItem *items, int nitems,
+                    long long total, int mixed, double *Q, double *G, double *Qs, double *Gs,
+                    double *Acc, double *S1, void *fs, float *Gf, float *Qv, double *frec,
+                    double *dt, double *t, double *red, double t_stop, StepSync *sync,
+                    double limit_s, int *status, cudaStream_t s);
+int launch_barrier_timeout(StepSync *sync, int blocks, double limit_s, int *status,
+                           cudaStream_t s);
 
 // persistent ensemble kernels (see ensemble.cu)
 // mixed ensemble kernels read the arenas' views (Gfa, Qhia, Qloa)

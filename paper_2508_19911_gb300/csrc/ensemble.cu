@@ -3,14 +3,16 @@
 // The instances' states are concatenated in caller-owned arenas (instance
 // i's Q block [5][cells_i] starts at 5*off_i, its gradQ block [5][3][cells_i]
 // at 15*off_i). The library splits every instance into work items of
-// `tile` cells; each phase of a time step (dt reduction, reconstruction,
-// flux, update) is ONE persistent launch whose blocks stride over the work
-// items of all instances, each instance with its own dt, time and physics.
-// A whole time step (8 launches; 12 in mixed precision, which adds the two
-// views of the state per stage) is captured once into a CUDA graph and
-// replayed; the autotuner times the graph for a set of tile sizes on a
-// scratch copy of the state and keeps the fastest. The same machinery
-// dumps the learned indicator's training data from all instances.
+// `tile` cells, each instance with its own dt, time and physics. A time
+// step is, in mode 1 (the default), ONE persistent launch whose blocks
+// stride over the work items of all instances phase by phase (dt,
+// reconstruction, flux, update; ensemble_step.cu), separated by grid-wide
+// barriers; in mode 0, one persistent launch per phase (8 launches; 12 in
+// mixed precision, which adds the two views of the state per stage). The
+// step is captured once into a CUDA graph and replayed; the autotuner times
+// the graph for a set of tile sizes on a scratch copy of the state and
+// keeps the fastest. The same work items serve the learned indicator's
+// training dumps from all instances.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -34,6 +36,8 @@ struct gks_ensemble {
     long long total = 0;
     int mixed = 0, indicator_on = 0;
     int tile = 1024;
+    int mode = 1;                    // 1: one launch per step; 0: one per phase
+    StepSync *sync = nullptr;        // the single-launch step's grid barrier
     std::vector<EnsItem> items;
     EnsItem *ditems = nullptr;
     int nitems = 0, items_cap = 0;
@@ -49,7 +53,7 @@ struct gks_ensemble {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const double *gQ = nullptr, *gG = nullptr;
-    int g_tile = 0, g_ind = 0;
+    int g_tile = 0, g_ind = 0, g_mode = -1;
     double g_tstop = 0.0;
 };
 
@@ -103,8 +107,19 @@ int build_items(gks_ensemble *e, int tile) {
     return GKS_OK;
 }
 
-// one time step of every instance on stream e->s (8 launches)
+// wall-clock limit of a grid-barrier wait in the single-launch step: far
+// above any phase's duration (the largest ensembles' flux phase takes well
+// under a second), short enough that a stuck launch returns
+constexpr double kStepWaitLimitS = 20.0;
+
+// one time step of every instance on stream e->s (one launch, or 8 / 12)
 int enqueue_step(gks_ensemble *e, double *Q, double *G, double t_stop) {
+    if (e->mode == 1 && !e->indicator_on)
+        return launch_ens_step(e->dinst, e->ninst, e->ditems, e->nitems, e->total, e->mixed, Q, G,
+                               e->Qs, e->Gs, e->Acc, e->S1, e->fs, e->Gf, e->Qv, e->frec, e->dt,
+                               e->t, e->red, t_stop, e->sync, kStepWaitLimitS, e->status, e->s)
+                   ? GKS_ERR_CUDA
+                   : GKS_OK;
     const int heavy = std::min(e->nitems, 2 * e->sms);  // 128-thread, register-heavy kernels
     const int light = std::min(e->nitems, 4 * e->sms);  // 256-thread kernels
     if (launch_dt_ens(e->dinst, e->ninst, e->ditems, e->nitems, light, Q, e->red, e->dt, e->t,
@@ -137,7 +152,7 @@ int run_steps(gks_ensemble *e, double *Q, double *G, int nsteps, double t_stop, 
         return GKS_OK;
     }
     if (!e->exec || e->gQ != Q || e->gG != G || e->g_tile != e->tile ||
-        e->g_tstop != t_stop || e->g_ind != e->indicator_on) {
+        e->g_tstop != t_stop || e->g_ind != e->indicator_on || e->g_mode != e->mode) {
         drop_graph(e);
         if (cudaStreamBeginCapture(e->s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return GKS_ERR_CUDA;
@@ -159,6 +174,7 @@ int run_steps(gks_ensemble *e, double *Q, double *G, int nsteps, double t_stop, 
         e->g_tile = e->tile;
         e->g_tstop = t_stop;
         e->g_ind = e->indicator_on;
+        e->g_mode = e->mode;
     }
     for (int k = 0; k < nsteps; ++k)
         if (cudaGraphLaunch(e->exec, e->s) != cudaSuccess) return GKS_ERR_CUDA;
@@ -188,6 +204,7 @@ void gks_ensemble_destroy(gks_ensemble *e) {
     cudaFree(e->t);
     cudaFree(e->red);
     cudaFree(e->status);
+    cudaFree(e->sync);
     cudaFree(e->skips);
     if (e->ev_in) cudaEventDestroy(e->ev_in);
     if (e->ev_out) cudaEventDestroy(e->ev_out);
@@ -255,7 +272,7 @@ int gks_ensemble_create(gks_ensemble **out, int n, const int *dims, const double
         (rc = ealloc(&e->frec, 90 * N)) || (rc = ealloc(&e->Qs, 5 * N)) ||
         (rc = ealloc(&e->Gs, 15 * N)) || (rc = ealloc(&e->Acc, 5 * N)) ||
         (rc = ealloc(&e->S1, 15 * N)) || (rc = ealloc(&e->dt, n)) || (rc = ealloc(&e->t, n)) ||
-        (rc = ealloc(&e->red, 2 * n)) || (rc = ealloc(&e->status, 1)) ||
+        (rc = ealloc(&e->red, 2 * n)) || (rc = ealloc(&e->status, 1)) || (rc = ealloc(&e->sync, 1)) ||
         (rc = ealloc(&e->skips, 1))) {
         gks_ensemble_destroy(e);
         return rc;
@@ -308,7 +325,41 @@ int gks_ensemble_times(gks_ensemble *e, double *t_host, int *status) {
         cudaMemcpy(&st, e->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return GKS_ERR_CUDA;
     if (status) *status = st;
+    if (st & kStatusTimeout) return GKS_ERR_TIMEOUT;
     return st ? GKS_ERR_NONPHYSICAL : GKS_OK;
+}
+
+int gks_ensemble_set_mode(gks_ensemble *e, int mode) {
+    if (!e || (mode != 0 && mode != 1)) return GKS_ERR_ARG;
+    if (e->s && cudaStreamSynchronize(e->s) != cudaSuccess) return GKS_ERR_CUDA;
+    e->mode = mode;
+    drop_graph(e);
+    return GKS_OK;
+}
+
+int gks_ensemble_mode(const gks_ensemble *e) { return e ? e->mode : -1; }
+
+int gks_barrier_timeout_check(double limit_s, void *cuda_stream) {
+    if (!(limit_s > 0.0 && limit_s <= 10.0)) return GKS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    StepSync *sync = nullptr;
+    int *st = nullptr;
+    if (ealloc(&sync, 1) || ealloc(&st, 1)) {
+        cudaFree(sync);
+        return GKS_ERR_NOMEM;
+    }
+    int host = 0;
+    int rc = GKS_OK;
+    if (cudaMemsetAsync(st, 0, sizeof(int), s) != cudaSuccess ||
+        launch_barrier_timeout(sync, 2, limit_s, st, s) ||
+        cudaMemcpyAsync(&host, st, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        rc = GKS_ERR_CUDA;
+    cudaStreamSynchronize(s);  // no copy into host left in flight
+    cudaFree(sync);
+    cudaFree(st);
+    if (rc) return rc;
+    return (host & kStatusTimeout) ? GKS_ERR_TIMEOUT : GKS_OK;
 }
 
 int gks_ensemble_autotune(gks_ensemble *e, const double *Q, const double *G, int *tile_out,

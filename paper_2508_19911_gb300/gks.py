@@ -95,6 +95,9 @@ SIGNATURES = {
     "gks_ensemble_autotune": (_I, [_VP, _VP, _VP, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]),
     "gks_ensemble_dump": (_I, [_VP, _VP, _VP, ctypes.c_float, _VP, _VP, _VP]),
     "gks_ensemble_set_indicator": (_I, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_float]),
+    "gks_ensemble_set_mode": (_I, [_VP, _I]),
+    "gks_ensemble_mode": (_I, [_VP]),
+    "gks_barrier_timeout_check": (_I, [_D, _VP]),
 }
 
 
@@ -452,6 +455,14 @@ class Ensemble:
     def set_tile(self, tile):
         _check(lib().gks_ensemble_set_tile(self.e, int(tile)), "gks_ensemble_set_tile")
 
+    def set_mode(self, mode):
+        """1: a step is one persistent launch (default); 0: one per phase."""
+        _check(lib().gks_ensemble_set_mode(self.e, int(mode)), "gks_ensemble_set_mode")
+
+    @property
+    def mode(self):
+        return int(lib().gks_ensemble_mode(self.e))
+
     def step(self, nsteps=1, t_stop=math.inf, graph=True):
         _check(lib().gks_ensemble_step(self.e, _ptr(self.Q), _ptr(self.G), int(nsteps),
                                        float(t_stop), int(bool(graph))), "gks_ensemble_step")
@@ -485,3 +496,11 @@ class Ensemble:
         p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
         _check(lib().gks_ensemble_set_indicator(self.e, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                                 float(theta)), "gks_ensemble_set_indicator")
+
+
+def barrier_timeout_check(limit_s=0.2, stream=None):
+    """The single-launch ensemble step's bounded barrier wait, made to run
+    out: returns the C-ABI code (GKS_ERR_TIMEOUT = -4 expected)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return int(lib().gks_barrier_timeout_check(float(limit_s), _VP(st.cuda_stream)))

@@ -166,3 +166,42 @@ def test_set_tile_right_after_an_asynchronous_step(env):
         runs.append((e.Q.clone(), e.G.clone()))
         e.close()
     assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
+
+
+@pytest.mark.parametrize("precision,tol,tol_t", [("fp64", 1e-13, 1e-12), ("mixed", 1e-6, 1e-8)])
+def test_single_launch_step_equals_the_per_phase_launches(env, precision, tol, tol_t):
+    """Mode 1 (one persistent launch per step, phases separated by grid-wide
+    barriers) against mode 0 (one persistent launch per phase): the same
+    device code in another kernel, so the same first dt and states equal to
+    rounding (the single-launch kernel's translation unit contracts the
+    mixed reconstruction's multiply-adds, which the per-phase one does not;
+    the later dt follow the states: 4e-10 apart after 4 mixed steps)."""
+    torch, dev, gks = env
+    insts = small_instances()
+    res = []
+    for mode in (0, 1):
+        e = build(env, insts, precision)
+        e.set_mode(mode)
+        assert e.mode == mode
+        e.step(1, graph=False)
+        t1 = e.times()
+        e.step(3, graph=True)
+        res.append((t1, e.times(), e.Q.clone(), e.G.clone()))
+        e.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    np.testing.assert_allclose(res[1][1], res[0][1], rtol=tol_t)
+    q0, q1 = res[0][2], res[1][2]
+    assert float((q1 - q0).abs().max() / q0.abs().max()) < tol
+
+
+def test_barrier_wait_runs_out_and_the_device_stays_usable(env):
+    """Two blocks wait at a barrier for a third that never arrives: their
+    bounded waits give up after 0.2 s and report a timeout (no hang, no
+    fault); an ensemble step afterwards runs normally."""
+    torch, dev, gks = env
+    assert gks.barrier_timeout_check(0.2) == -4  # GKS_ERR_TIMEOUT
+    insts = small_instances()[:2]
+    e = build(env, insts, "fp64")
+    e.step(2, graph=True)
+    t = e.times()
+    assert np.all(t > 0)
