@@ -113,11 +113,16 @@ def parse():
     ap.add_argument("--c3", action="store_true",
                     help="isotropic turbulence Mt 0.5 and 1.0 (Re_lambda 72), FP64 vs mixed vs "
                          "mixed + learned indicator, per-step E_k, eps_S, eps_D (default 256^3)")
+    ap.add_argument("--general", action="store_true",
+                    help="general-grid kernels: the Taylor-Green octant [0, pi]^3 bounded by six "
+                         "symmetry planes on a stretched mesh (cells 0.7-1.3 times the mean), "
+                         "FP64 and mixed, against the periodic uniform kernels on the same cell "
+                         "count (default 256^3)")
     ap.add_argument("--history", default=None,
                     help="--c2/--c3: write the sampled histories to this JSON file")
     args = ap.parse_args()
     if args.n is None:
-        args.n = (64 if args.c2 else 256 if args.c3 else 512 if args.c5
+        args.n = (64 if args.c2 else 256 if (args.c3 or args.general) else 512 if args.c5
                   else 128 if args.workload == "tgv" else 512)
     return args
 
@@ -947,8 +952,63 @@ def run_c4(args):
     }
 
 
+def run_general(args):
+    """Row N3 measured: CGKS-5th nonlinear on the Taylor-Green octant with
+    six symmetry planes (mirror ghosts) on a stretched mesh, through the
+    general-grid kernels, FP64 and mixed; the same cell count on the
+    periodic uniform kernels beside it (the cost of the general gathers and
+    the boundary faces). Cell-stage updates per second."""
+    import torch
+
+    from paper_2508_19911_gb300 import gks
+    from paper_2508_19911_gb300 import workloads as wl
+
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    n = args.n
+    e = wl.stretched_edges(2 * n, 2 * np.pi, 0.3)[:n + 1]
+    Qo, Go, go = wl.taylor_green(edges=(e, e, e))
+    Qp, Gp, gp = wl.taylor_green(n)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        for name, (Q, G, grid, kw) in {
+                "octant_symmetry_stretched": (Qo, Go, go, dict(bc=("symmetry",) * 3,
+                                                              spacing=go.spacing)),
+                "periodic_uniform": (Qp, Gp, gp, {})}.items():
+            s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision=prec,
+                                      mu=1.0 / 1600, **kw), stream)
+            Qd, Gd = torch.tensor(Q, device=dev), torch.tensor(G, device=dev)
+            ms, kt, clk = timed_steps(torch, s, Qd, Gd, args.warmup, args.steps, stream, 0)
+            if s.status():
+                raise RuntimeError(f"non-physical state ({name}, {prec})")
+            out[f"{name}_{prec}"] = {
+                "value": n ** 3 * 2 * args.steps / (ms / 1e3), "unit": "cell-stage/s",
+                "ms_per_step": ms / args.steps,
+                "recon_ms": kt["recon"][0] / max(kt["recon"][1], 1),
+                "flux_ms": kt["flux"][0] / max(kt["flux"][1], 1), "clocks": clk}
+            s.close()
+            del Qd, Gd
+            torch.cuda.empty_cache()
+    for prec in ("fp64", "mixed"):
+        out[f"general_over_periodic_{prec}"] = (out[f"octant_symmetry_stretched_{prec}"]["value"] /
+                                                out[f"periodic_uniform_{prec}"]["value"])
+    return {
+        "metric": METRIC, "value": out["octant_symmetry_stretched_fp64"]["value"],
+        "unit": "cell-stage/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": out["octant_symmetry_stretched_fp64"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Taylor-Green cell averages)",
+        "config": {"workload": f"taylor_green_octant_{n}^3_symmetry_stretched_cgks5",
+                   "cells": n ** 3, "stretch": "0.7-1.3 of the mean cell"},
+        "paths": out,
+    }
+
+
 def main():
     args = parse()
+    if args.general:
+        print(json.dumps(run_general(args)))
+        return
     if args.c4:
         print(json.dumps(run_c4(args)))
         return

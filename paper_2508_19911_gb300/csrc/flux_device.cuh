@@ -26,11 +26,17 @@ __device__ __forceinline__ void full_line(T C, T inv2l, T *m) {
     for (int k = 0; k + 2 < N; ++k) m[k + 2] = C * m[k + 1] + (k + 1) * inv2l * m[k];
 }
 
-// starting values of the half-line moments: sgn = +1 for u > 0, -1 for u < 0
+// starting values of the half-line moments: sgn = +1 for u > 0, -1 for u < 0.
+// With y = sgn sqrt(lam) C and E = exp(-y^2) (which the edge term needs
+// anyway), erfc(-y) = erfcx(|y|) E for y <= 0 and 2 - erfcx(|y|) E for
+// y > 0 (no cancellation either way): one exponential instead of two.
 __device__ __forceinline__ void half_start(double C, double lam, double sgn, double &m0, double &m1) {
     const double rsl = rsqrt(lam), sl = lam * rsl;
-    m0 = 0.5 * erfc(-sgn * sl * C);
-    const double edge = 0.28209479177387814347 * exp(-lam * C * C) * rsl;  // 1/(2 sqrt(pi))
+    const double y = sgn * sl * C;
+    const double E = exp(-lam * C * C);
+    const double ec = erfcx(fabs(y)) * E;  // erfc(|y|)
+    m0 = 0.5 * (y > 0.0 ? 2.0 - ec : ec);
+    const double edge = 0.28209479177387814347 * E * rsl;  // 1/(2 sqrt(pi))
     m1 = C * m0 + sgn * edge;
 }
 
@@ -181,30 +187,6 @@ __device__ __forceinline__ void time_integrals(double T, double tau, double c[6]
     c[5] = -t2 * E;
 }
 
-// the closed forms above for E = 1 - e^{-x}, given E directly
-__device__ __forceinline__ void time_integrals_closed(double T, double tau, double E, double c[6]) {
-    const double t2 = tau * tau;
-    c[0] = T - tau * E;
-    c[1] = 2.0 * t2 * E - tau * T * (2.0 - E);
-    c[2] = 0.5 * T * T - tau * T + t2 * E;
-    c[3] = tau * E;
-    c[4] = -2.0 * t2 * E + tau * T * (1.0 - E);
-    c[5] = -t2 * E;
-}
-
-// both intervals [0, dt] and [0, dt/2]: when dt/(2 tau) >= 1 one exponential
-// serves both (E = 1 - e_h^2, E_h = 1 - e_h, no cancellation for e_h <= 1/e)
-__device__ __forceinline__ void time_integrals_pair(double dt, double tau, double cA[6],
-                                                    double cH[6]) {
-    if (tau > 0.0 && dt >= 2.0 * tau) {
-        const double eh = exp(-0.5 * dt / tau);
-        time_integrals_closed(dt, tau, 1.0 - eh * eh, cA);
-        time_integrals_closed(0.5 * dt, tau, 1.0 - eh, cH);
-    } else {
-        time_integrals(dt, tau, cA);
-        time_integrals(0.5 * dt, tau, cH);
-    }
-}
 
 // Coefficients of terms 2..6 (k = 1..5) in F^n = sum_k al_k X_k and
 // F_t = sum_k be_k X_k, al_k = (4 C_k(dt/2) - C_k(dt))/dt, be_k =
@@ -501,31 +483,33 @@ __device__ __forceinline__ void interface_state(const Prim &L, const Prim &R, do
     for (int i = 0; i < 5; ++i) W0[i] += R.rho * o[i];
 }
 
-// collision time (Sec. 4) and F^n, F_t^n from the six term moments
+// collision time (Sec. 4) and F^n, F_t^n from the six term moments: the
+// coefficients al_k, be_k of time_coefficients (closed forms for
+// dt >= 2 tau, the time-integral series below), with al_1 = 1 - al_4 and
+// be_1 = -be_4 (the time functions of terms 1 and 4 add up to 1)
 __device__ __forceinline__ void combine_terms(const PhysParams &P, const Prim &L, const Prim &R,
                                               const Prim &Z, double dt, const double X[6][5],
                                               const double q[6], double out[10], double &dpr) {
     dpr = fabs((L.p - R.p) / (L.p + R.p));
     const double tau = P.inviscid ? (P.eps_tau * dt + P.C_tau * dpr * dt)
                                   : (viscosity(P, Z.rho, Z.p) / Z.p + P.C_tau * dpr * dt);
-    double cA[6], cH[6];
-    time_integrals_pair(dt, tau, cA, cH);
-    const double idt = 1.0 / dt, idt2 = idt * idt;
+    double al[6], be[6];
+    time_coefficients(dt, tau, al, be, 2.0);
+    al[0] = 1.0 - al[3];
+    be[0] = -be[3];
     const double prfix = 1.0 / P.Pr - 1.0;
     double qn = 0.0, qt = 0.0;
 #pragma unroll
     for (int i = 0; i < 10; ++i) out[i] = 0.0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        const double al = (4.0 * cH[k] - cA[k]) * idt;
-        const double be = 4.0 * (cA[k] - 2.0 * cH[k]) * idt2;
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            out[i] += al * X[k][i];
-            out[5 + i] += be * X[k][i];
+            out[i] += al[k] * X[k][i];
+            out[5 + i] += be[k] * X[k][i];
         }
-        qn += al * q[k];
-        qt += be * q[k];
+        qn += al[k] * q[k];
+        qt += be[k] * q[k];
     }
     out[4] += prfix * qn;
     out[9] += prfix * qt;
