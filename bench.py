@@ -52,7 +52,7 @@ _DRAM_NOTE = ("ncu dram__bytes_read+write per unit of one launch on a 64^3 grid,
 KERNEL_OPS = {
     "recon5": {"fp64": 15708.5, "fp32": 130.0, "bytes": 160 + 3840, "dram": 3832.4,
                "dram_note": _DRAM_NOTE},
-    "flux_cgks5": {"fp64": 4098.5, "fp32": 16.0, "bytes": (3840 + 720) / 12, "dram": 377.2,
+    "flux_cgks5": {"fp64": 4006.5, "fp32": 16.0, "bytes": (3840 + 720) / 12, "dram": 377.4,
                    "dram_note": _DRAM_NOTE},
     "recon5_mixed": {"fp64": 0.0, "fp32": 14676.2, "bytes": 40 + 60 + 1920, "dram": 1787.8,
                      "dram_note": _DRAM_NOTE},
