@@ -21,7 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["moments.cpp", "flux.cpp", "recon.cpp", "scheme.cpp", "mlp.cpp"]
+_SOURCES = ["moments.cpp", "flux.cpp", "recon.cpp", "scheme.cpp", "scheme_b.cpp", "mlp.cpp"]
 _LOCK = threading.Lock()
 _LIB = None
 
@@ -108,6 +108,11 @@ def lib():
                 "orc_flux_gp": [_P, _D, _D, ctypes.c_double, _D],
                 "orc_fbar": [_P, _D, _D, ctypes.c_double, ctypes.c_double, _D],
                 "orc_recon5_matrix": [_D],
+                "orc_recon5b_matrix": [_D],
+                "orc_recon5b_cell": [_D, _D, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, _D, _D],
+                "orc_run_b": [_P, _D, _D, ctypes.c_int, ctypes.c_double, _D, _D],
+                "orc_face_states_b": [_P, _D, _D, _D],
                 "orc_geno_misfit": [_D, _D, _D],
                 "orc_chi_field": [_P, _D, _D, _D],
                 "orc_recon5_cell": [_D, _D, ctypes.c_double, ctypes.c_double,
@@ -179,6 +184,40 @@ def recon5_matrix():
     R = np.zeros((34, 63))
     _check(lib().orc_recon5_matrix(_ptr(R)), "recon5_matrix")
     return R
+
+
+def recon5b_matrix():
+    """Reading B's least-squares matrix (34 x 72)."""
+    R = np.zeros((34, 72))
+    _check(lib().orc_recon5b_matrix(_ptr(R)), "recon5b_matrix")
+    return R
+
+
+def recon5b_cell(q0, dvec, h=(1.0, 1.0, 1.0), nonlinear=1):
+    out = np.zeros(480)
+    chi = np.zeros(5)
+    _check(lib().orc_recon5b_cell(_ptr(np.ascontiguousarray(q0, float)),
+                                  _ptr(np.ascontiguousarray(dvec, float)),
+                                  h[0], h[1], h[2], nonlinear, _ptr(out), _ptr(chi)),
+           "recon5b_cell")
+    return out.reshape(6, 4, 20), chi
+
+
+def run_b(P, Q, L, nsteps=1, t_stop=np.inf, t=0.0):
+    """CGKS-5th with reading B: advance Q [5][cells...] and the line-averaged
+    derivatives L [5][12][cells...] in place; returns (t, dt_last)."""
+    tt = np.array([t], float)
+    dl = np.zeros(1)
+    _check(lib().orc_run_b(ctypes.byref(P), _ptr(Q), _ptr(L), nsteps, t_stop,
+                           _ptr(tt), _ptr(dl)), "run_b")
+    return float(tt[0]), float(dl[0])
+
+
+def face_states_b(P, Q, L):
+    n = P.nx * P.ny * P.nz
+    fs = np.zeros((6, 4, 20, n))
+    _check(lib().orc_face_states_b(ctypes.byref(P), _ptr(Q), _ptr(L), _ptr(fs)), "face_states_b")
+    return fs
 
 
 def geno_misfit(q0, dvec):

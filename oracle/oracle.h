@@ -113,6 +113,15 @@ int orc_recon5_cell(const double *q0, const double *dvec, double hx,
 int orc_recon2_cell(const double *q7, double hx, double hy, double hz,
                     int nonlinear, double *out120, double *phi5);
 
+/* Reading B of S^0 (row N2): the target cell's 12 line-averaged
+ * derivatives instead of its averaged gradient. dvec[5*72]: entries 0..59
+ * as above, 60 + 4a + k the line along axis a at face Gauss point k
+ * (times h_a); R is 34 x 72.                                              */
+int orc_recon5b_matrix(double *R34x72);
+int orc_recon5b_cell(const double *q0, const double *dvec, double hx,
+                     double hy, double hz, int nonlinear, double *out480,
+                     double *chi5);
+
 /* --- Scheme (Sec. 3.4, Sec. 4) ------------------------------------------ */
 int orc_dt(const orc_params *P, const double *Q, double *dt);
 /* Advance nsteps (or until t reaches t_stop). Q [5][nz][ny][nx];
@@ -142,6 +151,14 @@ int orc_face_states_at(const orc_params *P, const double *Q, const double *G,
  * rec30 = F^n, F_t^n, Q^l, dQ^l/dt, Q^r, dQ^r/dt (5 each).               */
 int orc_face_record(const orc_params *P, int d, const double *sl, const double *sr,
                     double dt, double *rec30);
+/* CGKS-5th with reading B (periodic grids): state Q [5][cells] and the
+ * line-averaged derivatives L [5][12][cells] (axis a, Gauss point k at
+ * 4a + k; see scheme_b.cpp). Returns -1 for a non-periodic axis or
+ * GKS-2nd.                                                                */
+int orc_run_b(const orc_params *P, double *Q, double *L, int nsteps,
+              double t_stop, double *t, double *dt_last);
+int orc_face_states_b(const orc_params *P, const double *Q, const double *L,
+                      double *fs);
 /* out[12]: Ek, eps_S, eps_D, min rho, min p, sum Q h^3 (5), bad cells,
  * max(|U_d|+c).                                                           */
 int orc_diagnostics(const orc_params *P, const double *Q, const double *G,

@@ -40,10 +40,11 @@ int flux_gp(const orc_params &P, const double *sl, const double *sr,
             double dt, double *out30);
 
 /* recon.cpp */
-double geno_misfit(const double *q0, const double *d, const double *a, int v);
+/* variant 0: reading A (63-entry data vectors); 1: reading B (72) */
+double geno_misfit(const double *q0, const double *d, const double *a, int v, int variant);
 double geno_chi(double sigma);
 void recon5_cell(const double *q0, const double *dvec, double hx, double hy,
-                 double hz, int nonlinear, double *out480, double *chi5);
+                 double hz, int nonlinear, double *out480, double *chi5, int variant = 0);
 void recon2_cell(const double *q7, double hx, double hy, double hz,
                  int nonlinear, double *out120, double *phi5);
 /* Gauss points of a face in normalised cell coordinates: face f (0..5 =

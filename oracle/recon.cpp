@@ -19,6 +19,15 @@
  *                 to the centre-to-centre offset o (a < b its non-zero
  *                 axes), tau_1 the edge direction (the axis where o = 0)
  *   d[60+j]       h_j dQ/dx_j averaged over Omega_0.
+ * Reading B of S^0 (row N2, reading R17): the own cell's data are its 12
+ * line-averaged derivatives instead of its averaged gradient, d has 72
+ * entries and
+ *   d[60+4a+k]    h_a (Q(x_a = +h_a/2) - Q(x_a = -h_a/2))/h_a along the line
+ *                 through the cell parallel to axis a at the tangential
+ *                 position of face Gauss point k (k as face_gauss_point);
+ * the neighbours' gradients are their cell averages (the mean of their four
+ * line derivatives per axis), and P1_m's tangential slopes come from the
+ * own averaged gradient, the mean of its four lines per axis.
  */
 #include "oracle_internal.h"
 
@@ -113,15 +122,22 @@ int gauss_jordan(int n, int m, std::vector<ld> &A) {
 }
 
 struct Recon5Tables {
-    double R[34][63];          /* coefficients a = R d                      */
-    double B[45][34];          /* derivative rows of Eq. compact-big-5
-                                  (unweighted)                              */
-    double wq[45];             /* their least-squares weights (R3)          */
+    double R[34][72];          /* coefficients a = R d (nd columns)         */
+    double B[54][34];          /* derivative rows of Eq. compact-big-5
+                                  (unweighted; nB of them)                  */
+    double wq[54];             /* their least-squares weights (R3)          */
     double mean0[34];          /* mean of delta^d/d! over the target cell   */
+    int nd, nB;                /* 63, 45 (reading A); 72, 54 (reading B)   */
     int ok;
 };
 
-Recon5Tables build_tables() {
+/* value of delta^d/d! at x (normalised coordinates) */
+ld mono_at(const ld x[3], const int d[3]) {
+    return ipow(x[0], d[0]) * ipow(x[1], d[1]) * ipow(x[2], d[2]) /
+           (fact(d[0]) * fact(d[1]) * fact(d[2]));
+}
+
+Recon5Tables build_tables(int variant) {
     Recon5Tables T;
     std::memset(&T, 0, sizeof(T));
     const Basis b = make_basis();
@@ -130,7 +146,8 @@ Recon5Tables build_tables() {
      *   C a = d_C  (cell averages of the 18 neighbours, exact),
      *   B a ~ d_B  (45 derivative equations, weighted least squares R3).
      * KKT system [B^T B  C^T; C  0] [a; lambda] = [B^T d_B; d_C].        */
-    ld C[18][34], B[45][34];
+    const int nB = variant ? 54 : 45, nd = 18 + nB;
+    ld C[18][34], B[54][34];
     for (int k = 0; k < 18; ++k) {
         const int *o = (k < 6) ? kFace[k] : kEdge[k - 6];
         for (int i = 0; i < 34; ++i) C[k][i] = avg_p(o, b.d[i]);
@@ -153,8 +170,23 @@ Recon5Tables build_tables() {
         for (int i = 0; i < 34; ++i) B[r][i] = avg_dp(o, b.d[i], ez);
         ++r;
     }
-    for (int j = 0; j < 3; ++j, ++r)
-        for (int i = 0; i < 34; ++i) B[r][i] = avg_dp(z, b.d[i], j);
+    if (!variant) {
+        for (int j = 0; j < 3; ++j, ++r)
+            for (int i = 0; i < 34; ++i) B[r][i] = avg_dp(z, b.d[i], j);
+    } else {
+        /* the 12 line-averaged derivatives of the target cell: along axis a
+         * between the face Gauss points k of its two faces normal to a */
+        const ld g = 0.5L / std::sqrt(3.0L);
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 4; ++k, ++r) {
+                ld x1[3], x2[3];
+                x1[a] = -0.5L;
+                x2[a] = 0.5L;
+                x1[(a + 1) % 3] = x2[(a + 1) % 3] = (k & 1) ? g : -g;
+                x1[(a + 2) % 3] = x2[(a + 2) % 3] = (k & 2) ? g : -g;
+                for (int i = 0; i < 34; ++i) B[r][i] = mono_at(x2, b.d[i]) - mono_at(x1, b.d[i]);
+            }
+    }
 
     /* row weights h_1, h_2, h_3 of Eq. compact-big-5 (relative to the cell
      * size that scales the derivative data): the paper states only their
@@ -163,25 +195,25 @@ Recon5Tables build_tables() {
      * 0.1 for the edge neighbours' tangential derivatives, near the minimum
      * of the condition number of the weighted least-squares system on the
      * null space of the constraints (5.07 against 29.6 with unit weights). */
-    ld wq[45];
-    for (int q = 0; q < 45; ++q) wq[q] = (q >= 18 && q < 42) ? 0.1L : 1.0L;
-    for (int q = 0; q < 45; ++q) {
+    ld wq[54];
+    for (int q = 0; q < nB; ++q) wq[q] = (q >= 18 && q < 42) ? 0.1L : 1.0L;
+    for (int q = 0; q < nB; ++q) {
         T.wq[q] = (double)wq[q];
         for (int i = 0; i < 34; ++i) T.B[q][i] = (double)B[q][i];
     }
-    for (int q = 0; q < 45; ++q)
+    for (int q = 0; q < nB; ++q)
         for (int i = 0; i < 34; ++i) B[q][i] *= wq[q];
-    const int n = 34 + 18, m = 63, w = n + m;
+    const int n = 34 + 18, m = nd, w = n + m;
     std::vector<ld> A((size_t)n * w, 0);
     for (int i = 0; i < 34; ++i) {
         for (int j = 0; j < 34; ++j) {
             ld s = 0;
-            for (int q = 0; q < 45; ++q) s += B[q][i] * B[q][j];
+            for (int q = 0; q < nB; ++q) s += B[q][i] * B[q][j];
             A[i * w + j] = s;
         }
         for (int k = 0; k < 18; ++k) A[i * w + 34 + k] = C[k][i];
         /* right-hand side for the derivative data: (W B)^T W e_q */
-        for (int q = 0; q < 45; ++q) A[i * w + n + 18 + q] = wq[q] * B[q][i];
+        for (int q = 0; q < nB; ++q) A[i * w + n + 18 + q] = wq[q] * B[q][i];
     }
     for (int k = 0; k < 18; ++k) {
         for (int j = 0; j < 34; ++j) A[(34 + k) * w + j] = C[k][j];
@@ -189,18 +221,20 @@ Recon5Tables build_tables() {
     }
     if (gauss_jordan(n, m, A)) { T.ok = 0; return T; }
     for (int i = 0; i < 34; ++i)
-        for (int c = 0; c < 63; ++c) T.R[i][c] = (double)A[i * w + n + c];
+        for (int c = 0; c < nd; ++c) T.R[i][c] = (double)A[i * w + n + c];
+    T.nd = nd;
+    T.nB = nB;
 
     for (int i = 0; i < 34; ++i) T.mean0[i] = (double)avg_mono(z, b.d[i]);
     T.ok = 1;
     return T;
 }
 
-const Recon5Tables &tables() {
-    static Recon5Tables T;
-    static std::once_flag once;
-    std::call_once(once, [] { T = build_tables(); });
-    return T;
+const Recon5Tables &tables(int variant = 0) {
+    static Recon5Tables T[2];
+    static std::once_flag once[2];
+    std::call_once(once[variant ? 1 : 0], [variant] { T[variant ? 1 : 0] = build_tables(variant); });
+    return T[variant ? 1 : 0];
 }
 
 const Basis &basis() {
@@ -247,12 +281,12 @@ void eval_basis(const double x[3], double p[34], double dp[3][34]) {
  * misfit (no sharp switch on smooth but under-resolved data, whose
  * rounding it would amplify), chi ~ s^-2 at a discontinuity (chi < 1e-3
  * where sigma > 0.016; a jump through the cell gives 0.02 to 0.1). */
-double geno_misfit(const double *q0, const double *d, const double *a, int v) {
-    const Recon5Tables &T = tables();
+double geno_misfit(const double *q0, const double *d, const double *a, int v, int variant) {
+    const Recon5Tables &T = tables(variant);
     const double eps = 1e-15, kappa = 0.01;
     double res2 = 0.0, norm2 = 0.0;
     for (int k = 0; k < 18; ++k) norm2 += d[k] * d[k];
-    for (int q = 0; q < 45; ++q) {
+    for (int q = 0; q < T.nB; ++q) {
         double Ba = 0.0;
         for (int i = 0; i < 34; ++i) Ba += T.B[q][i] * a[i];
         const double r = T.wq[q] * (Ba - d[18 + q]);
@@ -273,20 +307,26 @@ double geno_chi(double sigma) {
 }
 
 void recon5_cell(const double *q0, const double *dvec, double hx, double hy,
-                 double hz, int nonlinear, double *out, double *chi5) {
-    const Recon5Tables &T = tables();
+                 double hz, int nonlinear, double *out, double *chi5, int variant) {
+    const Recon5Tables &T = tables(variant);
     const double h[3] = {hx, hy, hz};
     /* GENO constants of Eq. weno-new */
     const double eps = 1e-15, dm = 1.0 / 6.0;
     double val[5][24], grad[5][24][3];
     for (int v = 0; v < 5; ++v) {
-        const double *d = dvec + 63 * v;
+        const double *d = dvec + T.nd * v;
         double a[34];
         for (int i = 0; i < 34; ++i) {
             double s = 0.0;
-            for (int c = 0; c < 63; ++c) s += T.R[i][c] * d[c];
+            for (int c = 0; c < T.nd; ++c) s += T.R[i][c] * d[c];
             a[i] = s;
         }
+        /* the own averaged gradient (normalised): stored, or the mean of
+         * the four line derivatives per axis (reading B) */
+        double g0[3];
+        for (int j = 0; j < 3; ++j)
+            g0[j] = variant ? 0.25 * (d[60 + 4 * j] + d[61 + 4 * j] + d[62 + 4 * j] + d[63 + 4 * j])
+                            : d[60 + j];
         double chi = 1.0, w[6] = {0, 0, 0, 0, 0, 0}, bm[6][3];
         if (nonlinear) {
             /* linear sub-stencil polynomials P1_m (reading R4) and their
@@ -295,14 +335,14 @@ void recon5_cell(const double *q0, const double *dvec, double hx, double hy,
             for (int m = 0; m < 6; ++m) {
                 const int ax = m / 2;
                 const double sg = (m % 2) ? 1.0 : -1.0;
-                for (int j = 0; j < 3; ++j) bm[m][j] = d[60 + j];
+                for (int j = 0; j < 3; ++j) bm[m][j] = g0[j];
                 bm[m][ax] = sg * d[m];
                 const double IS = bm[m][0] * bm[m][0] + bm[m][1] * bm[m][1] + bm[m][2] * bm[m][2];
                 w[m] = dm / std::pow(IS + eps, 5);
                 wsum += w[m];
             }
             for (int m = 0; m < 6; ++m) w[m] /= wsum;
-            chi = geno_chi(geno_misfit(q0, d, a, v));
+            chi = geno_chi(geno_misfit(q0, d, a, v, variant));
         }
         if (chi5) chi5[v] = chi;
         for (int f = 0; f < 6; ++f)
@@ -415,9 +455,18 @@ void recon2_cell(const double *q7, double hx, double hy, double hz,
 }  // namespace orc
 
 extern "C" int orc_recon5_matrix(double *R) {
-    const orc::Recon5Tables &T = orc::tables();
+    const orc::Recon5Tables &T = orc::tables(0);
     if (!T.ok) return -1;
-    std::memcpy(R, T.R, sizeof(T.R));
+    for (int i = 0; i < 34; ++i)
+        for (int c = 0; c < 63; ++c) R[i * 63 + c] = T.R[i][c];
+    return 0;
+}
+
+extern "C" int orc_recon5b_matrix(double *R) {
+    const orc::Recon5Tables &T = orc::tables(1);
+    if (!T.ok) return -1;
+    for (int i = 0; i < 34; ++i)
+        for (int c = 0; c < 72; ++c) R[i * 72 + c] = T.R[i][c];
     return 0;
 }
 
@@ -431,7 +480,7 @@ extern "C" int orc_geno_misfit(const double *q0, const double *dvec, double *sig
             for (int c = 0; c < 63; ++c) s += orc::tables().R[i][c] * d[c];
             a[i] = s;
         }
-        sigma5[v] = orc::geno_misfit(q0, d, a, v);
+        sigma5[v] = orc::geno_misfit(q0, d, a, v, 0);
     }
     return 0;
 }
@@ -440,7 +489,15 @@ extern "C" int orc_recon5_cell(const double *q0, const double *dvec, double hx,
                                double hy, double hz, int nonlinear,
                                double *out480, double *chi5) {
     if (!orc::tables().ok) return -1;
-    orc::recon5_cell(q0, dvec, hx, hy, hz, nonlinear, out480, chi5);
+    orc::recon5_cell(q0, dvec, hx, hy, hz, nonlinear, out480, chi5, 0);
+    return 0;
+}
+
+extern "C" int orc_recon5b_cell(const double *q0, const double *dvec, double hx,
+                                double hy, double hz, int nonlinear,
+                                double *out480, double *chi5) {
+    if (!orc::tables(1).ok) return -1;
+    orc::recon5_cell(q0, dvec, hx, hy, hz, nonlinear, out480, chi5, 1);
     return 0;
 }
 

@@ -141,20 +141,47 @@ def _eval(terms, grid: Grid):
     return avg, grad
 
 
-def _conserved(grid, rho, u, v, w, p, gamma):
-    """Conserved separable fields from separable primitive fields."""
+def _lines(terms, grid: Grid):
+    """Line-averaged derivatives of a separable field, [12][nz][ny][nx]:
+    entry 4a + k is (f(x_a + h_a/2) - f(x_a - h_a/2))/h_a along the line
+    parallel to axis a through the cell at the tangential position of face
+    Gauss point k (offsets +-h/(2 sqrt 3) from the cell centre on axes
+    (a+1) % 3, bit 0 of k, and (a+2) % 3, bit 1)."""
+    nx, ny, nz = grid.n
+    gq = 0.5 / np.sqrt(3.0)
+    out = np.zeros((12, nz, ny, nx))
+    for c, fx, fy, fz in terms:
+        f = (fx, fy, fz)
+        for a in range(3):
+            for k in range(4):
+                parts = [None, None, None]
+                parts[a] = _dif1(f[a], grid, a)
+                for ax, bit in (((a + 1) % 3, k & 1), ((a + 2) % 3, k & 2)):
+                    xf = grid.faces(ax)
+                    mid = 0.5 * (xf[:-1] + xf[1:])
+                    parts[ax] = f[ax](mid + (gq if bit else -gq) * grid.widths(ax))
+                out[4 * a + k] += c * np.einsum("k,j,i->kji", parts[2], parts[1], parts[0])
+    return out
+
+
+def _conserved(grid, rho, u, v, w, p, gamma, lines=False):
+    """Conserved separable fields from separable primitive fields; with
+    lines=True also their line-averaged derivatives [5][12][...]."""
     mx, my, mz = _mul(rho, u), _mul(rho, v), _mul(rho, w)
     kin = _scale(_mul(rho, _mul(u, u) + _mul(v, v) + _mul(w, w)), 0.5)
     en = _scale(p, 1.0 / (gamma - 1.0)) + kin
     Q = np.zeros((5,) + tuple(reversed(grid.n)))
     G = np.zeros((5, 3) + tuple(reversed(grid.n)))
+    L = np.zeros((5, 12) + tuple(reversed(grid.n))) if lines else None
     for q, terms in enumerate((rho, mx, my, mz, en)):
         Q[q], G[q] = _eval(terms, grid)
-    return Q, G
+        if lines:
+            L[q] = _lines(terms, grid)
+    return (Q, G, L) if lines else (Q, G)
 
 
 def taylor_green(n=16, *, Ma=0.1, gamma=1.4, rho0=1.0, U0=1.0, L=1.0,
-                 rho_form="uniform", edges=None):
+                 rho_form="uniform", edges=None, lines=False):
     """Subsonic Taylor-Green vortex (Sec. 4.1) on [0, 2 pi L]^3.
 
     rho_form = "uniform": rho = rho0, p = p0 + rho0 U0^2/16 (...)(...);
@@ -181,6 +208,9 @@ def taylor_green(n=16, *, Ma=0.1, gamma=1.4, rho0=1.0, U0=1.0, L=1.0,
         p = _scale(rel, p0)
     else:
         raise ValueError(rho_form)
+    if lines:
+        Q, G, Ls = _conserved(grid, rho, u, v, w, p, gamma, lines=True)
+        return Q, G, grid, Ls
     Q, G = _conserved(grid, rho, u, v, w, p, gamma)
     return Q, G, grid
 
@@ -201,7 +231,7 @@ def taylor_green_supersonic(n=16, *, Ma=2.0, gamma=1.4, rho0=1.0, p0=1.0, L=1.0)
 
 
 def advection(n=16, *, amp=0.2, gamma=1.4, vel=(1.0, 1.0, 1.0), p=1.0,
-              dims=3, t=0.0, edges=None):
+              dims=3, t=0.0, edges=None, lines=False):
     """rho = 1 + amp sin(x + y + z - (U + V + W) t) (dims = 3) or
     rho = 1 + amp sin(x + y - (U + V) t) on an n x n x 1 grid (dims = 2,
     W = 0, the z extent one cell of size 2 pi/n), uniform velocity and
@@ -223,6 +253,10 @@ def advection(n=16, *, amp=0.2, gamma=1.4, vel=(1.0, 1.0, 1.0), p=1.0,
         sxyz = [(1.0, s, np.cos, np.cos), (1.0, c, np.sin, np.cos),
                 (1.0, c, np.cos, np.sin), (-1.0, s, np.sin, np.sin)]
     rho = _const(1.0) + _scale(sxyz, amp)
+    if lines:
+        Q, G, Ls = _conserved(grid, rho, _const(vel[0]), _const(vel[1]), _const(vel[2]),
+                              _const(p), gamma, lines=True)
+        return Q, G, grid, Ls
     Q, G = _conserved(grid, rho, _const(vel[0]), _const(vel[1]), _const(vel[2]),
                       _const(p), gamma)
     return Q, G, grid

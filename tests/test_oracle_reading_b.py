@@ -1,0 +1,167 @@
+"""Pins of the oracle's reading B of the CGKS-5th data (row N2; Sec. 3.1,
+3.2: S^0 = {Q_0, (d_l Q)_{0,G}}, reading R17): the target cell's own data
+are its 12 line-averaged derivatives (along each axis, between the face
+Gauss points with the same tangential position) instead of its averaged
+gradient.
+
+* The 34 x 72 least-squares matrix against an independent null-space
+  solve of the same weighted constrained least squares.
+* Exact reproduction of quartics (linear, and nonlinear with chi = 1).
+* The scheme with the lines as state: uniform flow bit for bit,
+  conservation to round-off, fifth order on smooth advection.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2508_19911_gb300 import workloads as wl
+from test_oracle_recon import (BASIS5, EDGE, FACE, _mean_mono, cell_avg, expected_face_states,
+                               random_poly)
+
+G2 = 0.5 / math.sqrt(3.0)
+
+
+def _mono_at(x, e):
+    return (x[0] ** e[0] * x[1] ** e[1] * x[2] ** e[2] /
+            (math.factorial(e[0]) * math.factorial(e[1]) * math.factorial(e[2])))
+
+
+def _line_points(a, k):
+    """End points (normalised coordinates) of line k along axis a."""
+    x1, x2 = [0.0] * 3, [0.0] * 3
+    x1[a], x2[a] = -0.5, 0.5
+    for ax, bit in (((a + 1) % 3, k & 1), ((a + 2) % 3, k & 2)):
+        x1[ax] = x2[ax] = G2 if bit else -G2
+    return x1, x2
+
+
+def _rows_b():
+    def dmean(o, e, j):
+        e2 = list(e)
+        e2[j] -= 1
+        return _mean_mono(o, e2)
+    C = np.array([[_mean_mono(o, e) - _mean_mono((0, 0, 0), e) for e in BASIS5]
+                  for o in FACE + EDGE])
+    rows, w = [], []
+    for o in FACE:
+        for j in range(3):
+            rows.append([dmean(o, e, j) for e in BASIS5])
+            w.append(1.0)
+    for o in EDGE:
+        a, b = [j for j in range(3) if o[j]]
+        ez = [j for j in range(3) if not o[j]][0]
+        rows.append([(o[a] * dmean(o, e, a) - o[b] * dmean(o, e, b)) / math.sqrt(2)
+                     for e in BASIS5])
+        rows.append([dmean(o, e, ez) for e in BASIS5])
+        w += [0.1, 0.1]
+    for a in range(3):
+        for k in range(4):
+            x1, x2 = _line_points(a, k)
+            rows.append([_mono_at(x2, e) - _mono_at(x1, e) for e in BASIS5])
+            w.append(1.0)
+    return C, np.array(rows), np.array(w)
+
+
+def test_reading_b_matrix_is_the_weighted_constrained_least_squares_solution(orc):
+    """For every data column: the quartic that meets the 18 neighbour
+    averages exactly and the 54 weighted derivative rows (face gradients,
+    edge tangential derivatives at weight 0.1, the 12 own lines) in the
+    least-squares sense, solved here on the null space of the constraints
+    (the oracle solves the KKT system)."""
+    C, B, w = _rows_b()
+    WB = w[:, None] * B
+    _, s, vt = np.linalg.svd(C)
+    Z = vt[np.sum(s > 1e-12):].T
+    R = np.zeros((34, 72))
+    for col in range(72):
+        dC = np.zeros(18)
+        dB = np.zeros(54)
+        if col < 18:
+            dC[col] = 1.0
+        else:
+            dB[col - 18] = 1.0
+        ap = np.linalg.lstsq(C, dC, rcond=None)[0]
+        y = np.linalg.lstsq(WB @ Z, w * dB - WB @ ap, rcond=None)[0]
+        R[:, col] = ap + Z @ y
+    got = orc.recon5b_matrix()
+    assert np.abs(got - R).max() <= 1e-10 * np.abs(R).max(), np.abs(got - R).max()
+
+
+def _data_vector_b(P, h):
+    """The 72-entry reading-B data vector of the target cell for a field P."""
+    q0 = cell_avg(P, (0, 0, 0), h)
+    d = np.zeros(72)
+    for m, o in enumerate(FACE):
+        d[m] = cell_avg(P, o, h) - q0
+        for j in range(3):
+            d[18 + 3 * m + j] = h[j] * cell_avg(P.d(j), o, h)
+    for n, o in enumerate(EDGE):
+        d[6 + n] = cell_avg(P, o, h) - q0
+        ax = [j for j in range(3) if o[j] != 0]
+        ez = [j for j in range(3) if o[j] == 0][0]
+        da = h[ax[0]] * cell_avg(P.d(ax[0]), o, h)
+        db = h[ax[1]] * cell_avg(P.d(ax[1]), o, h)
+        d[36 + 2 * n] = (o[ax[0]] * da - o[ax[1]] * db) / math.sqrt(2)
+        d[36 + 2 * n + 1] = h[ez] * cell_avg(P.d(ez), o, h)
+    for a in range(3):
+        for k in range(4):
+            x1, x2 = _line_points(a, k)
+            p1 = [x1[j] * h[j] for j in range(3)]
+            p2 = [x2[j] * h[j] for j in range(3)]
+            d[60 + 4 * a + k] = P(*p2) - P(*p1)  # h_a times the line's derivative
+    return q0, d
+
+
+@pytest.mark.parametrize("nonlinear", [0, 1])
+def test_reading_b_reproduces_quartics(orc, nonlinear):
+    rng = np.random.default_rng(41 + nonlinear)
+    h = (0.3, 0.5, 0.7)
+    polys = [random_poly(rng, 4) for _ in range(5)]
+    q0, d = zip(*[_data_vector_b(P, h) for P in polys])
+    out, chi = orc.recon5b_cell(np.array(q0), np.concatenate(d), h, nonlinear=nonlinear)
+    np.testing.assert_allclose(chi, 1.0, rtol=0, atol=1e-12)
+    exp = expected_face_states(polys, h)
+    np.testing.assert_allclose(out, exp, rtol=0, atol=1e-11 * np.abs(exp).max())
+
+
+def test_reading_b_uniform_flow_is_bitwise_steady(orc):
+    nx, ny, nz = 5, 6, 4
+    rho, U, V, W, p = 1.3, 0.2, -0.3, 0.1, 0.9
+    Q = np.zeros((5, nz, ny, nx))
+    Q[0], Q[1], Q[2], Q[3] = rho, rho * U, rho * V, rho * W
+    Q[4] = p / 0.4 + 0.5 * rho * (U * U + V * V + W * W)
+    L = np.zeros((5, 12, nz, ny, nx))
+    Q0 = Q.copy()
+    P = orc.params(n=(nx, ny, nz), L=(1.0, 1.3, 0.7), mu0=1e-3)
+    orc.run_b(P, Q, L, nsteps=3)
+    np.testing.assert_array_equal(Q, Q0)
+    assert np.all(L == 0.0)
+
+
+def test_reading_b_conserves_mass_momentum_and_energy(orc):
+    Q, G, grid, L = wl.taylor_green((6, 5, 4), lines=True)
+    Q, _ = wl.perturb(Q, G, amp=1e-2, seed=5)
+    P = orc.params(n=grid.n, L=grid.L)
+    s0 = Q.reshape(5, -1).sum(axis=1)
+    orc.run_b(P, Q, L, nsteps=4)
+    s1 = Q.reshape(5, -1).sum(axis=1)
+    scale = np.abs(Q).reshape(5, -1).max(axis=1) * Q[0].size
+    assert np.all(np.abs(s1 - s0) <= 1e-14 * scale), (s1 - s0) / scale
+
+
+def test_reading_b_is_fifth_order_on_smooth_advection(orc):
+    """tau = 0, 2D smooth advection to t = 2 at CFL 0.2, linear: the
+    cell-average density error falls at the design order between 16^2 and
+    32^2 (the lines are evolved from the point values at the face Gauss
+    points)."""
+    errs = []
+    for n in (16, 32):
+        Q, G, grid, L = wl.advection(n, dims=2, lines=True)
+        P = orc.params(n=grid.n, L=grid.L, scheme=1, nonlinear=0, inviscid=1, eps_tau=0.0,
+                       C_tau=0.0, cfl=0.2)
+        t, _ = orc.run_b(P, Q, L, nsteps=100000, t_stop=2.0)
+        Qe, _, _ = wl.advection(n, dims=2, t=t)
+        errs.append(np.abs(Q[0] - Qe[0]).mean())
+    order = math.log2(errs[0] / errs[1])
+    assert 4.5 < order < 5.6, (errs, order)
