@@ -118,11 +118,16 @@ def parse():
                          "symmetry planes on a stretched mesh (cells 0.7-1.3 times the mean), "
                          "FP64 and mixed, against the periodic uniform kernels on the same cell "
                          "count (default 256^3)")
+    ap.add_argument("--lines", action="store_true",
+                    help="CGKS-5th FP64 with the line-averaged derivatives as the cell's own data "
+                         "(gks_step_lines) against the averaged-gradient form on the same "
+                         "Taylor-Green grid (default 128^3)")
     ap.add_argument("--history", default=None,
                     help="--c2/--c3: write the sampled histories to this JSON file")
     args = ap.parse_args()
     if args.n is None:
-        args.n = (64 if args.c2 else 256 if (args.c3 or args.general) else 512 if args.c5
+        args.n = (64 if args.c2 else 128 if args.lines else 256 if (args.c3 or args.general)
+                  else 512 if args.c5
                   else 128 if args.workload == "tgv" else 512)
     return args
 
@@ -1004,8 +1009,61 @@ def run_general(args):
     }
 
 
+def run_lines(args):
+    """Row N2 measured: CGKS-5th nonlinear FP64 with the 12 line-averaged
+    derivatives per variable as the cell's own data (a dense 34 x 72
+    reconstruction, per-Gauss-point interface values, every line advanced)
+    against the averaged-gradient form, Taylor-Green n^3. Cell-stage
+    updates per second, CUDA events on the solver's stream."""
+    import torch
+
+    from paper_2508_19911_gb300 import gks
+    from paper_2508_19911_gb300 import workloads as wl
+
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    n = args.n
+    Q, G, grid, L = wl.taylor_green(n, lines=True)
+    out = {}
+    for form in ("lines", "gradients"):
+        s = gks.Solver(gks.Config(n=grid.n, L=grid.L, scheme="cgks5", precision="fp64",
+                                  mu=1.0 / 1600), stream)
+        Qd = torch.tensor(Q, device=dev)
+        Xd = torch.tensor(L if form == "lines" else G, device=dev)
+        step = s.step_lines if form == "lines" else s.step
+        for _ in range(args.warmup):
+            step(Qd, Xd, nsteps=1, sync=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            step(Qd, Xd, nsteps=args.steps, sync=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if s.status():
+            raise RuntimeError(f"non-physical state ({form})")
+        out[form] = {"value": n ** 3 * 2 * args.steps / (ms / 1e3), "unit": "cell-stage/s",
+                     "ms_per_step": ms / args.steps, "clocks": clk.summary()}
+        s.close()
+        del Qd, Xd
+        torch.cuda.empty_cache()
+    out["lines_over_gradients"] = out["lines"]["value"] / out["gradients"]["value"]
+    return {
+        "metric": METRIC, "value": out["lines"]["value"], "unit": "cell-stage/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["lines"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Taylor-Green cell averages and line-averaged derivatives)",
+        "config": {"workload": f"taylor_green_{n}^3_cgks5_lines", "cells": n ** 3},
+        "paths": out,
+    }
+
+
 def main():
     args = parse()
+    if args.lines:
+        print(json.dumps(run_lines(args)))
+        return
     if args.general:
         print(json.dumps(run_general(args)))
         return

@@ -211,6 +211,36 @@ int gks_step(gks_ctx *ctx, double *Q, double *gradQ, int nsteps,
 int gks_step_host(gks_ctx *ctx, double *Q, double *gradQ, int nsteps, double t_stop,
                   double *t);
 
+/* CGKS-5th with the target cell's own data as its 12 line-averaged
+ * derivatives (the set S^0 of Sec. 3.1-3.2: per variable and axis a, the
+ * derivative along a averaged over the line through the cell between the
+ * face Gauss points k of its two faces normal to a) instead of its averaged
+ * gradient. L: device double[5][12][n], entry (v, 4a + k, cell), line k
+ * through tangential position (+-, +-) of axis (a+1)%3 (bit 0 of k) and
+ * (a+2)%3 (bit 1); the averaged gradient along a is the mean of its four
+ * lines. FP64 CGKS-5th contexts on periodic grids only (GKS_ERR_STATE
+ * otherwise); the first call allocates 390 doubles per cell (face records
+ * [3][90][n], two line buffers) kept until gks_destroy.
+ *
+ * gks_reconstruct_lines: the face states of every cell, layout of
+ * gks_reconstruct (FP64), into face_states (device, or NULL: the context's
+ * buffer, GKS_ERR_STATE when that holds a slab only).
+ *
+ * gks_step_lines: nsteps two-stage steps as gks_step; Q as there, each line
+ * advanced from the time-dependent interface values at its two end points
+ * (Sec. 3.4 point by point): stage 1 L* = (Q^l(dt/2) at the high face -
+ * Q^r(dt/2) at the low face)/h_a, stage 2 from the t = 0 values plus dt
+ * times the stage-2 time derivatives. Asynchronous unless dt_host_last is
+ * non-NULL (then as gks_step). GKS_ERR_STATE when the context's face-state
+ * buffer holds a slab only.
+ *
+ * gks_lines_gradients: G[v][a][cell] (device double[15][n]) = the mean of
+ * the four lines of (v, a), e.g. for gks_diagnostics. Asynchronous. */
+int gks_reconstruct_lines(gks_ctx *ctx, const double *Q, const double *L, double *face_states);
+int gks_step_lines(gks_ctx *ctx, double *Q, double *L, int nsteps, double t_stop, double *t_dev,
+                   double *dt_host_last);
+int gks_lines_gradients(gks_ctx *ctx, const double *L, double *G);
+
 /* a5 -- diagnostics (Sec. 4.1/4.2), synchronising; out (host, 12 doubles):
  *  [0] E_k  = (1/|Omega|) sum rho |U|^2/2 h^3 (divide by rho0 U0^2 for the
  *            paper's normalisation)

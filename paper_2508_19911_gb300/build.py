@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["flux.cu", "recon.cu", "recon_fp64.cu", "update.cu", "capi.cu", "noalloc.cu", "mlp.cu", "ensemble.cu", "peak.cu",
-              "ensemble_step.cu"]
+              "ensemble_step.cu", "recon_lines.cu"]
 CPP_SOURCES = ["tables.cpp"]
 HEADERS = ["basis.h", "common.cuh", "ff.cuh", "recon_common.cuh", "flux_device.cuh",
            "recon_fp64_device.cuh", "recon_mixed_device.cuh", "update_device.cuh"]

@@ -253,4 +253,18 @@ struct ReconTables {
 // Builds the tables (host). Returns 0 on success.
 int build_recon_tables(ReconTables *t);
 
+// Reading B of the target cell's data (its 12 line-averaged derivatives
+// instead of its averaged gradient; data vector of 72 entries: 60 as above,
+// then the lines 60 + 4a + k): the dense least-squares matrix, the weighted
+// derivative rows for GENO's misfit, the monomial means and the monomials'
+// values and derivatives at the 24 face Gauss points.
+struct ReconTablesLines {
+    double R[kNumBasis][72];
+    double WB[54][kNumBasis];
+    double w[54];
+    double mean[kNumBasis];
+    double mpt[24][4][kNumBasis];   // [point][value, d/dx, d/dy, d/dz][monomial]
+};
+int build_recon_tables_lines(ReconTablesLines *t);
+
 }  // namespace gks

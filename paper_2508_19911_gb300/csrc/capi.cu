@@ -36,6 +36,7 @@ struct gks_ctx {
     int diag_blocks;
     double *hQ, *hG, *hT;  // device state of gks_step_host (allocated on its first call)
     double *hsz;           // stretched mesh: the nx + ny + nz cell sizes (device)
+    double *lrec, *Ls, *LS1;  // gks_step_lines: records [3][90][n], lines [60][n] x 2
     int timing;            // gks_kernel_timing: record events around the step's launches
     cudaEvent_t t_open;    // event before the launch being timed
     std::vector<struct KernelRec> *t_recs;  // (kind, start, end) of the timed launches
@@ -155,6 +156,9 @@ void gks_destroy(gks_ctx *c) {
     cudaFree(c->hG);
     cudaFree(c->hT);
     cudaFree(c->hsz);
+    cudaFree(c->lrec);
+    cudaFree(c->Ls);
+    cudaFree(c->LS1);
     time_clear(c);
     delete c->t_recs;
     if (prev >= 0) cudaSetDevice(prev);
@@ -501,6 +505,75 @@ int gks_step_host(gks_ctx *c, double *Q, double *G, int nsteps, double t_stop, d
     }
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return GKS_ERR_CUDA;
     return st ? GKS_ERR_NONPHYSICAL : GKS_OK;
+}
+
+namespace {
+// the line-averaged-derivative form needs the FP64 CGKS-5th on a periodic
+// grid; its buffers and tables are set up on first use
+int lines_ready(gks_ctx *c) {
+    if (c->P.scheme != GKS_SCHEME_CGKS5 || c->mixed || c->g.general) return GKS_ERR_STATE;
+    if (c->lrec) return GKS_OK;
+    const int t = upload_recon_tables_lines();
+    if (t) return t == -1 ? GKS_ERR_ARG : GKS_ERR_CUDA;
+    int rc;
+    const size_t n = (size_t)c->g.n;
+    if ((rc = dalloc(&c->Ls, 60 * n)) || (rc = dalloc(&c->LS1, 60 * n)) ||
+        (rc = dalloc(&c->lrec, 270 * n))) {
+        cudaFree(c->Ls);
+        cudaFree(c->LS1);
+        c->Ls = c->LS1 = nullptr;
+        return rc;
+    }
+    return GKS_OK;
+}
+}  // namespace
+
+int gks_reconstruct_lines(gks_ctx *c, const double *Q, const double *L, double *face_states) {
+    if (!c || !Q || !L) return GKS_ERR_ARG;
+    int rc;
+    if ((rc = lines_ready(c))) return rc;
+    if (!face_states && c->slab_planes) return GKS_ERR_STATE;
+    return launch_ok(launch_recon5_lines(c->g, c->P, Q, L, face_states ? face_states : (double *)c->fs,
+                                         c->stream));
+}
+
+int gks_step_lines(gks_ctx *c, double *Q, double *L, int nsteps, double t_stop, double *t_dev,
+                   double *dt_host_last) {
+    if (!c || !Q || !L || nsteps < 0) return GKS_ERR_ARG;
+    int rc;
+    if ((rc = lines_ready(c))) return rc;
+    if (c->slab_planes) return GKS_ERR_STATE;  // the face states of the whole grid at once
+    double *dt = dt_slot(c), *fs = (double *)c->fs;
+    for (int s = 0; s < nsteps; ++s) {
+        if (launch_dt(c->g, c->P, Q, red_slot(c), dt, t_dev, t_stop, c->stream) ||
+            launch_recon5_lines(c->g, c->P, Q, L, fs, c->stream) ||
+            launch_flux_faces_lines(c->g, c->P, fs, dt, c->lrec, c->status, c->stream) ||
+            launch_update_lines(c->g, c->P, 1, c->lrec, dt, Q, L, c->Qs, c->Ls, c->Acc, c->LS1,
+                                c->status, c->stream) ||
+            launch_recon5_lines(c->g, c->P, c->Qs, c->Ls, fs, c->stream) ||
+            launch_flux_faces_lines(c->g, c->P, fs, dt, c->lrec, c->status, c->stream) ||
+            launch_update_lines(c->g, c->P, 2, c->lrec, dt, Q, L, c->Qs, c->Ls, c->Acc, c->LS1,
+                                c->status, c->stream))
+            return GKS_ERR_CUDA;
+    }
+    if (dt_host_last) {
+        int st = 0;
+        if (cudaMemcpyAsync(dt_host_last, dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess) {
+            cudaStreamSynchronize(c->stream);
+            return GKS_ERR_CUDA;
+        }
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return GKS_ERR_CUDA;
+        if (st) return GKS_ERR_NONPHYSICAL;
+    }
+    return GKS_OK;
+}
+
+int gks_lines_gradients(gks_ctx *c, const double *L, double *G) {
+    if (!c || !L || !G) return GKS_ERR_ARG;
+    return launch_ok(launch_lines_to_grad(c->g.n, L, G, c->stream));
 }
 
 int gks_diagnostics(gks_ctx *c, const double *Q, const double *G, double *out) {

@@ -202,6 +202,18 @@ int launch_dt(const GridDesc &g, const PhysParams &P, const double *Q, double *r
 int launch_update(const GridDesc &g, const PhysParams &P, int stage, const double *frec,
                   const double *dt_dev, double *Q, double *G, double *Qs, double *Gs,
                   double *Acc, double *S1, int *status, cudaStream_t s);
+// CGKS-5th with the line-averaged derivatives as the target cell's data
+// (recon_lines.cu; FP64, periodic): L [5][12][n] (line 4a + k of variable
+// v along axis a), face records [3][90][n]
+int upload_recon_tables_lines(void);
+int launch_recon5_lines(const GridDesc &g, const PhysParams &P, const double *Q, const double *L,
+                        double *fs, cudaStream_t s);
+int launch_flux_faces_lines(const GridDesc &g, const PhysParams &P, const double *fs,
+                            const double *dt_dev, double *frec, int *status, cudaStream_t s);
+int launch_update_lines(const GridDesc &g, const PhysParams &P, int stage, const double *frec,
+                        const double *dt_dev, double *Q, double *L, double *Qs, double *Ls,
+                        double *Acc, double *S1, int *status, cudaStream_t s);
+int launch_lines_to_grad(long long n, const double *L, double *G, cudaStream_t s);
 // diagnostics: nblocks (1..kDiagMaxBlocks) blocks write kDiagSlots partial
 // results each to partials, one block reduces them into out_dev
 constexpr int kDiagSlots = 12;

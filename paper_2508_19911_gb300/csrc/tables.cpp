@@ -272,4 +272,146 @@ int build_recon_tables(ReconTables *t) {
     return 0;
 }
 
+// Reading B of the target cell's data (line-averaged derivatives, the
+// paper's S^0): the same constrained least squares with the 12 line rows
+// (value of x^e/e! at the line's end on the high face minus at its end on
+// the low face, tangential position of face Gauss point k) in place of the
+// 3 own-gradient rows, weight 1; solved by the same null-space method.
+int build_recon_tables_lines(ReconTablesLines *t) {
+    std::memset(t, 0, sizeof(*t));
+    constexpr int nb = kNumBasis, ne = 18, nl = 54, ncol = 72;
+    static const int zero[3] = {0, 0, 0};
+    Mat C(ne, nb);
+    for (int k = 0; k < ne; ++k) {
+        const int *o = (k < 6) ? kFaceOff[k] : kEdgeOff[k - 6];
+        for (int i = 0; i < nb; ++i) {
+            const int e[3] = {kExp[i][0], kExp[i][1], kExp[i][2]};
+            C(k, i) = cell_avg(o, e) - cell_avg(zero, e);
+        }
+    }
+    Mat B(nl, nb);
+    int r = 0;
+    for (int m = 0; m < 6; ++m)
+        for (int q = 0; q < 3; ++q, ++r)
+            for (int i = 0; i < nb; ++i) B(r, i) = cell_avg_deriv(kFaceOff[m], i, q);
+    const double rs2 = 1.0 / std::sqrt(2.0);
+    for (int n = 0; n < 12; ++n) {
+        const int *o = kEdgeOff[n];
+        const int a = edge_axis_a(n), b = edge_axis_b(n), e = edge_axis_e(n);
+        for (int i = 0; i < nb; ++i)
+            B(r, i) = rs2 * (o[a] * cell_avg_deriv(o, i, a) - o[b] * cell_avg_deriv(o, i, b));
+        ++r;
+        for (int i = 0; i < nb; ++i) B(r, i) = cell_avg_deriv(o, i, e);
+        ++r;
+    }
+    const double g = 0.5 / std::sqrt(3.0);
+    auto mono = [](const double x[3], int i) {
+        double v = 1.0;
+        for (int j = 0; j < 3; ++j) v *= std::pow(x[j], kExp[i][j]) / factorial(kExp[i][j]);
+        return v;
+    };
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 4; ++k, ++r) {
+            double x1[3], x2[3];
+            x1[a] = -0.5;
+            x2[a] = 0.5;
+            x1[(a + 1) % 3] = x2[(a + 1) % 3] = (k & 1) ? g : -g;
+            x1[(a + 2) % 3] = x2[(a + 2) % 3] = (k & 2) ? g : -g;
+            for (int i = 0; i < nb; ++i) B(r, i) = mono(x2, i) - mono(x1, i);
+        }
+    std::vector<double> wrow(nl, 1.0);
+    for (int k = 0; k < nl; ++k) wrow[k] = (k >= 18 && k < 42) ? kEdgeWeight : 1.0;
+    for (int k = 0; k < nl; ++k) {
+        t->w[k] = wrow[k];
+        for (int i = 0; i < nb; ++i) {
+            B(k, i) *= wrow[k];
+            t->WB[k][i] = B(k, i);
+        }
+    }
+    Mat Ct(nb, ne);
+    for (int k = 0; k < ne; ++k)
+        for (int i = 0; i < nb; ++i) Ct(i, k) = C(k, i);
+    Mat Qc(1, 1), Rc(1, 1);
+    householder_qr(Ct, Qc, Rc);
+    const int nz = nb - ne;
+    Mat BQ2(nl, nz), BQ1(nl, ne);
+    for (int i = 0; i < nl; ++i) {
+        for (int j = 0; j < nz; ++j) {
+            double s = 0.0;
+            for (int l = 0; l < nb; ++l) s += B(i, l) * Qc(l, ne + j);
+            BQ2(i, j) = s;
+        }
+        for (int j = 0; j < ne; ++j) {
+            double s = 0.0;
+            for (int l = 0; l < nb; ++l) s += B(i, l) * Qc(l, j);
+            BQ1(i, j) = s;
+        }
+    }
+    Mat Qm(1, 1), Rm(1, 1);
+    householder_qr(BQ2, Qm, Rm);
+    for (int i = 0; i < ne; ++i)
+        if (std::fabs(Rc(i, i)) < 1e-12) return -1;
+    for (int i = 0; i < nz; ++i)
+        if (std::fabs(Rm(i, i)) < 1e-12) return -1;
+    std::vector<double> dC(ne), dB(nl), y(ne), res(nl), z(nz), rhs(nz);
+    for (int col = 0; col < ncol; ++col) {
+        for (int k = 0; k < ne; ++k) dC[k] = (col == k) ? 1.0 : 0.0;
+        for (int k = 0; k < nl; ++k) dB[k] = (col == ne + k) ? wrow[k] : 0.0;
+        for (int i = 0; i < ne; ++i) {
+            double s = dC[i];
+            for (int j = 0; j < i; ++j) s -= Rc(j, i) * y[j];
+            y[i] = s / Rc(i, i);
+        }
+        for (int i = 0; i < nl; ++i) {
+            double s = dB[i];
+            for (int j = 0; j < ne; ++j) s -= BQ1(i, j) * y[j];
+            res[i] = s;
+        }
+        for (int j = 0; j < nz; ++j) {
+            double s = 0.0;
+            for (int i = 0; i < nl; ++i) s += Qm(i, j) * res[i];
+            rhs[j] = s;
+        }
+        for (int j = nz - 1; j >= 0; --j) {
+            double s = rhs[j];
+            for (int l = j + 1; l < nz; ++l) s -= Rm(j, l) * z[l];
+            z[j] = s / Rm(j, j);
+        }
+        for (int i = 0; i < nb; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < ne; ++j) s += Qc(i, j) * y[j];
+            for (int j = 0; j < nz; ++j) s += Qc(i, ne + j) * z[j];
+            t->R[i][col] = s;
+        }
+    }
+    auto mono_int = [](int n) { return (n % 2) ? 0.0 : std::pow(0.5, n) / (n + 1); };
+    for (int i = 0; i < nb; ++i) {
+        t->mean[i] = 1.0;
+        for (int j = 0; j < 3; ++j) t->mean[i] *= mono_int(kExp[i][j]) / factorial(kExp[i][j]);
+    }
+    // x^e/e! and its derivatives at the 24 face Gauss points (face f = 2d +
+    // side, point k), in the order of the face-state buffer
+    for (int f = 0; f < 6; ++f)
+        for (int k = 0; k < 4; ++k) {
+            const int d = f / 2, pt = 4 * f + k;
+            double x[3];
+            x[d] = (f & 1) ? 0.5 : -0.5;
+            x[(d + 1) % 3] = (k & 1) ? g : -g;
+            x[(d + 2) % 3] = (k & 2) ? g : -g;
+            for (int i = 0; i < nb; ++i) {
+                t->mpt[pt][0][i] = mono(x, i);
+                for (int q = 0; q < 3; ++q) {
+                    if (kExp[i][q] == 0) { t->mpt[pt][1 + q][i] = 0.0; continue; }
+                    double w = 1.0;
+                    for (int j = 0; j < 3; ++j) {
+                        const int e = kExp[i][j] - (j == q ? 1 : 0);
+                        w *= std::pow(x[j], e) / factorial(e);
+                    }
+                    t->mpt[pt][1 + q][i] = w;
+                }
+            }
+        }
+    return 0;
+}
+
 }  // namespace gks

@@ -98,6 +98,9 @@ SIGNATURES = {
     "gks_ensemble_set_mode": (_I, [_VP, _I]),
     "gks_ensemble_mode": (_I, [_VP]),
     "gks_barrier_timeout_check": (_I, [_D, _VP]),
+    "gks_reconstruct_lines": (_I, [_VP, _VP, _VP, _VP]),
+    "gks_step_lines": (_I, [_VP, _VP, _VP, _I, _D, _VP, ctypes.POINTER(_D)]),
+    "gks_lines_gradients": (_I, [_VP, _VP, _VP]),
 }
 
 
@@ -339,6 +342,35 @@ class Solver:
                                  float(t_stop), ctypes.byref(tt) if t is not None else None)
         _check(rc, "gks_step_host")
         return tt.value if t is not None else None
+
+    # -- the line-averaged derivatives as the cell's own data ------------------
+    def lines_shape(self):
+        nx, ny, nz = self.cfg.n
+        return (5, 12, nz, ny, nx)
+
+    def reconstruct_lines(self, Q, L, out=None):
+        """Face states (FP64, layout of reconstruct) from the averages Q and
+        the 12 line-averaged derivatives L [5][12] per cell."""
+        if out is None:
+            out = self.zeros(6, 4, 20, self.ncells)
+        _check(lib().gks_reconstruct_lines(self.ctx, _ptr(Q), _ptr(L), _ptr(out)),
+               "gks_reconstruct_lines")
+        return out
+
+    def step_lines(self, Q, L, nsteps=1, t_stop=math.inf, t=None, sync=True):
+        """Advance (Q, L) in place. Returns the last dt (sync=True) or None."""
+        last = _D(0.0)
+        rc = lib().gks_step_lines(self.ctx, _ptr(Q), _ptr(L), int(nsteps), float(t_stop), _ptr(t),
+                                  ctypes.byref(last) if sync else None)
+        _check(rc, "gks_step_lines")
+        return last.value if sync else None
+
+    def lines_gradients(self, L, out=None):
+        """Averaged gradients [5][3] per cell: the mean of each axis' lines."""
+        if out is None:
+            out = self.zeros(*self.state_shape()[1])
+        _check(lib().gks_lines_gradients(self.ctx, _ptr(L), _ptr(out)), "gks_lines_gradients")
+        return out
 
     def diagnostics(self, Q, G=None):
         out = (_D * 12)()
