@@ -1009,6 +1009,34 @@ def run_general(args):
     }
 
 
+# FP64 work per unit of the line-form kernels (ncu op counts on the
+# Taylor-Green 32^3 case of --lines; an FMA counts 2): the reconstruction
+# per cell, the flux per face Gauss point (12 per cell)
+LINES_OPS = {
+    "recon": {"name": "recon5_lines_kernel", "unit": "cell", "per_cell": 1, "fp64": 19289.0},
+    "flux": {"name": "flux_faces_lines_kernel", "unit": "Gauss point", "per_cell": 12,
+             "fp64": 3756.5},
+}
+
+
+def lines_cpu_baseline():
+    """The oracle's line form as it stands, all host cores, on a bounded
+    sample: Taylor-Green 32^3, one step."""
+    import oracle
+    from paper_2508_19911_gb300 import workloads as wl
+    cores = os.cpu_count() or 1
+    Q, _, grid, L = wl.taylor_green(8, lines=True)
+    oracle.run_b(oracle.params(n=grid.n, L=grid.L, threads=cores), Q, L, nsteps=1)  # tables
+    n = 32
+    Q, _, grid, L = wl.taylor_green(n, lines=True)
+    P = oracle.params(n=grid.n, L=grid.L, mu0=1.0 / 1600, threads=cores)
+    t0 = time.perf_counter()
+    oracle.run_b(P, Q, L, nsteps=1)
+    el = time.perf_counter() - t0
+    return {"value": n ** 3 * 2 / el, "unit": "cell-stage/s", "cores": cores, "kind": "oracle",
+            "sample": f"taylor_green {n}^3 cgks5 lines FP64 nonlinear, 1 step ({el:.1f} s)"}
+
+
 def run_lines(args):
     """Row N2 measured: CGKS-5th nonlinear FP64 with the 12 line-averaged
     derivatives per variable as the cell's own data (a dense 34 x 72
@@ -1041,20 +1069,45 @@ def run_lines(args):
             e1.record(stream)
             torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
+        # the per-kernel split from a second timed pass with launch events
+        s.kernel_timing(True)
+        step(Qd, Xd, nsteps=args.steps, sync=False)
+        torch.cuda.synchronize()
+        s.kernel_timing(False)
+        kt = s.kernel_times()
         if s.status():
             raise RuntimeError(f"non-physical state ({form})")
         out[form] = {"value": n ** 3 * 2 * args.steps / (ms / 1e3), "unit": "cell-stage/s",
-                     "ms_per_step": ms / args.steps, "clocks": clk.summary()}
+                     "ms_per_step": ms / args.steps, "clocks": clk.summary(),
+                     "kernel_ms_per_launch": {k: (v[0] / v[1] if v[1] else None)
+                                              for k, v in kt.items()}}
+        if form == "lines":
+            p64, _ = alu_peaks(torch, stream)
+            roof = {}
+            for kind, ops in LINES_OPS.items():
+                ms_l = kt[kind][0] / max(kt[kind][1], 1)
+                units = n ** 3 * ops["per_cell"]
+                r = {"kernel": ops["name"], "unit": ops["unit"], "ms_per_launch": ms_l,
+                     "fp64_flop_per_unit": ops["fp64"]}
+                if ops["fp64"]:
+                    a = ops["fp64"] * units / (ms_l / 1e3) / 1e12
+                    r.update({"bound": "alu", "achieved": a, "peak": p64,
+                              "unit_rate": "TFLOP/s (FP64)", "frac": a / p64,
+                              "peak_note": "measured FP64 FMA rate (gks_fma_rate)"})
+                roof[kind] = r
+            out[form]["roofline"] = roof
         s.close()
         del Qd, Xd
         torch.cuda.empty_cache()
     out["lines_over_gradients"] = out["lines"]["value"] / out["gradients"]["value"]
+    cpu = None if args.no_cpu else lines_cpu_baseline()
     return {
         "metric": METRIC, "value": out["lines"]["value"], "unit": "cell-stage/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["lines"]["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (Taylor-Green cell averages and line-averaged derivatives)",
         "config": {"workload": f"taylor_green_{n}^3_cgks5_lines", "cells": n ** 3},
+        "roofline": out["lines"]["roofline"], "cpu_baseline": cpu,
         "paths": out,
     }
 

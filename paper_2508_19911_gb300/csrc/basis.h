@@ -238,6 +238,83 @@ constexpr bool sym_table_ok() {
 }
 static_assert(sym_table_ok(), "reflection table of the data vector is incomplete");
 
+// The data vector of the line form (reading B of the own data: the
+// target cell's 12 line-averaged derivatives replace its averaged
+// gradient): columns 0..59 as above, then line k of axis a at
+// kColLines + 4a + k (k's bit 0: the side of axis (a+1)%3, bit 1: of
+// (a+2)%3). A reflection s maps a line of axis a to the line with the
+// tangential bits of the reflected axes flipped, times s_a (its end points
+// swap when axis a is reflected).
+constexpr int kNumDataL = 72, kColLines = 60;
+GKS_HD constexpr int data_reflect_l(int k, int s) {
+    if (k < kColLines) return data_reflect(k, s);
+    const int a = (k - kColLines) / 4, kk = (k - kColLines) % 4;
+    const int flip = ((s >> ((a + 1) % 3)) & 1) | (((s >> ((a + 2) % 3)) & 1) << 1);
+    return kColLines + 4 * a + (kk ^ flip);
+}
+GKS_HD constexpr int data_reflect_sign_l(int k, int s) {
+    return k < kColLines ? data_reflect_sign(k, s) : refl(s, (k - kColLines) / 4);
+}
+struct SymTableL {
+    int cls[kNumDataL];
+    int nm[kNumDataL];
+    int mem[kNumDataL][8];
+    int sgn[kNumDataL][8];
+    int orbit[kNumDataL];
+    int count;  // combinations found (kNumDataL when the basis is complete)
+};
+constexpr SymTableL make_sym_table_l() {
+    SymTableL t{};
+    bool seen[kNumDataL] = {};
+    int r = 0;
+    for (int k = 0; k < kNumDataL; ++k) {
+        if (seen[k]) continue;
+        const int first = r;
+        for (int s = 0; s < 8; ++s) seen[data_reflect_l(k, s)] = true;
+        for (int c = 0; c < 8; ++c) {
+            int coef[kNumDataL] = {};
+            for (int s = 0; s < 8; ++s) {
+                int chi = 1;
+                for (int j = 0; j < 3; ++j)
+                    if ((c >> j) & 1) chi *= refl(s, j);
+                coef[data_reflect_l(k, s)] += chi * data_reflect_sign_l(k, s);
+            }
+            int n = 0;
+            for (int m = 0; m < kNumDataL; ++m)
+                if (coef[m] != 0) {
+                    t.mem[r][n] = m;
+                    t.sgn[r][n] = coef[m] > 0 ? 1 : -1;
+                    ++n;
+                }
+            if (n == 0) continue;
+            if (r >= kNumDataL) return t;  // incomplete: caught below
+            t.cls[r] = c;
+            t.nm[r] = n;
+            t.orbit[r] = first;
+            ++r;
+        }
+    }
+    t.count = r;
+    return t;
+}
+constexpr SymTableL kSymL = make_sym_table_l();
+constexpr bool sym_table_l_ok() {
+    if (kSymL.count != kNumDataL) return false;
+    int covered[kNumDataL] = {};
+    for (int r = 0; r < kNumDataL; ++r) {
+        if (kSymL.nm[r] < 1 || kSymL.nm[r] > 8) return false;
+        for (int q = 0; q < kSymL.nm[r]; ++q) covered[kSymL.mem[r][q]] += 1;
+        const int f = kSymL.orbit[r];
+        if (kSymL.nm[r] != kSymL.nm[f]) return false;
+        for (int q = 0; q < kSymL.nm[r]; ++q)
+            if (kSymL.mem[r][q] != kSymL.mem[f][q]) return false;
+    }
+    for (int m = 0; m < kNumDataL; ++m)
+        if (covered[m] < 1) return false;
+    return true;
+}
+static_assert(sym_table_l_ok(), "reflection table of the line-form data vector is incomplete");
+
 struct ReconTables {
     double R[kNumBasis][kNumData];      // coefficients a = R d
     double Rs[kNumData][kMaxClass];     // a_{class(r), j} += Rs[r][j] d^s_r
@@ -256,14 +333,17 @@ int build_recon_tables(ReconTables *t);
 // Reading B of the target cell's data (its 12 line-averaged derivatives
 // instead of its averaged gradient; data vector of 72 entries: 60 as above,
 // then the lines 60 + 4a + k): the dense least-squares matrix, the weighted
-// derivative rows for GENO's misfit, the monomial means and the monomials'
-// values and derivatives at the 24 face Gauss points.
+// derivative rows for GENO's misfit, the monomial means and the magnitudes
+// of the monomials and their derivatives at the face Gauss points.
 struct ReconTablesLines {
     double R[kNumBasis][72];
     double WB[54][kNumBasis];
     double w[54];
     double mean[kNumBasis];
-    double mpt[24][4][kNumBasis];   // [point][value, d/dx, d/dy, d/dz][monomial]
+    double mval[3][kNumBasis];      // as ReconTables::mval
+    double mder[3][3][kNumBasis];   // as ReconTables::mder
+    double Rs[kNumDataL][kMaxClass];  // R in the symmetrised basis (kSymL)
+    double Bs[kNumDataL][kMaxClass];  // weighted derivative rows, same basis
 };
 int build_recon_tables_lines(ReconTablesLines *t);
 

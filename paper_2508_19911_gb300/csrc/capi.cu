@@ -545,16 +545,24 @@ int gks_step_lines(gks_ctx *c, double *Q, double *L, int nsteps, double t_stop, 
     if (c->slab_planes) return GKS_ERR_STATE;  // the face states of the whole grid at once
     double *dt = dt_slot(c), *fs = (double *)c->fs;
     for (int s = 0; s < nsteps; ++s) {
-        if (launch_dt(c->g, c->P, Q, red_slot(c), dt, t_dev, t_stop, c->stream) ||
-            launch_recon5_lines(c->g, c->P, Q, L, fs, c->stream) ||
-            launch_flux_faces_lines(c->g, c->P, fs, dt, c->lrec, c->status, c->stream) ||
-            launch_update_lines(c->g, c->P, 1, c->lrec, dt, Q, L, c->Qs, c->Ls, c->Acc, c->LS1,
-                                c->status, c->stream) ||
-            launch_recon5_lines(c->g, c->P, c->Qs, c->Ls, fs, c->stream) ||
-            launch_flux_faces_lines(c->g, c->P, fs, dt, c->lrec, c->status, c->stream) ||
-            launch_update_lines(c->g, c->P, 2, c->lrec, dt, Q, L, c->Qs, c->Ls, c->Acc, c->LS1,
-                                c->status, c->stream))
-            return GKS_ERR_CUDA;
+        time_open(c);
+        if (launch_dt(c->g, c->P, Q, red_slot(c), dt, t_dev, t_stop, c->stream)) return GKS_ERR_CUDA;
+        time_close(c, kTimeDt);
+        for (int stage = 1; stage <= 2; ++stage) {
+            const double *Qx = stage == 1 ? Q : c->Qs, *Lx = stage == 1 ? L : c->Ls;
+            time_open(c);
+            if (launch_recon5_lines(c->g, c->P, Qx, Lx, fs, c->stream)) return GKS_ERR_CUDA;
+            time_close(c, kTimeRecon);
+            time_open(c);
+            if (launch_flux_faces_lines(c->g, c->P, fs, dt, c->lrec, c->status, c->stream))
+                return GKS_ERR_CUDA;
+            time_close(c, kTimeFlux);
+            time_open(c);
+            if (launch_update_lines(c->g, c->P, stage, c->lrec, dt, Q, L, c->Qs, c->Ls, c->Acc,
+                                    c->LS1, c->status, c->stream))
+                return GKS_ERR_CUDA;
+            time_close(c, kTimeUpdate);
+        }
     }
     if (dt_host_last) {
         int st = 0;

@@ -7,31 +7,85 @@
 //   reconstruction: the 72-entry data vector (the neighbours' averages, the
 //     face neighbours' averaged gradients and the edge neighbours'
 //     tangential derivatives from their lines' means, the own 12 lines),
-//     a = R d with the dense 34 x 72 matrix of the constrained least
-//     squares, GENO (Eq. weno-new; the sub-stencil slopes' tangential parts
-//     from the own lines' means, chi from the misfit of the 54 weighted
-//     derivative rows), the quartic and its derivatives at the 24 face
-//     Gauss points from tabulated monomials;
+//     a = R d with the 34 x 72 matrix of the constrained least squares in
+//     the reflection-symmetrised data basis, GENO (Eq. weno-new; the
+//     sub-stencil slopes' tangential parts from the own lines' means, chi
+//     from the misfit of the 54 weighted derivative rows), the quartic and
+//     its derivatives at the 24 face Gauss points from its parity-class
+//     sums;
 //   flux: the Gauss-point flux of flux_device.cuh; F^n and F_t^n averaged
 //     over the face's 4 points, the interface values kept per point;
 //   update: Q as with gradients; each line from the interface values at
 //     its two face Gauss points (the two-stage update point by point).
-// The dense tables fill most of this translation unit's constant memory.
 #include "recon_common.cuh"
 #include "flux_device.cuh"
 
 namespace gks {
 namespace {
 
-constexpr int kNd = 72;    // data entries per variable
-constexpr int kNl = 54;    // weighted derivative rows
 constexpr int kRecL = 90;  // record values per face: F^n, F_t^n, then 4 x 20 interface values
 
-__constant__ double cRL[kNumBasis][kNd];
-__constant__ double cWBL[kNl][kNumBasis];
-__constant__ double cWL[kNl];
+__constant__ double cRsL[kNumDataL][kMaxClass];  // R in the symmetrised data basis
+__constant__ double cBsL[kNumDataL][kMaxClass];  // weighted derivative rows, same basis
 __constant__ double cMeanL[kNumBasis];
-__constant__ double cMptL[24][4][kNumBasis];
+__constant__ double cMvalL[3][kNumBasis];
+__constant__ double cMderL[3][3][kNumBasis];
+
+// values and derivatives at the 8 Gauss points of the two faces normal to
+// axis D from the quartic's parity-class sums (a monomial's value at the
+// point is its magnitude times the sign pattern of its class; the
+// Walsh-Hadamard transform turns the 8 class sums into the 8 points).
+// GENO's blend is folded in by the caller: a scaled by chi, base =
+// q0 - chi K, and P1's slopes w = (1 - chi) bbar added to the classes of
+// one odd axis (value: w_j |x_j|, |x_D| = 1/2, |x_T| = g) and to class 0
+// of the derivatives.
+template <int D>
+__device__ __forceinline__ void eval_faces_lines(double *__restrict__ fs, long long n, long long c,
+                                                 int v, const double a[kNumBasis], double base,
+                                                 const double w[3], bool blend, const double ih[3]) {
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    double S[8], Dq[3][8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        S[k] = 0.0;
+        Dq[0][k] = Dq[1][k] = Dq[2][k] = 0.0;
+    }
+    static_for<kNumBasis>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        S[basis_class(i)] = fma(a[i], cMvalL[D][i], S[basis_class(i)]);
+        static_for<3>([&](auto Qc) {
+            constexpr int q = decltype(Qc)::value;
+            if constexpr (has_deriv(i, q))
+                Dq[q][deriv_class(i, q)] = fma(a[i], cMderL[D][q][i], Dq[q][deriv_class(i, q)]);
+        });
+    });
+    if (blend) {
+        S[1 << D] = fma(0.5, w[D], S[1 << D]);
+        S[1 << T1] = fma(kG, w[T1], S[1 << T1]);
+        S[1 << T2] = fma(kG, w[T2], S[1 << T2]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Dq[q][0] += w[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) Dq[q][k] *= ih[q];
+    class_to_points(S);
+    class_to_points(Dq[0]);
+    class_to_points(Dq[1]);
+    class_to_points(Dq[2]);
+    const int cmp = frame_comp(v, D);
+#pragma unroll
+    for (int side = 0; side < 2; ++side)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int p = (side << D) | ((kk & 1) << T1) | (((kk >> 1) & 1) << T2);
+            double *o = fs + ((long long)((2 * D + side) * 4 + kk) * 20) * n + c;
+            o[(long long)cmp * n] = base + S[p];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) o[(long long)(5 + 5 * ((q - D + 3) % 3) + cmp) * n] = Dq[q][p];
+        }
+}
 
 // averaged gradient along axis a of variable v in cell nb: the mean of its
 // four lines
@@ -41,6 +95,41 @@ __device__ __forceinline__ double line_mean(const double *__restrict__ Lv, long 
                    __ldg(Lv + (long long)(4 * a + 2) * n + nb) + __ldg(Lv + (long long)(4 * a + 3) * n + nb));
 }
 
+// Value of line-form data column K for one (cell, variable): the
+// neighbours' averages minus q0, their gradients as their lines' means
+// (times h), the own lines (times h)
+template <int K>
+__device__ __forceinline__ double data_col_l(const double *__restrict__ Qv,
+                                             const double *__restrict__ Lv, long long n, long long c,
+                                             const long long nbF[6], const long long nbE[12],
+                                             double q0, const double h[3]) {
+    if constexpr (K < kColEdge) {
+        return __ldg(Qv + nbF[K]) - q0;
+    } else if constexpr (K < kColFaceGrad) {
+        return __ldg(Qv + nbE[K - kColEdge]) - q0;
+    } else if constexpr (K < kColEdgeGrad) {
+        constexpr int m = (K - kColFaceGrad) / 3, j = (K - kColFaceGrad) % 3;
+        return h[j] * line_mean(Lv, n, j, nbF[m]);
+    } else if constexpr (K < kColLines) {
+        constexpr int e = (K - kColEdgeGrad) / 2;
+        constexpr int ea = edge_axis_a(e), eb = edge_axis_b(e), ee = edge_axis_e(e);
+        if constexpr ((K - kColEdgeGrad) % 2 == 0) {
+            constexpr double oa = edge_off(e, ea), ob = edge_off(e, eb);
+            const double da = h[ea] * line_mean(Lv, n, ea, nbE[e]);
+            const double db = h[eb] * line_mean(Lv, n, eb, nbE[e]);
+            return (oa * da - ob * db) * kRs2;
+        } else {
+            return h[ee] * line_mean(Lv, n, ee, nbE[e]);
+        }
+    } else {
+        constexpr int a = (K - kColLines) / 4;
+        return h[a] * __ldg(Lv + (long long)(K - kColLines) * n + c);
+    }
+}
+
+// One (cell, variable) per thread (blockIdx.y = variable), periodic
+// uniform grid. a = R d orbit by orbit in the symmetrised data basis
+// (kSymL: 330 products instead of 34 x 72), GENO's misfit the same way.
 __global__ void __launch_bounds__(128) recon5_lines_kernel(GridDesc g, int nonlinear,
                                                            const double *__restrict__ Q,
                                                            const double *__restrict__ L,
@@ -53,72 +142,70 @@ __global__ void __launch_bounds__(128) recon5_lines_kernel(GridDesc g, int nonli
     const int j = (int)((c / g.nx) % g.ny);
     const int k = (int)(c / ((long long)g.nx * g.ny));
     const int c0[3] = {i, j, k};
+    long long nbF[6], nbE[12];
+#pragma unroll
+    for (int m = 0; m < 6; ++m)
+        nbF[m] = cell_index(g, wrap(i + face_off(m, 0), g.nx), wrap(j + face_off(m, 1), g.ny),
+                            wrap(k + face_off(m, 2), g.nz));
+#pragma unroll
+    for (int e = 0; e < 12; ++e)
+        nbE[e] = cell_index(g, wrap(i + edge_off(e, 0), g.nx), wrap(j + edge_off(e, 1), g.ny),
+                            wrap(k + edge_off(e, 2), g.nz));
+    double h[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) h[a] = cell_h(g, a, c0[a]);
+    const double ih[3] = {1.0 / h[0], 1.0 / h[1], 1.0 / h[2]};
     const double *Qv = Q + (long long)v * n;
     const double *Lv = L + (long long)v * 12 * n;
     const double q0 = __ldg(Qv + c);
-    double h0[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) h0[a] = cell_h(g, a, c0[a]);
 
-    double d[kNd];
-#pragma unroll 1
-    for (int m = 0; m < 6; ++m) {
-        int cc[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) cc[a] = wrap(c0[a] + face_off(m, a), axis_len(g, a));
-        const long long nb = cell_index(g, cc[0], cc[1], cc[2]);
-        d[m] = __ldg(Qv + nb) - q0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) d[18 + 3 * m + a] = cell_h(g, a, cc[a]) * line_mean(Lv, n, a, nb);
-    }
-#pragma unroll 1
-    for (int e = 0; e < 12; ++e) {
-        int cc[3], o[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            o[a] = edge_off(e, a);
-            cc[a] = wrap(c0[a] + o[a], axis_len(g, a));
-        }
-        const long long nb = cell_index(g, cc[0], cc[1], cc[2]);
-        d[6 + e] = __ldg(Qv + nb) - q0;
-        const int ea = edge_axis_a(e), eb = edge_axis_b(e), ee = edge_axis_e(e);
-        const double da = cell_h(g, ea, cc[ea]) * line_mean(Lv, n, ea, nb);
-        const double db = cell_h(g, eb, cc[eb]) * line_mean(Lv, n, eb, nb);
-        d[36 + 2 * e] = (o[ea] * da - o[eb] * db) * kRs2;
-        d[36 + 2 * e + 1] = cell_h(g, ee, cc[ee]) * line_mean(Lv, n, ee, nb);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) d[60 + 4 * a + kk] = h0[a] * __ldg(Lv + (long long)(4 * a + kk) * n + c);
-
-    // a = R d
     double a[kNumBasis];
 #pragma unroll
     for (int ii = 0; ii < kNumBasis; ++ii) a[ii] = 0.0;
-#pragma unroll 1
-    for (int col = 0; col < kNd; ++col) {
-        const double dc = d[col];
-#pragma unroll
-        for (int ii = 0; ii < kNumBasis; ++ii) a[ii] = fma(cRL[ii][col], dc, a[ii]);
-    }
+    double dface[6], g0[3] = {0.0, 0.0, 0.0};
+    double norm2 = 0.0;  // |d_C|^2 + |W d_B|^2 for GENO's misfit
+    double ov[8];
+    static_for<kNumDataL>([&](auto Rr) {
+        constexpr int r = decltype(Rr)::value;
+        constexpr int nm = kSymL.nm[r];
+        if constexpr (kSymL.orbit[r] == r) {
+            static_for<nm>([&](auto Qq) {
+                constexpr int q = decltype(Qq)::value;
+                constexpr int col = kSymL.mem[r][q];
+                ov[q] = data_col_l<col>(Qv, Lv, n, c, nbF, nbE, q0, h);
+                constexpr double wc = col_weight(col);
+                norm2 = fma(wc * wc * ov[q], ov[q], norm2);
+                if constexpr (col < kColEdge) dface[col] = ov[q];
+                if constexpr (col >= kColLines) g0[(col - kColLines) / 4] += 0.25 * ov[q];
+            });
+        }
+        double ds = kSymL.sgn[r][0] > 0 ? ov[0] : -ov[0];
+        static_for<nm - 1>([&](auto Qq) {
+            constexpr int q = decltype(Qq)::value + 1;
+            if constexpr (kSymL.sgn[r][q] > 0) ds += ov[q];
+            else ds -= ov[q];
+        });
+        constexpr int cls = kSymL.cls[r];
+        static_for<kClass.n[cls]>([&](auto J) {
+            constexpr int jj = decltype(J)::value;
+            constexpr int ib = kClass.member[cls][jj];
+            a[ib] = fma(cRsL[r][jj], ds, a[ib]);
+        });
+    });
     double K = 0.0;
-#pragma unroll
-    for (int ii = 0; ii < kNumBasis; ++ii) K = fma(a[ii], cMeanL[ii], K);
-    const double base = q0 - K;
+    static_for<kNumBasis>([&](auto I) {
+        constexpr int ii = decltype(I)::value;
+        if constexpr (basis_class(ii) == 0) K = fma(a[ii], cMeanL[ii], K);
+    });
 
     double chi = 1.0, bbar[3] = {0.0, 0.0, 0.0};
     if (nonlinear) {
         const double eps = 1e-15;
-        double g0[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-            g0[q] = 0.25 * (d[60 + 4 * q] + d[61 + 4 * q] + d[62 + 4 * q] + d[63 + 4 * q]);
         double w[6], wsum = 0.0;
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
             const int ax = m / 2;
-            const double bn = (m & 1) ? d[m] : -d[m];
+            const double bn = (m & 1) ? dface[m] : -dface[m];
             double s = bn * bn;
 #pragma unroll
             for (int q = 0; q < 3; ++q)
@@ -131,58 +218,57 @@ __global__ void __launch_bounds__(128) recon5_lines_kernel(GridDesc g, int nonli
         for (int m = 0; m < 6; ++m) w[m] /= wsum;
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-            bbar[q] = (1.0 - w[2 * q] - w[2 * q + 1]) * g0[q] - w[2 * q] * d[2 * q] +
-                      w[2 * q + 1] * d[2 * q + 1];
-        // GENO's misfit (reading R5) over the 54 weighted derivative rows
-        double res2 = 0.0, norm2 = 0.0;
-#pragma unroll
-        for (int m = 0; m < 18; ++m) norm2 = fma(d[m], d[m], norm2);
-#pragma unroll 1
-        for (int q = 0; q < kNl; ++q) {
-            const double wd = cWL[q] * d[18 + q];
-            double r = -wd;
-#pragma unroll
-            for (int ii = 0; ii < kNumBasis; ++ii) r = fma(cWBL[q][ii], a[ii], r);
-            res2 = fma(r, r, res2);
-            norm2 = fma(wd, wd, norm2);
-        }
+            bbar[q] = (1.0 - w[2 * q] - w[2 * q + 1]) * g0[q] - w[2 * q] * dface[2 * q] +
+                      w[2 * q + 1] * dface[2 * q + 1];
+        // GENO's misfit (reading R5): |W (B a - d_B)|^2 over the 54 weighted
+        // derivative rows, orbit by orbit (sum of res_r^2 / nm), the
+        // derivative columns loaded again
+        double res2 = 0.0;
+        static_for<kNumDataL>([&](auto Rr) {
+            constexpr int r = decltype(Rr)::value;
+            constexpr int nm = kSymL.nm[r];
+            if constexpr (kSymL.mem[r][0] >= kColFaceGrad) {
+                if constexpr (kSymL.orbit[r] == r) {
+                    static_for<nm>([&](auto Qq) {
+                        constexpr int q = decltype(Qq)::value;
+                        constexpr int col = kSymL.mem[r][q];
+                        ov[q] = data_col_l<col>(Qv, Lv, n, c, nbF, nbE, q0, h);
+                    });
+                }
+                double ds = kSymL.sgn[r][0] > 0 ? ov[0] : -ov[0];
+                static_for<nm - 1>([&](auto Qq) {
+                    constexpr int q = decltype(Qq)::value + 1;
+                    if constexpr (kSymL.sgn[r][q] > 0) ds += ov[q];
+                    else ds -= ov[q];
+                });
+                constexpr int cls = kSymL.cls[r];
+                constexpr double wr = col_weight(kSymL.mem[r][0]);
+                double res = -wr * ds;
+                static_for<kClass.n[cls]>([&](auto J) {
+                    constexpr int jj = decltype(J)::value;
+                    constexpr int ib = kClass.member[cls][jj];
+                    res = fma(cBsL[r][jj], a[ib], res);
+                });
+                res2 = fma(res * (1.0 / nm), res, res2);
+            }
+        });
         const double r0 = __ldg(Q + c), e0 = __ldg(Q + 4 * n + c);
         const double S = v == 0 ? r0 : (v == 4 ? e0 : sqrt(fabs(r0 * e0)));
         const double sig = res2 / (norm2 + kGenoKappa * kGenoKappa * S * S + eps);
         const double s = sig * (1.0 / kGenoSigma0);
         chi = 1.0 / (1.0 + s + s * s);
     }
-    // the 24 face Gauss points
-#pragma unroll 1
-    for (int pt = 0; pt < 24; ++pt) {
-        const int f = pt / 4, kk = pt % 4, D = f / 2, side = f & 1;
-        double val = base, der[3] = {0.0, 0.0, 0.0};
+    double w[3] = {0.0, 0.0, 0.0}, base = q0 - K;
+    if (nonlinear) {
 #pragma unroll
-        for (int ii = 0; ii < kNumBasis; ++ii) {
-            val = fma(a[ii], cMptL[pt][0][ii], val);
-            der[0] = fma(a[ii], cMptL[pt][1][ii], der[0]);
-            der[1] = fma(a[ii], cMptL[pt][2][ii], der[1]);
-            der[2] = fma(a[ii], cMptL[pt][3][ii], der[2]);
-        }
-        if (nonlinear) {
-            double x[3];
-            x[D] = side ? 0.5 : -0.5;
-            x[(D + 1) % 3] = (kk & 1) ? kG : -kG;
-            x[(D + 2) % 3] = (kk & 2) ? kG : -kG;
-            const double p1 = fma(bbar[0], x[0], fma(bbar[1], x[1], fma(bbar[2], x[2], q0)));
-            val = fma(chi, val - p1, p1);
+        for (int ii = 0; ii < kNumBasis; ++ii) a[ii] *= chi;
+        base = fma(-chi, K, q0);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) der[q] = fma(chi, der[q] - bbar[q], bbar[q]);
-        }
-        const int cmp = frame_comp(v, D);
-        double *o = fs + ((long long)pt * 20) * n + c;
-        o[(long long)cmp * n] = val;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const int jf = (q - D + 3) % 3;
-            o[(long long)(5 + 5 * jf + cmp) * n] = der[q] / h0[q];
-        }
+        for (int q = 0; q < 3; ++q) w[q] = (1.0 - chi) * bbar[q];
     }
+    eval_faces_lines<0>(fs, n, c, v, a, base, w, nonlinear, ih);
+    eval_faces_lines<1>(fs, n, c, v, a, base, w, nonlinear, ih);
+    eval_faces_lines<2>(fs, n, c, v, a, base, w, nonlinear, ih);
 }
 
 // The Gauss-point flux of every face (periodic): four adjacent lanes hold
@@ -336,11 +422,11 @@ int upload_recon_tables_lines(void) {
         if (build_recon_tables_lines(&t)) return -1;
         built = 1;
     }
-    if (cudaMemcpyToSymbol(cRL, t.R, sizeof(t.R)) != cudaSuccess) return -2;
-    if (cudaMemcpyToSymbol(cWBL, t.WB, sizeof(t.WB)) != cudaSuccess) return -2;
-    if (cudaMemcpyToSymbol(cWL, t.w, sizeof(t.w)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(cRsL, t.Rs, sizeof(t.Rs)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(cBsL, t.Bs, sizeof(t.Bs)) != cudaSuccess) return -2;
     if (cudaMemcpyToSymbol(cMeanL, t.mean, sizeof(t.mean)) != cudaSuccess) return -2;
-    if (cudaMemcpyToSymbol(cMptL, t.mpt, sizeof(t.mpt)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(cMvalL, t.mval, sizeof(t.mval)) != cudaSuccess) return -2;
+    if (cudaMemcpyToSymbol(cMderL, t.mder, sizeof(t.mder)) != cudaSuccess) return -2;
     return 0;
 }
 

@@ -9,6 +9,8 @@
 //   z = argmin |B Q2 z - (d_B - B Q1 y)|   (Householder QR of B Q2).
 // Applying this to the unit data vectors gives the 34 x 63 matrix R.
 #include <cmath>
+#include <memory>
+#include <new>
 #include <cstring>
 #include <vector>
 
@@ -389,28 +391,38 @@ int build_recon_tables_lines(ReconTablesLines *t) {
         t->mean[i] = 1.0;
         for (int j = 0; j < 3; ++j) t->mean[i] *= mono_int(kExp[i][j]) / factorial(kExp[i][j]);
     }
-    // x^e/e! and its derivatives at the 24 face Gauss points (face f = 2d +
-    // side, point k), in the order of the face-state buffer
-    for (int f = 0; f < 6; ++f)
-        for (int k = 0; k < 4; ++k) {
-            const int d = f / 2, pt = 4 * f + k;
-            double x[3];
-            x[d] = (f & 1) ? 0.5 : -0.5;
-            x[(d + 1) % 3] = (k & 1) ? g : -g;
-            x[(d + 2) % 3] = (k & 2) ? g : -g;
-            for (int i = 0; i < nb; ++i) {
-                t->mpt[pt][0][i] = mono(x, i);
-                for (int q = 0; q < 3; ++q) {
-                    if (kExp[i][q] == 0) { t->mpt[pt][1 + q][i] = 0.0; continue; }
-                    double w = 1.0;
-                    for (int j = 0; j < 3; ++j) {
-                        const int e = kExp[i][j] - (j == q ? 1 : 0);
-                        w *= std::pow(x[j], e) / factorial(e);
-                    }
-                    t->mpt[pt][1 + q][i] = w;
-                }
+    // R and the weighted derivative rows in the symmetrised basis of the
+    // line-form data vector (as for the averaged-gradient form; entries on
+    // class(r) monomials only, checked)
+    double rmax = 0.0, bmax = 0.0;
+    for (int i = 0; i < nb; ++i)
+        for (int k = 0; k < ncol; ++k) rmax = std::fmax(rmax, std::fabs(t->R[i][k]));
+    for (int k = 0; k < nl; ++k)
+        for (int i = 0; i < nb; ++i) bmax = std::fmax(bmax, std::fabs(t->WB[k][i]));
+    for (int r = 0; r < kNumDataL; ++r) {
+        const int c = kSymL.cls[r];
+        for (int i = 0; i < nb; ++i) {
+            double sr = 0.0, sb = 0.0;
+            for (int q = 0; q < kSymL.nm[r]; ++q) {
+                const int m = kSymL.mem[r][q];
+                sr += kSymL.sgn[r][q] * t->R[i][m];
+                if (m >= ne) sb += kSymL.sgn[r][q] * t->WB[m - ne][i];
+            }
+            sr /= kSymL.nm[r];
+            if (parity_class(kExp[i][0], kExp[i][1], kExp[i][2]) == c) {
+                t->Rs[r][kClass.pos[i]] = sr;
+                t->Bs[r][kClass.pos[i]] = sb;
+            } else if (std::fabs(sr) > 1e-12 * rmax || std::fabs(sb) > 1e-12 * bmax) {
+                return -1;
             }
         }
+    }
+    // magnitudes of the monomials and their derivatives at the face Gauss
+    // points: the same as for the averaged-gradient form
+    std::unique_ptr<ReconTables> base(new (std::nothrow) ReconTables);
+    if (!base || build_recon_tables(base.get())) return -1;
+    std::memcpy(t->mval, base->mval, sizeof(t->mval));
+    std::memcpy(t->mder, base->mder, sizeof(t->mder));
     return 0;
 }
 
