@@ -271,6 +271,17 @@ int gks_status(gks_ctx *ctx, int *status);
  * caller-owned host memory of 34*63 doubles. */
 int gks_recon_matrix(double *R);
 
+/* N2 -- host-only: the least-squares matrix of the line form (the cell's
+ * own data its 12 line-averaged derivatives; gks_step_lines), the same
+ * weighted constrained least squares with the 3 own-gradient rows replaced
+ * by the 12 line rows (weight 1; a line's row is the difference of the
+ * monomial at its two end points): a = R d, d of 72 entries per variable
+ * (the first 60 as for gks_recon_matrix, then line k of axis a at
+ * 60 + 4a + k, scaled by h_a). R is caller-owned host memory of 34*72
+ * doubles. GKS_ERR_ARG if the tables fail their own reflection-symmetry
+ * check. */
+int gks_recon_matrix_lines(double *R);
+
 /* a8 -- learned smoothness indicator (an extension of the method: the
  * paper has no such component). A per-(cell, variable) network predicts
  * whether GENO's chi (Eq. weno-new) would equal 1 -- the nonlinear

@@ -645,6 +645,16 @@ int gks_recon_matrix(double *R) {
     return rc == 0 ? GKS_OK : GKS_ERR_ARG;
 }
 
+int gks_recon_matrix_lines(double *R) {
+    if (!R) return GKS_ERR_ARG;
+    ReconTablesLines *t = new (std::nothrow) ReconTablesLines;
+    if (!t) return GKS_ERR_NOMEM;
+    const int rc = build_recon_tables_lines(t);
+    if (rc == 0) std::memcpy(R, t->R, sizeof(t->R));
+    delete t;
+    return rc == 0 ? GKS_OK : GKS_ERR_ARG;
+}
+
 int gks_kernel_timing(gks_ctx *c, int on) {
     if (!c || (on != 0 && on != 1)) return GKS_ERR_ARG;
     if (on) {

@@ -75,6 +75,7 @@ SIGNATURES = {
     "gks_diagnostics": (_I, [_VP, _VP, _VP, ctypes.POINTER(_D)]),
     "gks_status": (_I, [_VP, ctypes.POINTER(_I)]),
     "gks_recon_matrix": (_I, [ctypes.POINTER(_D)]),
+    "gks_recon_matrix_lines": (_I, [ctypes.POINTER(_D)]),
     "gks_diagnostics_noalloc": (_I, [_VP, _VP, _I, _I, _I, _D, _D, _D, _D, _D, _I, _D, _VP, _VP]),
     "gks_fma_rate": (_I, [_I, _VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "gks_kernel_timing": (_I, [_VP, _I]),
@@ -172,6 +173,14 @@ def mlp_train(params, x, y, epochs=10, batch=4096, lr=3e-3, neg_weight=1.0, seed
                                float(lr), float(neg_weight), int(seed) & 0xFFFFFFFF,
                                _ptr(hist, torch.float32), _VP(st.cuda_stream)), "gks_mlp_train")
     return hist.cpu().numpy()[:epochs]
+
+
+def recon_matrix_lines() -> np.ndarray:
+    """The library's line-form reconstruction matrix (34 x 72), host-built."""
+    R = np.zeros((34, 72))
+    _check(lib().gks_recon_matrix_lines(R.ctypes.data_as(ctypes.POINTER(_D))),
+           "gks_recon_matrix_lines")
+    return R
 
 
 def recon_matrix() -> np.ndarray:

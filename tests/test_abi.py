@@ -34,6 +34,16 @@ def test_host_recon_matrix_matches_oracle(orc):
     np.testing.assert_allclose(R, orc.recon5_matrix(), rtol=0, atol=1e-12)
 
 
+def test_host_line_form_matrix_matches_oracle(orc):
+    """The library's and the oracle's line-form matrices come from separate
+    solves (null-space QR here, a KKT system there) of the same least
+    squares; the library's builder also checks its symmetrised tables."""
+    from paper_2508_19911_gb300 import gks
+    R = gks.recon_matrix_lines()
+    ref = orc.recon5b_matrix()
+    np.testing.assert_allclose(R, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
 def test_error_strings_and_defaults():
     from paper_2508_19911_gb300 import gks
     L = gks.lib()
