@@ -218,8 +218,8 @@ int gks_step_host(gks_ctx *ctx, double *Q, double *gradQ, int nsteps, double t_s
  * gradient. L: device double[5][12][n], entry (v, 4a + k, cell), line k
  * through tangential position (+-, +-) of axis (a+1)%3 (bit 0 of k) and
  * (a+2)%3 (bit 1); the averaged gradient along a is the mean of its four
- * lines. FP64 CGKS-5th contexts on periodic grids only (GKS_ERR_STATE
- * otherwise); the first call allocates 390 doubles per cell (face records
+ * lines. FP64 CGKS-5th contexts on periodic grids (uniform or stretched)
+ * only (GKS_ERR_STATE otherwise); the first call allocates 390 doubles per cell (face records
  * [3][90][n], two line buffers) kept until gks_destroy.
  *
  * gks_reconstruct_lines: the face states of every cell, layout of

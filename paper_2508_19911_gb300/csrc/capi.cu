@@ -509,9 +509,13 @@ int gks_step_host(gks_ctx *c, double *Q, double *G, int nsteps, double t_stop, d
 
 namespace {
 // the line-averaged-derivative form needs the FP64 CGKS-5th on a periodic
-// grid; its buffers and tables are set up on first use
+// grid (uniform or stretched); its buffers and tables are set up on first
+// use
 int lines_ready(gks_ctx *c) {
-    if (c->P.scheme != GKS_SCHEME_CGKS5 || c->mixed || c->g.general) return GKS_ERR_STATE;
+    if (c->P.scheme != GKS_SCHEME_CGKS5 || c->mixed) return GKS_ERR_STATE;
+    if (c->g.bc[0] != GKS_BC_PERIODIC || c->g.bc[1] != GKS_BC_PERIODIC ||
+        c->g.bc[2] != GKS_BC_PERIODIC)
+        return GKS_ERR_STATE;
     if (c->lrec) return GKS_OK;
     const int t = upload_recon_tables_lines();
     if (t) return t == -1 ? GKS_ERR_ARG : GKS_ERR_CUDA;

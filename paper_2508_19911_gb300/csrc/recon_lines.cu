@@ -98,37 +98,40 @@ __device__ __forceinline__ double line_mean(const double *__restrict__ Lv, long 
 // Value of line-form data column K for one (cell, variable): the
 // neighbours' averages minus q0, their gradients as their lines' means
 // (times h), the own lines (times h)
+// hm[a][o + 1]: the cell size along axis a of the cells at offset o = -1,
+// 0, 1 (a stretched mesh takes each neighbour's gradient in its own index
+// coordinates, as the reference-cell mapping of the averaged-gradient form)
 template <int K>
 __device__ __forceinline__ double data_col_l(const double *__restrict__ Qv,
                                              const double *__restrict__ Lv, long long n, long long c,
                                              const long long nbF[6], const long long nbE[12],
-                                             double q0, const double h[3]) {
+                                             double q0, const double hm[3][3]) {
     if constexpr (K < kColEdge) {
         return __ldg(Qv + nbF[K]) - q0;
     } else if constexpr (K < kColFaceGrad) {
         return __ldg(Qv + nbE[K - kColEdge]) - q0;
     } else if constexpr (K < kColEdgeGrad) {
         constexpr int m = (K - kColFaceGrad) / 3, j = (K - kColFaceGrad) % 3;
-        return h[j] * line_mean(Lv, n, j, nbF[m]);
+        return hm[j][face_off(m, j) + 1] * line_mean(Lv, n, j, nbF[m]);
     } else if constexpr (K < kColLines) {
         constexpr int e = (K - kColEdgeGrad) / 2;
         constexpr int ea = edge_axis_a(e), eb = edge_axis_b(e), ee = edge_axis_e(e);
         if constexpr ((K - kColEdgeGrad) % 2 == 0) {
             constexpr double oa = edge_off(e, ea), ob = edge_off(e, eb);
-            const double da = h[ea] * line_mean(Lv, n, ea, nbE[e]);
-            const double db = h[eb] * line_mean(Lv, n, eb, nbE[e]);
+            const double da = hm[ea][edge_off(e, ea) + 1] * line_mean(Lv, n, ea, nbE[e]);
+            const double db = hm[eb][edge_off(e, eb) + 1] * line_mean(Lv, n, eb, nbE[e]);
             return (oa * da - ob * db) * kRs2;
         } else {
-            return h[ee] * line_mean(Lv, n, ee, nbE[e]);
+            return hm[ee][1] * line_mean(Lv, n, ee, nbE[e]);
         }
     } else {
         constexpr int a = (K - kColLines) / 4;
-        return h[a] * __ldg(Lv + (long long)(K - kColLines) * n + c);
+        return hm[a][1] * __ldg(Lv + (long long)(K - kColLines) * n + c);
     }
 }
 
-// One (cell, variable) per thread (blockIdx.y = variable), periodic
-// uniform grid. a = R d orbit by orbit in the symmetrised data basis
+// One (cell, variable) per thread (blockIdx.y = variable), periodic grid
+// (uniform or stretched). a = R d orbit by orbit in the symmetrised data basis
 // (kSymL: 330 products instead of 34 x 72), GENO's misfit the same way.
 __global__ void __launch_bounds__(128) recon5_lines_kernel(GridDesc g, int nonlinear,
                                                            const double *__restrict__ Q,
@@ -151,10 +154,12 @@ __global__ void __launch_bounds__(128) recon5_lines_kernel(GridDesc g, int nonli
     for (int e = 0; e < 12; ++e)
         nbE[e] = cell_index(g, wrap(i + edge_off(e, 0), g.nx), wrap(j + edge_off(e, 1), g.ny),
                             wrap(k + edge_off(e, 2), g.nz));
-    double h[3];
+    double hm[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) h[a] = cell_h(g, a, c0[a]);
-    const double ih[3] = {1.0 / h[0], 1.0 / h[1], 1.0 / h[2]};
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int o = 0; o < 3; ++o) hm[a][o] = cell_h(g, a, wrap(c0[a] + o - 1, axis_len(g, a)));
+    const double ih[3] = {1.0 / hm[0][1], 1.0 / hm[1][1], 1.0 / hm[2][1]};
     const double *Qv = Q + (long long)v * n;
     const double *Lv = L + (long long)v * 12 * n;
     const double q0 = __ldg(Qv + c);
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(128) recon5_lines_kernel(GridDesc g, int nonli
             static_for<nm>([&](auto Qq) {
                 constexpr int q = decltype(Qq)::value;
                 constexpr int col = kSymL.mem[r][q];
-                ov[q] = data_col_l<col>(Qv, Lv, n, c, nbF, nbE, q0, h);
+                ov[q] = data_col_l<col>(Qv, Lv, n, c, nbF, nbE, q0, hm);
                 constexpr double wc = col_weight(col);
                 norm2 = fma(wc * wc * ov[q], ov[q], norm2);
                 if constexpr (col < kColEdge) dface[col] = ov[q];
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(128) recon5_lines_kernel(GridDesc g, int nonli
                     static_for<nm>([&](auto Qq) {
                         constexpr int q = decltype(Qq)::value;
                         constexpr int col = kSymL.mem[r][q];
-                        ov[q] = data_col_l<col>(Qv, Lv, n, c, nbF, nbE, q0, h);
+                        ov[q] = data_col_l<col>(Qv, Lv, n, c, nbF, nbE, q0, hm);
                     });
                 }
                 double ds = kSymL.sgn[r][0] > 0 ? ov[0] : -ov[0];

@@ -4,8 +4,8 @@ CPU oracle, through the C-ABI (gks_reconstruct_lines, gks_step_lines,
 gks_lines_gradients).
 
 Ragged periodic grids (9 x 8 x 7 cells: several warps, a ragged tail in
-every axis) from a perturbed Taylor-Green state whose lines carry their own
-seeded perturbation. FP64 results must agree with the oracle within 1e-11
+every axis; uniform, and stretched along x and y) from a perturbed
+Taylor-Green state whose lines carry their own seeded perturbation. FP64 results must agree with the oracle within 1e-11
 relative to each physical group's magnitude (lines: plus max|Q|/h, their
 rounding scale, as for the gradients of the averaged-gradient form).
 """
@@ -33,6 +33,19 @@ def torch_dev():
 
 def case(n=(9, 8, 7), amp=0.02, seed=47):
     Q, G, grid, L = wl.taylor_green(n, Ma=0.3, lines=True)
+    Q, G = wl.perturb(Q, G, amp=amp, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    scale = np.abs(L).reshape(5, -1).max(axis=1)[:, None, None, None, None]
+    L = L + amp * scale * rng.standard_normal(L.shape)
+    return Q, np.ascontiguousarray(L), grid
+
+
+def stretched_case(n=(9, 8, 7), amp=0.005, seed=53):
+    """The same state on a periodic box whose x and y cells are stretched
+    (0.7-1.3 of the mean size)."""
+    edges = (wl.stretched_edges(n[0], 2 * np.pi, 0.3), wl.stretched_edges(n[1], 2 * np.pi, -0.25),
+             np.linspace(0.0, 2 * np.pi, n[2] + 1))
+    Q, G, grid, L = wl.taylor_green(edges=edges, Ma=0.3, lines=True)
     Q, G = wl.perturb(Q, G, amp=amp, seed=seed)
     rng = np.random.default_rng(seed + 1)
     scale = np.abs(L).reshape(5, -1).max(axis=1)[:, None, None, None, None]
@@ -92,6 +105,33 @@ def test_ten_steps_with_lines_match_oracle(torch_dev, nonlinear):
     for v in range(5):
         sc = np.abs(Lo[v]).max() + qscale[v]
         assert np.abs(Lg[v] - Lo[v]).max() / sc < TOL, v
+
+
+@pytest.mark.parametrize("nonlinear", [False, True])
+def test_lines_on_a_stretched_periodic_grid_match_oracle(torch_dev, nonlinear):
+    """Face states and 10 steps on a stretched periodic mesh (each
+    neighbour's gradient taken in its own index coordinates)."""
+    torch, dev = torch_dev
+    Q, L, grid = stretched_case()
+    s = solver(grid, nonlinear=nonlinear, spacing=grid.spacing)
+    P = oparams(grid, nonlinear, spacing=grid.spacing)
+    fs = s.reconstruct_lines(torch.tensor(Q, device=dev), torch.tensor(L, device=dev))
+    ref = oracle.face_states_b(P, Q, L).transpose(0, 2, 1, 3).reshape(6, 20, -1)
+    got = fs.cpu().numpy().transpose(0, 2, 1, 3).reshape(6, 20, -1)
+    scale = np.abs(ref).max(axis=2, keepdims=True)
+    scale = np.where(scale == 0, 1.0, scale)
+    assert float(np.max(np.abs(got - ref) / scale)) < TOL
+    Qd, Ld = torch.tensor(Q, device=dev), torch.tensor(L, device=dev)
+    s.step_lines(Qd, Ld, nsteps=10)
+    assert s.status() == 0
+    Qo, Lo = Q.copy(), L.copy()
+    oracle.run_b(P, Qo, Lo, nsteps=10)
+    assert group_err(Qd.cpu().numpy(), Qo) < TOL
+    h = min(float(w.min()) for w in grid.spacing)
+    qscale = np.abs(Qo).reshape(5, -1).max(axis=1) / h
+    Lg = Ld.cpu().numpy()
+    for v in range(5):
+        assert np.abs(Lg[v] - Lo[v]).max() / (np.abs(Lo[v]).max() + qscale[v]) < TOL, v
 
 
 def test_uniform_flow_with_lines_is_bitwise_steady(torch_dev):
