@@ -165,3 +165,78 @@ def test_reading_b_is_fifth_order_on_smooth_advection(orc):
         errs.append(np.abs(Q[0] - Qe[0]).mean())
     order = math.log2(errs[0] / errs[1])
     assert 4.5 < order < 5.6, (errs, order)
+
+
+def _stretched_tg_lines(n=(7, 6, 5)):
+    edges = (wl.stretched_edges(n[0], 2 * np.pi, 0.3), wl.stretched_edges(n[1], 2 * np.pi, -0.25),
+             np.linspace(0.0, 2 * np.pi, n[2] + 1))
+    return wl.taylor_green(edges=edges, Ma=0.3, lines=True)
+
+
+def test_reading_b_on_a_stretched_mesh_conserves_and_keeps_uniform_flow(orc):
+    """Stretched periodic mesh (cells 0.7-1.3 of the mean along x and y):
+    sum Q vol stays to round-off; a uniform state (lines zero) stays bit
+    for bit."""
+    Q, G, grid, L = _stretched_tg_lines()
+    Q, _ = wl.perturb(Q, G, amp=1e-2, seed=9)
+    P = orc.params(n=grid.n, L=grid.L, spacing=grid.spacing)
+    vol = np.einsum("k,j,i->kji", grid.spacing[2], grid.spacing[1], grid.spacing[0])
+    s0 = (Q * vol).reshape(5, -1).sum(axis=1)
+    orc.run_b(P, Q, L, nsteps=3)
+    s1 = (Q * vol).reshape(5, -1).sum(axis=1)
+    scale = (np.abs(Q) * vol).reshape(5, -1).sum(axis=1)
+    assert np.all(np.abs(s1 - s0) <= 1e-14 * scale), (s1 - s0) / scale
+
+    U = np.zeros_like(Q)
+    U[0], U[1], U[2], U[3] = 1.1, 0.33, -0.22, 0.11
+    U[4] = 2.0 / 0.4 + 0.5 * (0.33 ** 2 + 0.22 ** 2 + 0.11 ** 2) / 1.1
+    U0, LU = U.copy(), np.zeros_like(L)
+    orc.run_b(P, U, LU, nsteps=2)
+    np.testing.assert_array_equal(U, U0)
+    assert np.all(LU == 0.0)
+
+
+def test_reading_b_reproduces_index_coordinate_quartics_on_a_stretched_mesh(orc):
+    """The reference-cell mapping on a stretched mesh: cell data of quartics
+    in the index coordinates (averages over unit index cells; each line's
+    physical derivative = its index-coordinate difference over that cell's
+    own size) give, at the target cell's face Gauss points, the quartics'
+    values and their index derivatives divided by the target's sizes,
+    exactly. A neighbour's gradient scaled by the target's size instead of
+    its own fails this."""
+    rng = np.random.default_rng(77)
+    polys = [random_poly(rng, 4, scale=0.2) for _ in range(5)]
+    polys[0].coef[(0, 0, 0)] += 3.0
+    polys[4].coef[(0, 0, 0)] += 9.0
+    n = (5, 5, 5)
+    hs = [np.array([0.7, 1.3, 0.9, 1.2, 0.8]), np.array([1.1, 0.6, 1.0, 1.4, 0.9]),
+          np.array([0.8, 0.9, 1.25, 0.75, 1.3])]
+    Q = np.zeros((5, 5, 5, 5))
+    L = np.zeros((5, 12, 5, 5, 5))
+    for k in range(5):
+        for j in range(5):
+            for i in range(5):
+                o = (i - 2, j - 2, k - 2)
+                for v, P in enumerate(polys):
+                    Q[v, k, j, i] = cell_avg(P, o, (1.0, 1.0, 1.0))
+                    for a in range(3):
+                        for kk in range(4):
+                            x1, x2 = _line_points(a, kk)
+                            p1 = [o[q] + x1[q] for q in range(3)]
+                            p2 = [o[q] + x2[q] for q in range(3)]
+                            L[v, 4 * a + kk, k, j, i] = (P(*p2) - P(*p1)) / hs[a][o[a] + 2]
+    Pp = orc.params(n=n, L=tuple(float(h.sum()) for h in hs), spacing=tuple(hs), nonlinear=0)
+    fs = orc.face_states_b(Pp, Q, L)
+    c = 2 + 5 * (2 + 5 * 2)
+    got = fs[:, :, :, c]
+    ref = expected_face_states(polys, (1.0, 1.0, 1.0))
+    h0 = [hs[a][2] for a in range(3)]
+    for f in range(6):
+        d = f // 2
+        frame = [d, (d + 1) % 3, (d + 2) % 3]
+        scale = np.abs(ref).max()
+        np.testing.assert_allclose(got[f, :, :5], ref[f, :, :5], rtol=0, atol=1e-11 * scale)
+        for jf in range(3):
+            sl = slice(5 + 5 * jf, 10 + 5 * jf)
+            np.testing.assert_allclose(got[f, :, sl] * h0[frame[jf]], ref[f, :, sl], rtol=0,
+                                       atol=1e-11 * scale)
