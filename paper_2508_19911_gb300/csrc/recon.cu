@@ -19,6 +19,8 @@
 //   3. evaluate P4 and its gradient at the 24 face Gauss points: the
 //      monomials are summed into 8 parity classes per face axis and the 8
 //      points of a face follow by a Walsh-Hadamard transform.
+#include <mutex>
+
 #include "recon_mixed_device.cuh"
 
 namespace gks {
@@ -172,6 +174,9 @@ __global__ void __launch_bounds__(128) recon2_mixed_kernel(GridDesc g, Slab S, i
 }  // namespace
 
 int upload_recon_tables(void) {
+    // one builder at a time: contexts may be created from several threads
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     static ReconTables t;
     static int built = 0;
     if (!built) {

@@ -17,6 +17,8 @@
 //     over the face's 4 points, the interface values kept per point;
 //   update: Q as with gradients; each line from the interface values at
 //     its two face Gauss points (the two-stage update point by point).
+#include <mutex>
+
 #include "recon_common.cuh"
 #include "flux_device.cuh"
 
@@ -421,6 +423,8 @@ __global__ void lines_to_grad_kernel(long long n, const double *__restrict__ L,
 }  // namespace
 
 int upload_recon_tables_lines(void) {
+    static std::mutex mu;  // contexts may be used from several threads
+    std::lock_guard<std::mutex> lock(mu);
     static ReconTablesLines t;
     static int built = 0;
     if (!built) {
