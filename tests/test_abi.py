@@ -68,6 +68,10 @@ def test_init_rejects_bad_arguments_before_touching_the_gpu():
         assert not ctx.value
     assert L.gks_step(None, None, None, 1, 0.0, None, None) == gks.GKS_ERR_ARG
     assert L.gks_step_host(None, None, None, 1, 0.0, None) == gks.GKS_ERR_ARG
+    assert L.gks_reconstruct_lines(None, None, None, None) == gks.GKS_ERR_ARG
+    assert L.gks_step_lines(None, None, None, 1, 0.0, None, None) == gks.GKS_ERR_ARG
+    assert L.gks_lines_gradients(None, None, None) == gks.GKS_ERR_ARG
+    assert L.gks_recon_matrix_lines(None) == gks.GKS_ERR_ARG
 
 
 def test_fma_rate_rejects_bad_arguments_before_touching_the_gpu():
