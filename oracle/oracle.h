@@ -39,7 +39,9 @@
  *       volume;
  *   R10 dt computed once per step, used unchanged in both stages.
  * None of R1-R10 can be pinned to the paper (it defers them to its
- * references): "parity unpinned" for those choices; everything else is
+ * references): "parity unpinned" for those choices, except R7, whose
+ * effect the Navier-Stokes limit fixes (heat flux c_p mu/Pr dT/dx at
+ * Pr = 0.72, pinned by the Chapman-Enskog test); everything else is
  * pinned by the CPU tests (closed forms, brute-force quadrature, exact
  * polynomial reproduction, invariants, the Sod solution).
  */
