@@ -240,3 +240,57 @@ def test_reading_b_reproduces_index_coordinate_quartics_on_a_stretched_mesh(orc)
             sl = slice(5 + 5 * jf, 10 + 5 * jf)
             np.testing.assert_allclose(got[f, :, sl] * h0[frame[jf]], ref[f, :, sl], rtol=0,
                                        atol=1e-11 * scale)
+
+
+@pytest.mark.parametrize("normal,offset", [((1, 0, 0), 5.3), ((1, 1, 0), 10.2),
+                                           ((1, 1, 1), 15.1), ((1, 0.3, 0), 6.6)])
+def test_reading_b_chi_collapses_where_a_discontinuity_cuts(orc, normal, offset):
+    """GENO with the line data (Sec. 3.2): a unit density step along a plane
+    of several orientations; in every cell the plane cuts through its middle
+    (centre within 0.3 h of it) chi <= 1e-3. The lines of a cell are the
+    step's differences between their end points; a neighbour's gradient is
+    the mean of its four lines."""
+    from test_oracle_recon import _step_cells
+    n = 10
+    Qs, _ = _step_cells(normal, offset, n)
+    nv = np.asarray(normal, float)
+    f = lambda p: float(nv @ np.asarray(p, float) > offset)
+    Ls = np.zeros((12, n, n, n))
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                centre = np.array([i + 0.5, j + 0.5, k + 0.5])
+                for a in range(3):
+                    for kk in range(4):
+                        x1, x2 = _line_points(a, kk)
+                        Ls[4 * a + kk, k, j, i] = f(centre + x2) - f(centre + x1)
+    grad = Ls.reshape(3, 4, n, n, n).mean(axis=1)   # [axis][k][j][i]
+    idx = np.arange(n) + 0.5
+    cut = []
+    for k in range(3, n - 3):
+        for j in range(3, n - 3):
+            for i in range(3, n - 3):
+                if abs(nv @ np.array([idx[i], idx[j], idx[k]]) - offset) / np.linalg.norm(nv) <= 0.3:
+                    cut.append((i, j, k))
+    assert len(cut) >= 4
+    for (i, j, k) in cut:
+        q00 = 1.0 + Qs[k, j, i]
+        d = np.zeros(72)
+        at = lambda o: (k + o[2], j + o[1], i + o[0])
+        for m, o in enumerate(FACE):
+            d[m] = 1.0 + Qs[at(o)] - q00
+            for a in range(3):
+                d[18 + 3 * m + a] = grad[(a,) + at(o)]
+        for e, o in enumerate(EDGE):
+            d[6 + e] = 1.0 + Qs[at(o)] - q00
+            ax = [q for q in range(3) if o[q] != 0]
+            ez = [q for q in range(3) if o[q] == 0][0]
+            d[36 + 2 * e] = (o[ax[0]] * grad[(ax[0],) + at(o)] -
+                             o[ax[1]] * grad[(ax[1],) + at(o)]) / math.sqrt(2)
+            d[36 + 2 * e + 1] = grad[(ez,) + at(o)]
+        d[60:] = Ls[:, k, j, i]
+        q0 = np.array([q00, 0.0, 0.0, 0.0, 2.5])
+        dvec = np.concatenate([d] + [np.zeros(72)] * 4)
+        _, chi = orc.recon5b_cell(q0, dvec, (1.0, 1.0, 1.0), nonlinear=1)
+        assert chi[0] <= 1e-3, ((i, j, k), chi[0])
+        np.testing.assert_array_equal(chi[1:], 1.0)
