@@ -205,7 +205,8 @@ def recon5b_cell(q0, dvec, h=(1.0, 1.0, 1.0), nonlinear=1):
 
 def run_b(P, Q, L, nsteps=1, t_stop=np.inf, t=0.0):
     """CGKS-5th with reading B: advance Q [5][cells...] and the line-averaged
-    derivatives L [5][12][cells...] in place; returns (t, dt_last)."""
+    derivatives L [5][12][cells...] in place (any of the boundaries of
+    params(bc=...), uniform or stretched); returns (t, dt_last)."""
     tt = np.array([t], float)
     dl = np.zeros(1)
     _check(lib().orc_run_b(ctypes.byref(P), _ptr(Q), _ptr(L), nsteps, t_stop,

@@ -337,3 +337,74 @@ def test_reading_b_chi_collapses_where_a_discontinuity_cuts(orc, normal, offset)
         _, chi = orc.recon5b_cell(q0, dvec, (1.0, 1.0, 1.0), nonlinear=1)
         assert chi[0] <= 1e-3, ((i, j, k), chi[0])
         np.testing.assert_array_equal(chi[1:], 1.0)
+
+
+def _group_err_b(A, B):
+    worst = 0.0
+    for g in ([0], [1, 2, 3], [4]):
+        worst = max(worst, float(np.abs(A[g] - B[g]).max() / (np.abs(B[g]).max() + 1e-300)))
+    return worst
+
+
+@pytest.mark.parametrize("nonlinear", [1, 0])
+@pytest.mark.parametrize("stretch", [0.0, 0.3])
+def test_reading_b_octant_with_symmetry_planes_equals_the_periodic_vortex(orc, nonlinear, stretch):
+    """Mirror ghosts with the line data (reading R15 for lines: a ghost's
+    average s Q, its lines' mean along the normal -s, along the boundary
+    s times the cell's; boundary faces pair the cell's face states with
+    their mirror image): the Taylor-Green vortex is symmetric about x, y,
+    z = 0, pi, so the octant [0, pi]^3 with six symmetry planes must follow
+    the periodic [0, 2 pi]^3 run's first octant to rounding, lines
+    included."""
+    n, steps = 6, 3
+    full_edges = wl.stretched_edges(2 * n, 2 * np.pi, stretch)
+    Qf, _, gf, Lf = wl.taylor_green(edges=(full_edges,) * 3, lines=True)
+    Qo, _, go, Lo = wl.taylor_green(edges=(full_edges[:n + 1],) * 3, lines=True)
+    np.testing.assert_array_equal(Qo, Qf[..., :n, :n, :n])
+    np.testing.assert_array_equal(Lo, Lf[..., :n, :n, :n])
+    sp_f = gf.spacing if stretch else (None,) * 3
+    sp_o = go.spacing if stretch else (None,) * 3
+    Pf = orc.params(n=gf.n, L=gf.L, nonlinear=nonlinear, spacing=sp_f)
+    Po = orc.params(n=go.n, L=go.L, nonlinear=nonlinear, spacing=sp_o, bc=(orc.BC_SYMMETRY,) * 3)
+    tf, _ = orc.run_b(Pf, Qf, Lf, nsteps=steps)
+    to, _ = orc.run_b(Po, Qo, Lo, nsteps=steps)
+    assert abs(tf - to) <= 1e-14 * tf
+    assert _group_err_b(Qo, Qf[..., :n, :n, :n]) < 1e-12
+    h = min(float(np.min(w)) for w in go.spacing)
+    Lq = Lf[..., :n, :n, :n]
+    for g in ([0], [1, 2, 3], [4]):
+        scale = np.abs(Lq[g]).max() + np.abs(Qo[g]).max() / h
+        assert np.abs(Lo[g] - Lq[g]).max() / scale < 1e-12, g
+
+
+def test_reading_b_closed_box_conserves_mass_and_energy(orc):
+    n = 6
+    edges = (wl.stretched_edges(n, np.pi, 0.4), wl.stretched_edges(n, np.pi, -0.2),
+             np.linspace(0.0, np.pi, n + 1))
+    Q, G, g, L = wl.taylor_green(edges=edges, Ma=0.3, lines=True)
+    Q, _ = wl.perturb(Q, G, amp=1e-2, seed=3)
+    P = orc.params(n=g.n, L=g.L, spacing=g.spacing, bc=(1, 1, 1))
+    vol = np.einsum("k,j,i->kji", *[g.widths(a) for a in (2, 1, 0)])
+    m0 = [np.sum(Q[v] * vol) for v in (0, 4)]
+    orc.run_b(P, Q, L, nsteps=4)
+    m1 = [np.sum(Q[v] * vol) for v in (0, 4)]
+    for a, b in zip(m0, m1):
+        assert abs(b - a) <= 1e-13 * abs(a)
+
+
+def test_reading_b_uniform_flow_along_walls_and_through_outflow_is_bitwise_steady(orc):
+    nx, ny, nz = 5, 6, 4
+    edges = (wl.stretched_edges(nx, 1.0, 0.5), wl.stretched_edges(ny, 2.0, -0.4),
+             np.linspace(0.0, 1.0, nz + 1))
+    g = wl.grid_from_edges(edges)
+    rho, U, V, W, p = 1.3, 0.0, 0.4, -0.25, 0.9
+    Q = np.zeros((5, nz, ny, nx))
+    Q[0], Q[1], Q[2], Q[3] = rho, rho * U, rho * V, rho * W
+    Q[4] = p / 0.4 + 0.5 * rho * (U * U + V * V + W * W)
+    L = np.zeros((5, 12, nz, ny, nx))
+    Q0 = Q.copy()
+    # x: symmetry planes (no normal velocity); y: outflow; z: periodic
+    P = orc.params(n=g.n, L=g.L, spacing=g.spacing, bc=(1, 2, 0), mu0=1e-2)
+    orc.run_b(P, Q, L, nsteps=3)
+    np.testing.assert_array_equal(Q, Q0)
+    assert np.all(L == 0.0)
