@@ -251,13 +251,19 @@ def reference_arm(args, rank):
     el = time.perf_counter() - t0
     stages = 2 if cg else 1
     val = n ** 3 * stages * args.steps / el
+    full_n = getattr(args, "n", None) or 512
+    tag = "learned" if getattr(args, "indicator", False) else getattr(args, "precision", "fp64")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "cell-stage/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{name}_{n}^3_{args.scheme}_fp64_nonlinear",
-                   "note": f"bounded CPU sample of the {name} workload"},
+        # the GPU arm's config (same workload name and physics); each timed
+        # step is a bounded sample of it, described in cpu_baseline.sample
+        "config": {"workload": f"{name}_{full_n}^3_{args.scheme}_{tag}_nonlinear",
+                   "cells": full_n ** 3, "scheme": args.scheme, "stages_per_step": stages,
+                   "gamma": 1.4, "Pr": 0.72, "cfl": 0.3, "parallelism": "host cores",
+                   "sample": f"{name} {n}^3 per timed step (same generator and physics)"},
         "cpu_baseline": {"value": val, "unit": "cell-stage/s", "cores": cores, "kind": "oracle",
                          "sample": f"{name} {n}^3 {args.scheme} FP64, {args.steps} steps"},
         "e2e": {"value": val, "unit": "cell-stage/s", "h2d_bytes_per_step": 0,
